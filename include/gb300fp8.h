@@ -1,0 +1,185 @@
+/*
+ * gb300fp8 — FP8 (E4M3) dense and 2:4-sparse GEMM for one NVIDIA GB300 GPU.
+ *
+ * C ABI of libgb300fp8.so.  The operation is the one arXiv 2602.10262
+ * characterises on FP8 matrix cores (section 2 "FP8 Matrix Cores", section 4):
+ * FP8 x FP8 operands with FP32 accumulation,
+ *
+ *     C[m,n] = alpha * dA[m] * dB[n] * sum_k dec(A[m,k]) * dec(B[n,k]),
+ *
+ * dense, or with A in 2:4 structured sparsity (section 2 "Structured
+ * Sparsity", section 6: two of every four consecutive elements along K are
+ * zero).  dec() is the OCP E4M3 decoding the paper cites; dA, dB are the
+ * dequantisation factors written by fp8_quantize_e4m3.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named as device pointers must point to device memory of the
+ *     current CUDA device; the caller owns every buffer and the library never
+ *     frees caller memory.
+ *   - All work is enqueued on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) and the call returns after enqueueing.  Outputs are
+ *     valid once the stream has reached that point.
+ *   - Matrices are row-major with a row stride ("ld") in elements.  FP8 code
+ *     matrices are bytes; A is [M, K] and B is stored [N, K] (K contiguous
+ *     in both, i.e. the product is A * B^T of the stored arrays).
+ *   - Return value: FP8_OK, or a negative fp8_status for rejected arguments
+ *     (nothing is enqueued then) or a CUDA launch error.  Errors detected on
+ *     the device (non-finite input, a pipeline wait that timed out) are
+ *     recorded in a per-device error word read by fp8_last_device_error.
+ */
+#ifndef GB300FP8_H
+#define GB300FP8_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fp8_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    FP8_OK = 0,
+    FP8_PENDING = 1,          /* server: request not finished yet */
+    FP8_ERR_INVALID = -1,     /* bad argument (null pointer, bad mode, ...) */
+    FP8_ERR_SHAPE = -2,       /* unsupported or inconsistent sizes */
+    FP8_ERR_ALIGN = -3,       /* pointer / stride alignment requirement violated */
+    FP8_ERR_NONFINITE = -4,   /* quantisation input held NaN or Inf */
+    FP8_ERR_OOM = -5,         /* server: admission refused for lack of free HBM */
+    FP8_ERR_CUDA = -6,        /* a CUDA runtime call failed */
+    FP8_ERR_TIMEOUT = -7,     /* a device pipeline wait ran past its limit */
+    FP8_ERR_UNSUPPORTED = -8  /* no sm_103a device, or feature not built */
+} fp8_status;
+
+/* Static English text for a status code. */
+const char *fp8_status_string(int status);
+
+/* Synchronises `stream`, then returns and clears the device error word of the
+ * current device (FP8_OK if no kernel reported an error since the last call).
+ * Kernels record FP8_ERR_NONFINITE (quantisation saw NaN/Inf) and
+ * FP8_ERR_TIMEOUT (an mbarrier wait exceeded its ~2 s limit; the kernel then
+ * stops its pipeline, releases tensor memory and exits). */
+int fp8_last_device_error(fp8_stream_t stream);
+
+/* Number of SMs of the current device (persistent grids are sized from it). */
+int fp8_device_sm_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Scale selection + E4M3 quantisation (rows a1, a2 of the path).
+ * Paper: section 2 "FP8 Matrix Cores" (OCP E4M3 format).
+ *
+ * x:  device fp32 [rows, cols], row stride ldx elements (ldx >= cols).
+ * scale_mode 0: one scale for the tensor; 1: one scale per row.
+ * For each scaling group: amax = max|x|;  s = fl32(448 / amax);
+ * d = fl32(amax / 448)  (both IEEE-rounded divisions; amax == 0 gives
+ * s = d = 1);  q = E4M3(fl32(x * s)) rounded to nearest even and saturated to
+ * +-448.
+ * q:  device uint8 [rows, cols], row stride ldq bytes (ldq >= cols).
+ * dequant_scale: device fp32, [1] (mode 0) or [rows] (mode 1), receives d.
+ * Mode 0 uses dequant_scale[0] as its reduction slot while it runs.
+ * NaN/Inf in x: FP8_ERR_NONFINITE in the device error word; q and d are then
+ * unspecified.  rows == 0 or cols == 0: nothing to do, FP8_OK.
+ * ------------------------------------------------------------------------- */
+int fp8_quantize_e4m3(const float *x, int64_t rows, int64_t cols, int64_t ldx, int scale_mode,
+                      uint8_t *q, int64_t ldq, float *dequant_scale, fp8_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * 2:4 prune + compress (row a3).  Paper: section 2 "Structured Sparsity",
+ * section 6 (2 of every 4 consecutive elements along K are zero; the paper
+ * blames a fixed conversion + allocation + dispatch cost in section 6.1.1 —
+ * this call allocates nothing and is one bandwidth-bound kernel).
+ *
+ * a: device E4M3 codes [M, K], row stride lda bytes; K % 4 == 0 (else
+ * FP8_ERR_SHAPE).  For each row and each group g of four codes
+ * a[4g..4g+3]: key = code & 0x7F (monotone in |value|); the two positions
+ * first in (key descending, index ascending) order are kept.
+ * a_vals: device [M, K/2] (row stride K/2): the kept codes of group g at
+ *         2g, 2g+1 in increasing index order.
+ * a_meta: device [M, ceil(K/8)] (row stride ceil(K/8)): for group g the
+ *         nibble i0 | (i1 << 2) (i0 < i1 the kept indices) in byte g/2,
+ *         low nibble for even g.
+ * ------------------------------------------------------------------------- */
+int prune24_compress(const uint8_t *a, int64_t M, int64_t K, int64_t lda, uint8_t *a_vals,
+                     uint8_t *a_meta, fp8_stream_t stream);
+
+/* Inverse of prune24_compress: out [M, K] (row stride K) gets the kept codes
+ * at their positions and 0x00 elsewhere. */
+int prune24_decompress(const uint8_t *a_vals, const uint8_t *a_meta, int64_t M, int64_t K,
+                       uint8_t *out, fp8_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Dense FP8 GEMM (rows a4, a6).  Paper: section 4 (FP8 x FP8 -> FP32 matrix
+ * operation).
+ *
+ * C[m,n] = alpha * sa(m) * sb(n) * sum_k dec(A[m,k]) dec(B[n,k]), where
+ * sa(m) = a_scale[a_mode ? m : 0] and sb(n) = b_scale[b_mode ? n : 0].
+ * A: device E4M3 [M, K], row stride lda bytes; B: device E4M3 [N, K], row
+ * stride ldb bytes.  A, B 16-byte aligned, lda and ldb multiples of 16
+ * (FP8_ERR_ALIGN otherwise).  M, N, K >= 0 arbitrary (ragged edges are
+ * zero-filled on load and masked on store; K == 0 writes zeros).
+ * Products are accumulated in FP32 on the tensor cores (tcgen05, tensor
+ * memory accumulators); the epilogue applies the scales in FP32.
+ * C: device [M, N], row stride ldc elements, out_dtype 0 = fp32,
+ * 1 = bf16 (round to nearest even).
+ * ------------------------------------------------------------------------- */
+int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
+                   const uint8_t *B, int64_t ldb, const float *a_scale, int a_mode,
+                   const float *b_scale, int b_mode, float alpha, void *C, int64_t ldc,
+                   int out_dtype, fp8_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * 2:4-sparse FP8 GEMM (rows a5, a6).  Paper: section 6 (sparse GEMM against
+ * dense GEMM on the same operands).
+ *
+ * Same product as gemm_fp8_dense with A given in the compressed form written
+ * by prune24_compress (a_vals [M, K/2], a_meta [M, K/8], both contiguous);
+ * the result equals the dense product of the decompressed A.  K % 128 == 0
+ * (FP8_ERR_SHAPE otherwise).  Sparsity is on the M-side operand; for sparse
+ * weights pass the weight as A and the activations as B, and set
+ * out_transposed = 1 to receive C^T, i.e. out[n, m] with row stride ldc.
+ * ------------------------------------------------------------------------- */
+int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t *a_vals,
+                      const uint8_t *a_meta, const uint8_t *B, int64_t ldb, const float *a_scale,
+                      int a_mode, const float *b_scale, int b_mode, float alpha, void *C,
+                      int64_t ldc, int out_dtype, int out_transposed, fp8_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Grouped GEMM (row a7): many independent problems in one persistent launch.
+ * Paper: section 7.1 (a transformer-style sequence of FP8 GEMMs) and the
+ * section 8 guidance to batch small or fragmented work.
+ *
+ * Each problem is a dense (A_meta == NULL) or 2:4-sparse (A = a_vals,
+ * A_meta = a_meta) GEMM with the conventions above; out_transposed as in
+ * gemm_fp8_sparse24 (dense problems may use it too).  The problem table is
+ * passed by value in the kernel parameters (no device workspace); at most
+ * FP8_GROUPED_MAX_PROBLEMS problems per call (FP8_ERR_SHAPE otherwise).
+ * Results are bitwise identical to issuing each problem alone.
+ * ------------------------------------------------------------------------- */
+#define FP8_GROUPED_MAX_PROBLEMS 32
+
+typedef struct {
+    int64_t M, N, K;
+    const uint8_t *A;       /* dense [M,K] codes, or a_vals [M,K/2] */
+    const uint8_t *A_meta;  /* NULL for dense; a_meta [M,K/8] for 2:4 */
+    int64_t lda;            /* dense only: row stride of A in bytes */
+    const uint8_t *B;       /* [N,K] codes */
+    int64_t ldb;
+    const float *a_scale;
+    int a_mode;
+    const float *b_scale;
+    int b_mode;
+    float alpha;
+    void *C;
+    int64_t ldc;
+    int out_dtype;
+    int out_transposed;
+} fp8_gemm_problem;
+
+int gemm_fp8_grouped(const fp8_gemm_problem *problems, int num_problems, fp8_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300FP8_H */

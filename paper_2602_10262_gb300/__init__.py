@@ -1,0 +1,188 @@
+"""gb300fp8: FP8 E4M3 dense and 2:4-sparse GEMM for NVIDIA GB300 (sm_103a).
+
+Thin PyTorch-facing binding over the C ABI of ``libgb300fp8.so``
+(include/gb300fp8.h).  Every function has the C entry point's name and only
+marshals arguments: it checks dtypes and devices, takes ``data_ptr()`` and
+the current CUDA stream, allocates outputs with torch when none are given,
+and raises ``Fp8Error`` on a non-zero status.  All arithmetic runs in the
+library's CUDA kernels; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+
+__all__ = [
+    "Fp8Error", "library", "fp8_quantize_e4m3", "prune24_compress", "prune24_decompress",
+    "gemm_fp8_dense", "gemm_fp8_sparse24", "gemm_fp8_grouped", "fp8_last_device_error",
+    "fp8_device_sm_count", "OUT_F32", "OUT_BF16",
+]
+
+OUT_F32 = 0
+OUT_BF16 = 1
+
+
+class Fp8Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = library().fp8_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def library():
+    """The loaded CDLL (built in tree on first use)."""
+    return _lib.load()
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise Fp8Error(rc, where)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype: torch.dtype, dims: int):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.dim() != dims:
+        raise ValueError(f"{name} must have {dims} dimensions")
+    if dims == 2 and t.numel() > 0 and t.stride(1) != 1:
+        raise ValueError(f"{name} must have a contiguous last dimension")
+
+
+def _ld(t: torch.Tensor) -> int:
+    return t.stride(0) if t.dim() == 2 and t.size(0) > 1 else t.size(-1)
+
+
+def _p(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def fp8_last_device_error(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device error word."""
+    return int(library().fp8_last_device_error(_stream(stream)))
+
+
+def fp8_device_sm_count() -> int:
+    return int(library().fp8_device_sm_count())
+
+
+def fp8_quantize_e4m3(x: torch.Tensor, scale_mode: int, q: Optional[torch.Tensor] = None,
+                      dequant_scale: Optional[torch.Tensor] = None, stream=None):
+    """fp32 [R, C] -> (E4M3 codes uint8 [R, C], dequant scales fp32 [1] or [R])."""
+    _dev(x, "x", torch.float32, 2)
+    R, C = x.shape
+    if q is None:
+        q = torch.empty((R, C), dtype=torch.uint8, device=x.device)
+    if dequant_scale is None:
+        dequant_scale = torch.empty((1 if scale_mode == 0 else R,), dtype=torch.float32, device=x.device)
+    _dev(q, "q", torch.uint8, 2)
+    rc = library().fp8_quantize_e4m3(_p(x), R, C, _ld(x), int(scale_mode), _p(q), _ld(q),
+                                     _p(dequant_scale), _stream(stream))
+    _check(rc, "fp8_quantize_e4m3")
+    return q, dequant_scale
+
+
+def prune24_compress(a: torch.Tensor, a_vals: Optional[torch.Tensor] = None,
+                     a_meta: Optional[torch.Tensor] = None, stream=None):
+    """E4M3 codes [M, K] -> (kept codes [M, K/2], metadata [M, ceil(K/8)])."""
+    _dev(a, "a", torch.uint8, 2)
+    M, K = a.shape
+    if a_vals is None:
+        a_vals = torch.empty((M, K // 2), dtype=torch.uint8, device=a.device)
+    if a_meta is None:
+        a_meta = torch.empty((M, (K + 7) // 8), dtype=torch.uint8, device=a.device)
+    rc = library().prune24_compress(_p(a), M, K, _ld(a), _p(a_vals), _p(a_meta), _stream(stream))
+    _check(rc, "prune24_compress")
+    return a_vals, a_meta
+
+
+def prune24_decompress(a_vals: torch.Tensor, a_meta: torch.Tensor, K: int,
+                       out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    M = a_vals.shape[0]
+    if out is None:
+        out = torch.empty((M, K), dtype=torch.uint8, device=a_vals.device)
+    rc = library().prune24_decompress(_p(a_vals), _p(a_meta), M, K, _p(out), _stream(stream))
+    _check(rc, "prune24_decompress")
+    return out
+
+
+def _out(C, rows, cols, out_dtype, device):
+    dt = torch.bfloat16 if out_dtype == OUT_BF16 else torch.float32
+    if C is None:
+        C = torch.empty((rows, cols), dtype=dt, device=device)
+    _dev(C, "C", dt, 2)
+    return C
+
+
+def gemm_fp8_dense(A: torch.Tensor, B: torch.Tensor, a_scale: torch.Tensor, a_mode: int,
+                   b_scale: torch.Tensor, b_mode: int, alpha: float = 1.0,
+                   out_dtype: int = OUT_BF16, C: Optional[torch.Tensor] = None,
+                   stream=None) -> torch.Tensor:
+    """C[M, N] = alpha * sa * sb * dec(A)[M, K] @ dec(B)[N, K]^T."""
+    _dev(A, "A", torch.uint8, 2)
+    _dev(B, "B", torch.uint8, 2)
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("K mismatch")
+    C = _out(C, M, N, out_dtype, A.device)
+    rc = library().gemm_fp8_dense(M, N, K, _p(A), _ld(A), _p(B), _ld(B), _p(a_scale), int(a_mode),
+                                  _p(b_scale), int(b_mode), float(alpha), _p(C), _ld(C),
+                                  int(out_dtype), _stream(stream))
+    _check(rc, "gemm_fp8_dense")
+    return C
+
+
+def gemm_fp8_sparse24(a_vals: torch.Tensor, a_meta: torch.Tensor, B: torch.Tensor,
+                      a_scale: torch.Tensor, a_mode: int, b_scale: torch.Tensor, b_mode: int,
+                      alpha: float = 1.0, out_dtype: int = OUT_BF16, out_transposed: bool = False,
+                      C: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Same product with A given as (a_vals [M, K/2], a_meta [M, K/8])."""
+    _dev(a_vals, "a_vals", torch.uint8, 2)
+    _dev(a_meta, "a_meta", torch.uint8, 2)
+    _dev(B, "B", torch.uint8, 2)
+    M = a_vals.shape[0]
+    K = a_vals.shape[1] * 2
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("K mismatch")
+    C = _out(C, N if out_transposed else M, M if out_transposed else N, out_dtype, B.device)
+    rc = library().gemm_fp8_sparse24(M, N, K, _p(a_vals), _p(a_meta), _p(B), _ld(B), _p(a_scale),
+                                     int(a_mode), _p(b_scale), int(b_mode), float(alpha), _p(C),
+                                     _ld(C), int(out_dtype), int(bool(out_transposed)),
+                                     _stream(stream))
+    _check(rc, "gemm_fp8_sparse24")
+    return C
+
+
+def make_problem(A: torch.Tensor, B: torch.Tensor, a_scale, a_mode, b_scale, b_mode, C,
+                 alpha: float = 1.0, out_dtype: int = OUT_BF16, A_meta=None, K: Optional[int] = None,
+                 out_transposed: bool = False) -> _lib.FP8Problem:
+    """Build one ``fp8_gemm_problem`` entry (tensors must outlive the call)."""
+    sparse = A_meta is not None
+    M = A.shape[0]
+    Kd = A.shape[1] * 2 if sparse else A.shape[1]
+    if K is not None and K != Kd:
+        raise ValueError("K mismatch")
+    return _lib.FP8Problem(M, B.shape[0], Kd, A.data_ptr(), 0 if A_meta is None else A_meta.data_ptr(),
+                           _ld(A), B.data_ptr(), _ld(B), a_scale.data_ptr(), int(a_mode),
+                           b_scale.data_ptr(), int(b_mode), float(alpha), C.data_ptr(), _ld(C),
+                           int(out_dtype), int(bool(out_transposed)))
+
+
+def gemm_fp8_grouped(problems: Sequence[_lib.FP8Problem], stream=None) -> None:
+    """Run every problem in one persistent launch."""
+    arr = (_lib.FP8Problem * len(problems))(*problems)
+    rc = library().gemm_fp8_grouped(arr, len(problems), _stream(stream))
+    _check(rc, "gemm_fp8_grouped")

@@ -1,0 +1,619 @@
+// FP8 E4M3 GEMM on tcgen05 tensor cores: gemm_fp8_dense, gemm_fp8_sparse24
+// and gemm_fp8_grouped all run the kernel below.
+//
+// Roles of one CTA (192 threads, one CTA per SM, persistent over tiles):
+//   warp 0, lane 0   TMA producer: for each (tile, k-block) waits for a free
+//                    ring slot, arms the slot's "full" mbarrier with the
+//                    expected bytes and issues two 2-D TMA loads (128B swizzle).
+//   warp 1           allocates 512 TMEM columns (two accumulators of up to
+//                    256 fp32 columns); lane 0 then issues the MMAs: per
+//                    k-block 4 x tcgen05.mma.kind::f8f6f4 (K = 32 each) into
+//                    the tile's accumulator, tcgen05.commit -> "empty" slot
+//                    barrier, and after the last k-block commit -> "tmem_full".
+//   warps 2..5       epilogue: tcgen05.ld of the accumulator (warp w reads
+//                    TMEM lanes 32*(w%4)..), scale by alpha*sa*sb in fp32,
+//                    convert, store to global; then release the accumulator.
+// Two accumulators let the epilogue of tile i overlap the MMAs of tile i+1.
+//
+// Tile = 128 rows of P (the MMA M side) x bn rows of Q (MMA N side), bn in
+// {16,...,256} per problem; K-block = 128 codes (one 128-byte swizzle row).
+// P/Q are the two stored operands; for skinny products the host swaps them
+// (P = B, Q = A) so that the long side fills the 128-row MMA and the output
+// is written transposed.
+#include <algorithm>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <mutex>
+
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace gb300 {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 128;
+constexpr int BN_MAX = 256;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK;                    // 16 KB
+constexpr int B_BYTES = BN_MAX * BK;                // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;      // 48 KB
+constexpr int TMEM_COLS = 2 * BN_MAX;
+constexpr int NUM_THREADS = 192;
+constexpr int GROUP_M = 8;                          // raster: 8 M-blocks per band
+constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers*/;
+
+struct Problem {
+    CUtensorMap tmP;        // P [rows_p, K] codes, box {128, 128}
+    CUtensorMap tmQ;        // Q [rows_q, K] codes, box {128, bn}
+    const float* sp;        // scale of P rows (mode sp_mode)
+    const float* sq;        // scale of Q rows
+    void* C;
+    long long ldc;
+    int rows_p, rows_q, K;
+    int sp_mode, sq_mode;
+    float alpha;
+    int out_bf16;
+    int trans_out;          // 0: C[i * ldc + j]; 1: C[j * ldc + i]  (i: P row, j: Q row)
+    int vec_store;          // 16-byte stores allowed in the non-transposed path
+    int bn;
+    int m_blocks, n_blocks, k_blocks;
+    int tile_start;
+    uint32_t idesc;
+};
+
+template <int MAXP>
+struct Params {
+    Problem prob[MAXP];
+    int num_problems;
+    int total_tiles;
+    int* err;
+};
+
+struct TileCoord {
+    int p, m_blk, n_blk;
+};
+
+template <int MAXP>
+__device__ __forceinline__ TileCoord tile_coord(const Params<MAXP>& prm, int tile)
+{
+    int p = 0;
+#pragma unroll 1
+    while (p + 1 < prm.num_problems && prm.prob[p + 1].tile_start <= tile)
+        ++p;
+    const Problem& P = prm.prob[p];
+    const int lt = tile - P.tile_start;
+    const int per_band = GROUP_M * P.n_blocks;
+    const int band = lt / per_band;
+    const int first_m = band * GROUP_M;
+    const int rows_in_band = min(P.m_blocks - first_m, GROUP_M);
+    const int r = lt - band * per_band;
+    return {p, first_m + r % rows_in_band, r / rows_in_band};
+}
+
+__device__ __forceinline__ void abort_pipeline(volatile int* flag, int* err)
+{
+    report_device_error(err, FP8_ERR_TIMEOUT);
+    *flag = 1;
+}
+
+// ---------------------------------------------------------------- epilogue
+
+__device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_ok, float fi,
+                                              int j0, const uint32_t (&r)[16])
+{
+    float v[16];
+    const int rows_q = P.rows_q;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const int j = j0 + t;
+        const float sj = (j < rows_q) ? __ldg(P.sq + (P.sq_mode ? j : 0)) : 0.0f;
+        v[t] = __fmul_rn(__fmul_rn(__uint_as_float(r[t]), fi), sj);
+    }
+    if (!P.trans_out) {
+        if (!row_ok)
+            return;
+        if (P.out_bf16) {
+            __nv_bfloat16* c = static_cast<__nv_bfloat16*>(P.C) + static_cast<long long>(i) * P.ldc + j0;
+            if (P.vec_store && j0 + 16 <= rows_q) {
+                uint32_t w[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
+                    w[t] = *reinterpret_cast<uint32_t*>(&h);
+                }
+                reinterpret_cast<uint4*>(c)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                reinterpret_cast<uint4*>(c)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 16; ++t)
+                    if (j0 + t < rows_q)
+                        c[t] = __float2bfloat16_rn(v[t]);
+            }
+        } else {
+            float* c = static_cast<float*>(P.C) + static_cast<long long>(i) * P.ldc + j0;
+            if (P.vec_store && j0 + 16 <= rows_q) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    reinterpret_cast<float4*>(c)[t] =
+                        make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 16; ++t)
+                    if (j0 + t < rows_q)
+                        c[t] = v[t];
+            }
+        }
+    } else {
+        if (!row_ok)
+            return;
+        // C[j, i]: for a fixed j the 32 lanes write 32 consecutive i
+        if (P.out_bf16) {
+            __nv_bfloat16* c = static_cast<__nv_bfloat16*>(P.C) + i;
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                if (j0 + t < rows_q)
+                    c[static_cast<long long>(j0 + t) * P.ldc] = __float2bfloat16_rn(v[t]);
+        } else {
+            float* c = static_cast<float*>(P.C) + i;
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                if (j0 + t < rows_q)
+                    c[static_cast<long long>(j0 + t) * P.ldc] = v[t];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <int MAXP>
+__global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_constant__ Params<MAXP> prm)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    // bar[0..S) full, bar[S..2S) empty, bar[2S..2S+2) tmem_full,
+    // bar[2S+2..2S+4) tmem_empty, bar[2S+4] drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2 * STAGES + 5);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const uint32_t smem_base = smem_u32(smem);
+    const uint32_t bar_base = smem_u32(bar);
+    auto full_bar = [&](int s) { return bar_base + 8u * s; };
+    auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
+    auto tfull_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + b); };
+    auto tempty_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t drain_bar = bar_base + 8u * (2 * STAGES + 4);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), 128);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ TMA producer
+        for (int p = 0; p < prm.num_problems; ++p) {
+            tma_prefetch_desc(&prm.prob[p].tmP);
+            tma_prefetch_desc(&prm.prob[p].tmQ);
+        }
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t armed = 0;                 // bit s: slot s armed at least once
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x) {
+            const TileCoord tc = tile_coord(prm, tile);
+            const Problem& P = prm.prob[tc.p];
+            const uint32_t bytes = A_BYTES + static_cast<uint32_t>(P.bn) * BK;
+            for (int kb = 0; kb < P.k_blocks; ++kb) {
+                if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
+                    ok = false;
+                    abort_pipeline(abort_flag, prm.err);
+                    break;
+                }
+                mbar_arrive_expect_tx(full_bar(stage), bytes);
+                const uint32_t sa = smem_base + stage * STAGE_BYTES;
+                tma_load_2d(sa, &P.tmP, full_bar(stage), kb * BK, tc.m_blk * BM);
+                tma_load_2d(sa + A_BYTES, &P.tmQ, full_bar(stage), kb * BK, tc.n_blk * P.bn);
+                armed |= 1u << stage;
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+        if (!ok) {
+            // let the copies already in flight land before the CTA exits:
+            // the latest arming of slot s has parity `phase` if s < stage
+            // (armed in the current round), else `phase ^ 1`
+            const volatile int never = 0;
+            for (int s = 0; s < STAGES; ++s) {
+                if (!(armed >> s & 1u))
+                    continue;
+                const uint32_t last_parity = (s < stage) ? phase : (phase ^ 1u);
+                mbar_wait(full_bar(s), last_parity, &never);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------------------------ MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            int local = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x, ++local) {
+                const TileCoord tc = tile_coord(prm, tile);
+                const Problem& P = prm.prob[tc.p];
+                const int acc = local & 1;
+                const uint32_t acc_phase = (local >> 1) & 1;
+                if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag)) {
+                    abort_pipeline(abort_flag, prm.err);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN_MAX);
+                for (int kb = 0; kb < P.k_blocks; ++kb) {
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag)) {
+                        ok = false;
+                        abort_pipeline(abort_flag, prm.err);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_base + stage * STAGE_BYTES;
+                    const uint64_t adesc = sdesc_kmajor_sw128(sa);
+                    const uint64_t bdesc = sdesc_kmajor_sw128(sa + A_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 32; ++k) {
+                        // advance the start address by 32 bytes (K = 32 codes)
+                        mma_f8f6f4(d_tmem, adesc + 2u * k, bdesc + 2u * k, P.idesc,
+                                   (kb | k) != 0 ? 1u : 0u);
+                    }
+                    mma_commit(empty_bar(stage));
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (ok)
+                    mma_commit(tfull_bar(acc));
+            }
+            // every MMA this thread issued has finished before TMEM is freed
+            const volatile int never = 0;
+            mma_commit(drain_bar);
+            mbar_wait(drain_bar, 0u, &never);
+        }
+    } else {
+        // ---------------------------------------------------- epilogue
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        int local = 0;
+        for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++local) {
+            const TileCoord tc = tile_coord(prm, tile);
+            const Problem& P = prm.prob[tc.p];
+            const int acc = local & 1;
+            const uint32_t acc_phase = (local >> 1) & 1;
+            // the whole warp takes the same branch (tcgen05.ld is warp-collective)
+            const bool got = mbar_wait(tfull_bar(acc), acc_phase, abort_flag);
+            if (!__all_sync(0xFFFFFFFFu, got)) {
+                abort_pipeline(abort_flag, prm.err);
+                break;
+            }
+            tc_fence_after();
+            const int i = tc.m_blk * BM + row;
+            const bool row_ok = i < P.rows_p;
+            const float fi = row_ok ? __fmul_rn(P.alpha, __ldg(P.sp + (P.sp_mode ? i : 0))) : 0.0f;
+            const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                   static_cast<uint32_t>(acc * BN_MAX);
+            const int jbase = tc.n_blk * P.bn;
+            for (int c0 = 0; c0 < P.bn; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld_32x32b_x16(taddr + c0, r);
+                tmem_ld_wait();
+                store_chunk16(P, i, row_ok, fi, jbase + c0, r);
+            }
+            tc_fence_before();
+            mbar_arrive(tempty_bar(acc));
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D map over a byte matrix [rows, cols] with row stride ld bytes; box
+// {128 bytes, box_rows}, 128-byte swizzle, out-of-range elements read as 0.
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+              int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return false;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int pick_bn(int64_t rows_q)
+{
+    if (rows_q <= 16) return 16;
+    if (rows_q <= 32) return 32;
+    if (rows_q <= 64) return 64;
+    if (rows_q <= 128) return 128;
+    return 256;
+}
+
+// One GEMM in the kernel's (P, Q) roles.
+struct Job {
+    int64_t rows_p, rows_q, K;
+    const uint8_t* P;
+    int64_t ldp;
+    const uint8_t* Q;
+    int64_t ldq;
+    const float* sp;
+    int sp_mode;
+    const float* sq;
+    int sq_mode;
+    float alpha;
+    void* C;
+    int64_t ldc;
+    int out_bf16;
+    int trans_out;
+};
+
+int validate_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
+                   const uint8_t* B, int64_t ldb, const float* a_scale, int a_mode,
+                   const float* b_scale, int b_mode, void* C, int64_t ldc, int out_dtype)
+{
+    if (M < 0 || N < 0 || K < 0)
+        return FP8_ERR_INVALID;
+    if ((a_mode != 0 && a_mode != 1) || (b_mode != 0 && b_mode != 1) ||
+        (out_dtype != 0 && out_dtype != 1))
+        return FP8_ERR_INVALID;
+    if (M == 0 || N == 0)
+        return FP8_OK;
+    if (!C || !a_scale || !b_scale)
+        return FP8_ERR_INVALID;
+    if (K > 0 && (!A || !B))
+        return FP8_ERR_INVALID;
+    if (K > 0 && (lda < K || ldb < K))
+        return FP8_ERR_SHAPE;
+    if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
+        return FP8_ERR_SHAPE;
+    if (K > 0 && (!aligned16(A) || !aligned16(B) || lda % 16 || ldb % 16))
+        return FP8_ERR_ALIGN;
+    return FP8_OK;
+}
+
+// Fill one problem entry.  Returns FP8_OK or an error.
+int fill_problem(Problem& pr, const Job& j, int bn)
+{
+    memset(&pr, 0, sizeof(pr));
+    if (!make_map(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BM) ||
+        !make_map(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, bn))
+        return FP8_ERR_CUDA;
+    pr.sp = j.sp;
+    pr.sq = j.sq;
+    pr.C = j.C;
+    pr.ldc = j.ldc;
+    pr.rows_p = static_cast<int>(j.rows_p);
+    pr.rows_q = static_cast<int>(j.rows_q);
+    pr.K = static_cast<int>(j.K);
+    pr.sp_mode = j.sp_mode;
+    pr.sq_mode = j.sq_mode;
+    pr.alpha = j.alpha;
+    pr.out_bf16 = j.out_bf16;
+    pr.trans_out = j.trans_out;
+    const int esz = j.out_bf16 ? 2 : 4;
+    pr.vec_store = aligned16(j.C) && ((j.ldc * esz) % 16 == 0);
+    pr.bn = bn;
+    pr.m_blocks = static_cast<int>((j.rows_p + BM - 1) / BM);
+    pr.n_blocks = static_cast<int>((j.rows_q + bn - 1) / bn);
+    pr.k_blocks = static_cast<int>((j.K + BK - 1) / BK);
+    pr.idesc = idesc_e4m3_f32(BM, bn);
+    return FP8_OK;
+}
+
+// Zero C for K == 0 (the sum over an empty K range).
+int write_zeros(void* C, int64_t ldc, int64_t rows, int64_t cols, int out_bf16, cudaStream_t st)
+{
+    const size_t esz = out_bf16 ? 2 : 4;
+    GB_CUDA_OK(cudaMemset2DAsync(C, ldc * esz, 0, cols * esz, rows, st));
+    return FP8_OK;
+}
+
+template <int MAXP>
+int launch(Params<MAXP>& prm, cudaStream_t st)
+{
+    static std::once_flag attr_once[64];
+    int dev = 0;
+    GB_CUDA_OK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64)
+        return FP8_ERR_UNSUPPORTED;
+    cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once[dev], [&] {
+        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    });
+    GB_CUDA_OK(attr_err);
+    int tiles = 0;
+    for (int p = 0; p < prm.num_problems; ++p) {
+        prm.prob[p].tile_start = tiles;
+        tiles += prm.prob[p].m_blocks * prm.prob[p].n_blocks;
+    }
+    prm.total_tiles = tiles;
+    if (tiles == 0)
+        return FP8_OK;
+    prm.err = device_error_word();
+    const int grid = std::min(tiles, sm_count());
+    gemm_fp8_kernel<MAXP><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(prm);
+    GB_CUDA_OK(cudaGetLastError());
+    return FP8_OK;
+}
+
+// Map a user-level GEMM (A [M,K], B [N,K], C [M,N]) onto (P, Q) roles.  Small
+// M goes to the MMA N side (Q = A, P = B) and the output is written
+// transposed back into C.
+Job make_job(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B,
+             int64_t ldb, const float* a_scale, int a_mode, const float* b_scale, int b_mode,
+             float alpha, void* C, int64_t ldc, int out_dtype, int out_transposed, bool allow_swap)
+{
+    Job j{};
+    const bool swap = allow_swap && M <= 128 && N > M;
+    j.K = K;
+    j.alpha = alpha;
+    j.C = C;
+    j.ldc = ldc;
+    j.out_bf16 = out_dtype;
+    if (!swap) {
+        j.rows_p = M, j.P = A, j.ldp = lda, j.sp = a_scale, j.sp_mode = a_mode;
+        j.rows_q = N, j.Q = B, j.ldq = ldb, j.sq = b_scale, j.sq_mode = b_mode;
+        j.trans_out = out_transposed;
+    } else {
+        j.rows_p = N, j.P = B, j.ldp = ldb, j.sp = b_scale, j.sp_mode = b_mode;
+        j.rows_q = M, j.Q = A, j.ldq = lda, j.sq = a_scale, j.sq_mode = a_mode;
+        j.trans_out = !out_transposed;
+    }
+    return j;
+}
+
+}  // namespace
+}  // namespace gb300
+
+extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
+                              const uint8_t* B, int64_t ldb, const float* a_scale, int a_mode,
+                              const float* b_scale, int b_mode, float alpha, void* C, int64_t ldc,
+                              int out_dtype, fp8_stream_t stream)
+{
+    using namespace gb300;
+    int rc = validate_dense(M, N, K, A, lda, B, ldb, a_scale, a_mode, b_scale, b_mode, C, ldc,
+                            out_dtype);
+    if (rc != FP8_OK || M == 0 || N == 0)
+        return rc;
+    if (ldc < N)
+        return FP8_ERR_SHAPE;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (K == 0)
+        return write_zeros(C, ldc, M, N, out_dtype, st);
+    Job j = make_job(M, N, K, A, lda, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C, ldc,
+                     out_dtype, 0, true);
+    Params<1> prm;
+    memset(&prm, 0, sizeof(prm));
+    rc = fill_problem(prm.prob[0], j, pick_bn(j.rows_q));
+    if (rc != FP8_OK)
+        return rc;
+    prm.num_problems = 1;
+    return launch(prm, st);
+}
+
+extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t* a_vals,
+                                 const uint8_t* a_meta, const uint8_t* B, int64_t ldb,
+                                 const float* a_scale, int a_mode, const float* b_scale, int b_mode,
+                                 float alpha, void* C, int64_t ldc, int out_dtype,
+                                 int out_transposed, fp8_stream_t stream)
+{
+    (void)M, (void)N, (void)K, (void)a_vals, (void)a_meta, (void)B, (void)ldb, (void)a_scale;
+    (void)a_mode, (void)b_scale, (void)b_mode, (void)alpha, (void)C, (void)ldc, (void)out_dtype;
+    (void)out_transposed, (void)stream;
+    return FP8_ERR_UNSUPPORTED;
+}
+
+extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_problems,
+                                fp8_stream_t stream)
+{
+    using namespace gb300;
+    if (num_problems < 0 || (num_problems > 0 && !problems))
+        return FP8_ERR_INVALID;
+    if (num_problems > FP8_GROUPED_MAX_PROBLEMS)
+        return FP8_ERR_SHAPE;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
+    memset(&prm, 0, sizeof(prm));
+    int n = 0;
+    for (int i = 0; i < num_problems; ++i) {
+        const fp8_gemm_problem& g = problems[i];
+        if (g.A_meta != nullptr)
+            return FP8_ERR_UNSUPPORTED;
+        int rc = validate_dense(g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.a_scale, g.a_mode,
+                                g.b_scale, g.b_mode, g.C, g.ldc, g.out_dtype);
+        if (rc != FP8_OK)
+            return rc;
+        if (g.M == 0 || g.N == 0)
+            continue;
+        if (g.ldc < (g.out_transposed ? g.M : g.N) || (g.out_transposed != 0 && g.out_transposed != 1))
+            return FP8_ERR_SHAPE;
+    }
+    for (int i = 0; i < num_problems; ++i) {
+        const fp8_gemm_problem& g = problems[i];
+        if (g.M == 0 || g.N == 0)
+            continue;
+        if (g.K == 0) {
+            int rc = g.out_transposed ? write_zeros(g.C, g.ldc, g.N, g.M, g.out_dtype, st)
+                                      : write_zeros(g.C, g.ldc, g.M, g.N, g.out_dtype, st);
+            if (rc != FP8_OK)
+                return rc;
+            continue;
+        }
+        Job j = make_job(g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.a_scale, g.a_mode, g.b_scale,
+                         g.b_mode, g.alpha, g.C, g.ldc, g.out_dtype, g.out_transposed, true);
+        int rc = fill_problem(prm.prob[n], j, pick_bn(j.rows_q));
+        if (rc != FP8_OK)
+            return rc;
+        ++n;
+    }
+    prm.num_problems = n;
+    if (n == 0)
+        return FP8_OK;
+    return launch(prm, st);
+}

@@ -1,0 +1,161 @@
+// 2:4 prune + compress (prune24_compress) and its inverse.
+//
+// One thread takes 32 input bytes (eight groups of four codes): two 16-byte
+// loads, a branch-free rank selection per group, one 16-byte store of the
+// kept codes and one 4-byte store of the eight metadata nibbles.  Rows whose
+// length or alignment does not allow the vector path fall back to one group
+// per iteration.  Bandwidth-bound: 1 byte read, 0.625 bytes written per
+// element; no allocation, one launch.
+#include "common.cuh"
+
+namespace gb300 {
+namespace {
+
+constexpr int kThreads = 256;
+
+// One group of four codes (byte i of w = element i).  Element j outranks
+// element i when key_j > key_i, or key_j == key_i and j < i (key = code &
+// 0x7F).  The two elements outranked by fewer than two others are kept.
+// Returns the two kept codes in the low 16 bits (lower index first) and the
+// nibble i0 | i1 << 2 in bits 16..19.
+__device__ __forceinline__ uint32_t select_group(uint32_t w)
+{
+    const uint32_t k0 = w & 0x7Fu, k1 = (w >> 8) & 0x7Fu, k2 = (w >> 16) & 0x7Fu,
+                   k3 = (w >> 24) & 0x7Fu;
+    const uint32_t r0 = (k1 > k0) + (k2 > k0) + (k3 > k0);
+    const uint32_t r1 = (k0 >= k1) + (k2 > k1) + (k3 > k1);
+    const uint32_t r2 = (k0 >= k2) + (k1 >= k2) + (k3 > k2);
+    const uint32_t r3 = (k0 >= k3) + (k1 >= k3) + (k2 >= k3);
+    const uint32_t keep = (r0 < 2u) | ((r1 < 2u) << 1) | ((r2 < 2u) << 2) | ((r3 < 2u) << 3);
+    const uint32_t i0 = __ffs(keep) - 1;
+    const uint32_t i1 = 31 - __clz(keep);
+    const uint32_t vals = __byte_perm(w, 0u, i0 | (i1 << 4)) & 0xFFFFu;
+    return vals | ((i0 | (i1 << 2)) << 16);
+}
+
+// vec: K % 32 == 0, a 16-aligned, lda % 16 == 0, outputs 16-aligned.
+__global__ void __launch_bounds__(kThreads) prune24_kernel(const uint8_t* __restrict__ a,
+                                                           int64_t M, int64_t K, int64_t lda,
+                                                           uint8_t* __restrict__ vals,
+                                                           uint8_t* __restrict__ meta, int vec)
+{
+    const int64_t ldv = K / 2, ldm = (K + 7) / 8;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    if (vec) {
+        const int64_t chunks = K / 32;                  // 32 codes per thread
+        for (int64_t i = tid; i < M * chunks; i += stride) {
+            const int64_t r = i / chunks, c = i - r * chunks;
+            const uint4* src = reinterpret_cast<const uint4*>(a + r * lda + c * 32);
+            const uint4 x0 = __ldg(src), x1 = __ldg(src + 1);
+            const uint32_t w[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            uint32_t v[4] = {0, 0, 0, 0};
+            uint32_t nib = 0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const uint32_t s = select_group(w[g]);
+                v[g / 2] |= (s & 0xFFFFu) << (16 * (g % 2));
+                nib |= (s >> 16) << (4 * g);
+            }
+            *reinterpret_cast<uint4*>(vals + r * ldv + c * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<uint32_t*>(meta + r * ldm + c * 4) = nib;
+        }
+        return;
+    }
+    // scalar path: one metadata byte (two groups, or one at an odd tail) per
+    // iteration so that no two threads write the same byte
+    for (int64_t i = tid; i < M * ldm; i += stride) {
+        const int64_t r = i / ldm, b = i - r * ldm;
+        uint8_t out = 0;
+        for (int h = 0; h < 2; ++h) {
+            const int64_t g = 2 * b + h;
+            if (4 * g >= K)
+                break;
+            const uint8_t* p = a + r * lda + 4 * g;
+            const uint32_t w = p[0] | (p[1] << 8) | (p[2] << 16) | (static_cast<uint32_t>(p[3]) << 24);
+            const uint32_t s = select_group(w);
+            vals[r * ldv + 2 * g] = static_cast<uint8_t>(s & 0xFFu);
+            vals[r * ldv + 2 * g + 1] = static_cast<uint8_t>((s >> 8) & 0xFFu);
+            out |= static_cast<uint8_t>(((s >> 16) & 0xFu) << (4 * h));
+        }
+        meta[r * ldm + b] = out;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) decompress24_kernel(const uint8_t* __restrict__ vals,
+                                                                const uint8_t* __restrict__ meta,
+                                                                int64_t M, int64_t K,
+                                                                uint8_t* __restrict__ out)
+{
+    const int64_t ldv = K / 2, ldm = (K + 7) / 8, groups = K / 4;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < M * groups;
+         i += stride) {
+        const int64_t r = i / groups, g = i - r * groups;
+        const uint32_t nib = (meta[r * ldm + g / 2] >> (4 * (g % 2))) & 0xFu;
+        const uint32_t i0 = nib & 3u, i1 = nib >> 2;
+        uint32_t w = 0;
+        w |= static_cast<uint32_t>(vals[r * ldv + 2 * g]) << (8 * i0);
+        w |= static_cast<uint32_t>(vals[r * ldv + 2 * g + 1]) << (8 * i1);
+        uint8_t* o = out + r * K + 4 * g;
+        o[0] = w & 0xFFu;
+        o[1] = (w >> 8) & 0xFFu;
+        o[2] = (w >> 16) & 0xFFu;
+        o[3] = (w >> 24) & 0xFFu;
+    }
+}
+
+int grid_for(int64_t items)
+{
+    const int64_t blocks = (items + kThreads - 1) / kThreads;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
+    return static_cast<int>(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+}
+
+}  // namespace
+}  // namespace gb300
+
+extern "C" int prune24_compress(const uint8_t* a, int64_t M, int64_t K, int64_t lda,
+                                uint8_t* a_vals, uint8_t* a_meta, fp8_stream_t stream)
+{
+    using namespace gb300;
+    if (M < 0 || K < 0)
+        return FP8_ERR_INVALID;
+    if (K % 4 != 0)
+        return FP8_ERR_SHAPE;
+    if (M == 0 || K == 0)
+        return FP8_OK;
+    if (!a || !a_vals || !a_meta)
+        return FP8_ERR_INVALID;
+    if (lda < K)
+        return FP8_ERR_SHAPE;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    const int vec = (K % 32 == 0) && aligned16(a) && (lda % 16 == 0) && aligned16(a_vals) &&
+                    aligned16(a_meta);
+    const int64_t items = vec ? M * (K / 32) : M * ((K + 7) / 8);
+    prune24_kernel<<<grid_for(items), kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        a, M, K, lda, a_vals, a_meta, vec);
+    GB_CUDA_OK(cudaGetLastError());
+    return FP8_OK;
+}
+
+extern "C" int prune24_decompress(const uint8_t* a_vals, const uint8_t* a_meta, int64_t M,
+                                  int64_t K, uint8_t* out, fp8_stream_t stream)
+{
+    using namespace gb300;
+    if (M < 0 || K < 0)
+        return FP8_ERR_INVALID;
+    if (K % 4 != 0)
+        return FP8_ERR_SHAPE;
+    if (M == 0 || K == 0)
+        return FP8_OK;
+    if (!a_vals || !a_meta || !out)
+        return FP8_ERR_INVALID;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    decompress24_kernel<<<grid_for(M * (K / 4)), kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        a_vals, a_meta, M, K, out);
+    GB_CUDA_OK(cudaGetLastError());
+    return FP8_OK;
+}

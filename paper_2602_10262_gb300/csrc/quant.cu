@@ -1,0 +1,219 @@
+// Scale selection + E4M3 quantisation (fp8_quantize_e4m3).
+//
+// Per row (scale_mode 1): one CTA per row.  Pass 1 takes amax of the row with
+// 16-byte loads and a warp/CTA max reduction on the fp32 bit patterns of |x|
+// (monotone for non-negative floats; Inf and NaN compare above every finite
+// value, which is how non-finite input is detected).  Pass 2 re-reads the
+// row (an L2 hit: the rows in flight are far smaller than L2) and writes the
+// codes.  HBM traffic: 4 bytes read + 1 byte written per element.
+//
+// Per tensor (scale_mode 0): a grid-stride amax kernel folds into the
+// dequant_scale[0] slot with atomicMax, an encode kernel reads it, and a
+// one-thread kernel turns the slot into d = amax / 448.
+//
+// The scale is s = 448 / amax with an IEEE-rounded division (__fdiv_rn) and
+// each code is cvt.rn.satfinite.e4m3 of the IEEE product x * s (__fmul_rn).
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+
+namespace gb300 {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr uint32_t kInfBits = 0x7F800000u;
+
+__device__ __forceinline__ uint32_t abs_bits(float v)
+{
+    return __float_as_uint(v) & 0x7FFFFFFFu;
+}
+
+// Two fp32 values -> two E4M3 codes (a in the low byte).
+__device__ __forceinline__ uint32_t enc2(float a, float b)
+{
+    return static_cast<uint32_t>(
+        __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3));
+}
+
+__device__ __forceinline__ uint32_t enc4(float4 v, float s)
+{
+    return enc2(__fmul_rn(v.x, s), __fmul_rn(v.y, s)) |
+           (enc2(__fmul_rn(v.z, s), __fmul_rn(v.w, s)) << 16);
+}
+
+__device__ __forceinline__ uint32_t block_max_u32(uint32_t v, uint32_t* red)
+{
+    v = __reduce_max_sync(0xFFFFFFFFu, v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (blockDim.x >> 5) ? red[lane] : 0u;
+        w = __reduce_max_sync(0xFFFFFFFFu, w);
+        if (lane == 0)
+            red[0] = w;
+    }
+    __syncthreads();
+    uint32_t r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// scale and dequant factor from the amax bit pattern
+__device__ __forceinline__ void scale_from_amax(uint32_t amax_bits, float& s, float& d)
+{
+    const float amax = __uint_as_float(amax_bits);
+    if (amax_bits == 0u) {
+        s = 1.0f;
+        d = 1.0f;
+    } else {
+        s = __fdiv_rn(448.0f, amax);
+        d = __fdiv_rn(amax, 448.0f);
+    }
+}
+
+// vec: x rows and q rows allow 16-byte loads / 4-byte stores (x 16-aligned,
+// ldx % 4 == 0, q 4-aligned, ldq % 4 == 0).
+__global__ void __launch_bounds__(kThreads) quant_row_kernel(const float* __restrict__ x,
+                                                             int64_t rows, int64_t cols,
+                                                             int64_t ldx, uint8_t* __restrict__ q,
+                                                             int64_t ldq, float* __restrict__ d,
+                                                             int vec, int* err)
+{
+    __shared__ uint32_t red[kThreads / 32];
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float* xr = x + r * ldx;
+        uint8_t* qr = q + r * ldq;
+        const int64_t nvec = vec ? cols / 4 : 0;
+        uint32_t m = 0;
+        for (int64_t i = threadIdx.x; i < nvec; i += kThreads) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(xr) + i);
+            m = max(m, max(max(abs_bits(v.x), abs_bits(v.y)), max(abs_bits(v.z), abs_bits(v.w))));
+        }
+        for (int64_t c = nvec * 4 + threadIdx.x; c < cols; c += kThreads)
+            m = max(m, abs_bits(xr[c]));
+        m = block_max_u32(m, red);
+        if (m >= kInfBits && threadIdx.x == 0)
+            report_device_error(err, FP8_ERR_NONFINITE);
+        float s, dq;
+        scale_from_amax(m, s, dq);
+        if (threadIdx.x == 0)
+            d[r] = dq;
+        for (int64_t i = threadIdx.x; i < nvec; i += kThreads) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(xr) + i);
+            reinterpret_cast<uint32_t*>(qr)[i] = enc4(v, s);
+        }
+        for (int64_t c = nvec * 4 + threadIdx.x; c < cols; c += kThreads)
+            qr[c] = static_cast<uint8_t>(enc2(__fmul_rn(xr[c], s), 0.0f) & 0xFFu);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) quant_amax_kernel(const float* __restrict__ x,
+                                                              int64_t rows, int64_t cols,
+                                                              int64_t ldx, int vec,
+                                                              uint32_t* __restrict__ slot)
+{
+    __shared__ uint32_t red[kThreads / 32];
+    uint32_t m = 0;
+    const int64_t per_row = vec ? cols / 4 : 0;
+    const int64_t total_vec = per_row * rows;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < total_vec;
+         i += stride) {
+        const int64_t r = i / per_row, c4 = i - r * per_row;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(x + r * ldx) + c4);
+        m = max(m, max(max(abs_bits(v.x), abs_bits(v.y)), max(abs_bits(v.z), abs_bits(v.w))));
+    }
+    const int64_t tail = cols - per_row * 4;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < tail * rows;
+         i += stride) {
+        const int64_t r = i / tail, c = per_row * 4 + (i - r * tail);
+        m = max(m, abs_bits(x[r * ldx + c]));
+    }
+    m = block_max_u32(m, red);
+    if (threadIdx.x == 0 && m != 0u)
+        atomicMax(slot, m);
+}
+
+__global__ void __launch_bounds__(kThreads) quant_encode_kernel(const float* __restrict__ x,
+                                                                int64_t rows, int64_t cols,
+                                                                int64_t ldx, uint8_t* __restrict__ q,
+                                                                int64_t ldq, int vec,
+                                                                const uint32_t* __restrict__ slot)
+{
+    float s, dq;
+    scale_from_amax(*slot, s, dq);
+    const int64_t per_row = vec ? cols / 4 : 0;
+    const int64_t total_vec = per_row * rows;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < total_vec;
+         i += stride) {
+        const int64_t r = i / per_row, c4 = i - r * per_row;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(x + r * ldx) + c4);
+        reinterpret_cast<uint32_t*>(q + r * ldq)[c4] = enc4(v, s);
+    }
+    const int64_t tail = cols - per_row * 4;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < tail * rows;
+         i += stride) {
+        const int64_t r = i / tail, c = per_row * 4 + (i - r * tail);
+        q[r * ldq + c] = static_cast<uint8_t>(enc2(__fmul_rn(x[r * ldx + c], s), 0.0f) & 0xFFu);
+    }
+}
+
+__global__ void quant_finalize_kernel(uint32_t* slot, int* err)
+{
+    const uint32_t m = *slot;
+    if (m >= kInfBits)
+        report_device_error(err, FP8_ERR_NONFINITE);
+    float s, dq;
+    scale_from_amax(m, s, dq);
+    *reinterpret_cast<float*>(slot) = dq;
+}
+
+}  // namespace
+}  // namespace gb300
+
+extern "C" int fp8_quantize_e4m3(const float* x, int64_t rows, int64_t cols, int64_t ldx,
+                                 int scale_mode, uint8_t* q, int64_t ldq, float* dequant_scale,
+                                 fp8_stream_t stream)
+{
+    using namespace gb300;
+    if (rows < 0 || cols < 0 || (scale_mode != 0 && scale_mode != 1))
+        return FP8_ERR_INVALID;
+    if (rows == 0 || cols == 0)
+        return FP8_OK;
+    if (!x || !q || !dequant_scale)
+        return FP8_ERR_INVALID;
+    if (ldx < cols || ldq < cols)
+        return FP8_ERR_SHAPE;
+    if ((reinterpret_cast<uintptr_t>(x) & 3u) || (reinterpret_cast<uintptr_t>(dequant_scale) & 3u))
+        return FP8_ERR_ALIGN;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    int* err = device_error_word();
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int vec = aligned16(x) && (ldx % 4 == 0) &&
+                    (reinterpret_cast<uintptr_t>(q) % 4 == 0) && (ldq % 4 == 0);
+    const int sms = sm_count();
+    if (scale_mode == 1) {
+        const int64_t grid = rows < 65535LL * 8 ? rows : 65535LL * 8;
+        quant_row_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(
+            x, rows, cols, ldx, q, ldq, dequant_scale, vec, err);
+        GB_CUDA_OK(cudaGetLastError());
+        return FP8_OK;
+    }
+    uint32_t* slot = reinterpret_cast<uint32_t*>(dequant_scale);
+    GB_CUDA_OK(cudaMemsetAsync(slot, 0, sizeof(uint32_t), st));
+    const int64_t work = (rows * cols + 4 * kThreads - 1) / (4 * kThreads);
+    const int64_t grid = work < static_cast<int64_t>(sms) * 8 ? (work > 0 ? work : 1) : sms * 8;
+    quant_amax_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(x, rows, cols, ldx, vec,
+                                                                        slot);
+    GB_CUDA_OK(cudaGetLastError());
+    quant_encode_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(x, rows, cols, ldx, q,
+                                                                          ldq, vec, slot);
+    GB_CUDA_OK(cudaGetLastError());
+    quant_finalize_kernel<<<1, 1, 0, st>>>(slot, err);
+    GB_CUDA_OK(cudaGetLastError());
+    return FP8_OK;
+}

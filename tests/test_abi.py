@@ -1,0 +1,72 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every function that include/gb300fp8.h declares, and rejects bad arguments
+on the host before touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def _declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            if not m.group(0).lstrip().startswith(("typedef", "#")):
+                names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_10262_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_path():
+    names = _declared_functions()
+    for n in ("fp8_quantize_e4m3", "prune24_compress", "gemm_fp8_dense", "gemm_fp8_sparse24",
+              "gemm_fp8_grouped", "fp8_last_device_error", "fp8_status_string"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    assert lib.fp8_status_string(0) == b"ok"
+    assert lib.fp8_status_string(-7) == b"device pipeline wait timed out"
+    assert lib.fp8_status_string(12345) == b"unknown status"
+
+
+def test_host_validation_without_gpu(lib):
+    P = ctypes.c_void_p
+    # negative sizes, bad modes and bad K are rejected before any CUDA call
+    assert lib.gemm_fp8_dense(-1, 4, 4, None, 16, None, 16, None, 0, None, 0, 1.0, None, 4, 0, None) == -1
+    assert lib.gemm_fp8_dense(4, 4, 4, None, 16, None, 16, None, 2, None, 0, 1.0, None, 4, 0, None) == -1
+    assert lib.gemm_fp8_dense(4, 4, 4, P(16), 16, P(16), 16, P(16), 0, P(16), 0, 1.0, P(16), 4, 5, None) == -1
+    assert lib.gemm_fp8_dense(4, 4, 32, P(16), 16, P(16), 32, P(16), 0, P(16), 0, 1.0, P(16), 4, 0, None) == -2
+    assert lib.gemm_fp8_dense(4, 4, 32, P(16), 40, P(16), 48, P(16), 0, P(16), 0, 1.0, P(16), 4, 0, None) == -3
+    assert lib.gemm_fp8_dense(4, 4, 32, P(8), 32, P(16), 32, P(16), 0, P(16), 0, 1.0, P(16), 4, 0, None) == -3
+    assert lib.prune24_compress(P(16), 4, 6, 16, P(16), P(16), None) == -2
+    assert lib.fp8_quantize_e4m3(P(16), 4, 4, 4, 3, P(16), 4, P(16), None) == -1
+    assert lib.fp8_quantize_e4m3(P(16), 4, 8, 4, 0, P(16), 8, P(16), None) == -2
+    # empty problems are a no-op
+    assert lib.gemm_fp8_dense(0, 4, 4, None, 16, None, 16, None, 0, None, 0, 1.0, None, 4, 0, None) == 0
+    assert lib.fp8_quantize_e4m3(None, 0, 4, 4, 0, None, 4, None, None) == 0
+
+
+def test_grouped_rejects_too_many(lib):
+    from paper_2602_10262_gb300 import _lib
+    arr = (_lib.FP8Problem * 33)()
+    assert lib.gemm_fp8_grouped(arr, 33, None) == -2
+    assert lib.gemm_fp8_grouped(None, 1, None) == -1
+    assert lib.gemm_fp8_grouped(None, 0, None) in (0, -8)

@@ -1,0 +1,158 @@
+"""GPU parity: gemm_fp8_dense (and the grouped launch) against the FP64 oracle.
+
+Exact cases (small-integer codes: every partial sum is an integer far below
+2^24) must match bit for bit in FP32 output; N(0,1) cases are checked with
+the tolerances in tests/parity.py; full-size shapes are checked on seeded
+sampled entries plus two full rows and two full columns.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import paper_2602_10262_gb300 as gb
+    gb.library()
+    return gb
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _ones(n=1):
+    return torch.ones(n, dtype=torch.float32, device="cuda")
+
+
+def _gemm(gb, A, B, dA, a_mode, dB, b_mode, alpha, out_dtype):
+    C = gb.gemm_fp8_dense(_cuda(A), _cuda(B), _cuda(dA), a_mode, _cuda(dB), b_mode, alpha,
+                          out_dtype)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    return C.float().cpu().numpy()
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 256), (128, 256, 128), (200, 72, 320),
+                                   (16, 512, 1024), (1, 1, 1), (300, 17, 4100)])
+def test_small_integers_bit_exact(gb, orc, M, N, K):
+    A = workloads.small_int_codes((M, K), seed=M)
+    B = workloads.small_int_codes((N, K), seed=N + 1)
+    one = np.ones(1, np.float32)
+    C = _gemm(gb, A, B, one, 0, one, 0, 1.0, gb.OUT_F32)
+    ref = orc.gemm(A, B, one, 0, one, 0)
+    assert np.array_equal(C.astype(np.float64), ref)
+
+
+def _quantized(M, N, K, a_mode, b_mode, orc, seed=0):
+    x = workloads.randn_f32((M, K), seed=workloads.SEED_A + seed)
+    w = workloads.randn_f32((N, K), seed=workloads.SEED_B + seed)
+    A, dA = orc.quantize(x, a_mode)
+    B, dB = orc.quantize(w, b_mode)
+    return A, dA, B, dB
+
+
+def test_dense_256_fp32_per_tensor(gb, orc):
+    """The 256^3 single-call case: per-tensor scales, FP32 output."""
+    A, dA, B, dB = _quantized(256, 256, 256, 0, 0, orc)
+    C = _gemm(gb, A, B, dA, 0, dB, 0, 1.0, gb.OUT_F32)
+    ref = orc.gemm(A, B, dA, 0, dB, 0)
+    parity.check_fp32(C, ref)
+
+
+@pytest.mark.parametrize("M,N,K", [(1024, 1024, 1024), (1000, 1500, 700), (16, 8192, 1024),
+                                   (64, 3000, 512), (128, 1024, 2048), (129, 333, 256)])
+def test_dense_bf16_per_row(gb, orc, M, N, K):
+    A, dA, B, dB = _quantized(M, N, K, 1, 1, orc, seed=M)
+    C = _gemm(gb, A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16)
+    ref = orc.gemm(A, B, dA, 1, dB, 1)
+    S = orc.gemm(parity.abs_codes(A), parity.abs_codes(B), dA, 1, dB, 1)
+    parity.check_bf16(C, ref, S, K)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 256), (500, 300, 1000)])
+def test_dense_fp32_per_row_alpha(gb, orc, M, N, K):
+    A, dA, B, dB = _quantized(M, N, K, 1, 1, orc, seed=3)
+    C = _gemm(gb, A, B, dA, 1, dB, 1, -0.625, gb.OUT_F32)
+    parity.check_fp32(C, orc.gemm(A, B, dA, 1, dB, 1, -0.625))
+
+
+def _sampled_check(gb, orc, M, N, K, out_dtype, seed=0):
+    A, dA, B, dB = _quantized(M, N, K, 1, 1, orc, seed=seed)
+    C = _gemm(gb, A, B, dA, 1, dB, 1, 1.0, out_dtype)
+    ms, ns = workloads.sample_pairs(M, N, 4096, seed=99)
+    rows = np.array([0, M - 1])
+    cols = np.array([0, N - 1])
+    ms = np.concatenate([ms, np.repeat(rows, N), np.tile(np.arange(M), 2)])
+    ns = np.concatenate([ns, np.tile(np.arange(N), 2), np.repeat(cols, M)])
+    ref = orc.gemm_sampled(A, B, dA, 1, dB, 1, 1.0, ms, ns)
+    S = orc.gemm_sampled(parity.abs_codes(A), parity.abs_codes(B), dA, 1, dB, 1, 1.0, ms, ns)
+    got = C[ms, ns]
+    if out_dtype == gb.OUT_BF16:
+        parity.check_bf16(got, ref, S, K)
+    else:
+        parity.check_fp32(got, ref)
+
+
+@pytest.mark.parametrize("M,N,K", [(8192, 8192, 8192), (16, 8192, 8192), (128, 8192, 8192)])
+def test_full_size_sampled(gb, orc, M, N, K):
+    _sampled_check(gb, orc, M, N, K, gb.OUT_BF16)
+
+
+def test_identity(gb, orc):
+    K = 256
+    A = workloads.random_codes((300, K), seed=5)
+    one = torch.tensor([1.0]).to(torch.float8_e4m3fn).view(torch.uint8).item()
+    I = np.zeros((K, K), np.uint8)
+    I[np.arange(K), np.arange(K)] = one
+    s = np.ones(1, np.float32)
+    C = _gemm(gb, A, I, s, 0, s, 0, 1.0, gb.OUT_F32)
+    assert np.array_equal(C.astype(np.float64), orc.e4m3_decode(A))
+
+
+def test_row_permutation_bitwise(gb, orc):
+    A, dA, B, dB = _quantized(384, 256, 512, 1, 1, orc, seed=7)
+    C = _gemm(gb, A, B, dA, 1, dB, 1, 1.0, gb.OUT_F32)
+    # permute whole 128-row tiles so each row keeps its accumulation order
+    perm = np.concatenate([np.arange(256, 384), np.arange(0, 128), np.arange(128, 256)])
+    Cp = _gemm(gb, A[perm], B, dA[perm], 1, dB, 1, 1.0, gb.OUT_F32)
+    assert np.array_equal(Cp, C[perm])
+
+
+def test_k_zero_writes_zeros(gb):
+    C = torch.full((5, 7), 3.0, device="cuda")
+    gb.gemm_fp8_dense(torch.empty((5, 0), dtype=torch.uint8, device="cuda"),
+                      torch.empty((7, 0), dtype=torch.uint8, device="cuda"), _ones(), 0, _ones(),
+                      0, 1.0, gb.OUT_F32, C=C)
+    assert torch.count_nonzero(C).item() == 0
+
+
+def test_misaligned_ld_rejected(gb):
+    A = torch.zeros((4, 40), dtype=torch.uint8, device="cuda")[:, :36]
+    B = torch.zeros((4, 36), dtype=torch.uint8, device="cuda")
+    with pytest.raises(gb.Fp8Error) as e:
+        gb.gemm_fp8_dense(A, B, _ones(), 0, _ones(), 0)
+    assert e.value.status == -3
+
+
+def test_grouped_equals_single_bitwise(gb, orc):
+    shapes = [(512, 768, 1024), (16, 2048, 512), (300, 200, 256), (1024, 256, 4096)]
+    probs, outs, singles, keep = [], [], [], []
+    for i, (M, N, K) in enumerate(shapes):
+        A, dA, B, dB = _quantized(M, N, K, 1, 1, orc, seed=20 + i)
+        t = [_cuda(A), _cuda(B), _cuda(dA), _cuda(dB)]
+        C = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+        keep += t
+        outs.append(C)
+        probs.append(gb.make_problem(t[0], t[1], t[2], 1, t[3], 1, C, 1.0, gb.OUT_BF16))
+        singles.append(gb.gemm_fp8_dense(t[0], t[1], t[2], 1, t[3], 1, 1.0, gb.OUT_BF16))
+    gb.gemm_fp8_grouped(probs)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    for C, Cs in zip(outs, singles):
+        assert torch.equal(C, Cs)
