@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
         *abort_flag = 0;
         fence_mbar_init();
     }
+    __syncwarp();
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
         tmem_relinquish();
@@ -337,10 +338,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
         }
     }
 
+    // In warps 0 and 1 only lane 0 ran a role loop: reconverge every warp
+    // before the CTA-wide barrier (bar.sync is warp-aligned).
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
-        __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem_base, TMEM_COLS);
     }
