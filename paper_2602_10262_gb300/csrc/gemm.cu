@@ -213,47 +213,50 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // ------------------------------------------------ TMA producer
-        for (int p = 0; p < prm.num_problems; ++p) {
-            tma_prefetch_desc(&prm.prob[p].tmP);
-            tma_prefetch_desc(&prm.prob[p].tmQ);
-        }
-        int stage = 0;
-        uint32_t phase = 0;
-        uint32_t armed = 0;                 // bit s: slot s armed at least once
-        bool ok = true;
-        for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x) {
-            const TileCoord tc = tile_coord(prm, tile);
-            const Problem& P = prm.prob[tc.p];
-            const uint32_t bytes = A_BYTES + static_cast<uint32_t>(P.bn) * BK;
-            for (int kb = 0; kb < P.k_blocks; ++kb) {
-                if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
-                    ok = false;
-                    abort_pipeline(abort_flag, prm.err);
-                    break;
-                }
-                mbar_arrive_expect_tx(full_bar(stage), bytes);
-                const uint32_t sa = smem_base + stage * STAGE_BYTES;
-                tma_load_2d(sa, &P.tmP, full_bar(stage), kb * BK, tc.m_blk * BM);
-                tma_load_2d(sa + A_BYTES, &P.tmQ, full_bar(stage), kb * BK, tc.n_blk * P.bn);
-                armed |= 1u << stage;
-                if (++stage == STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
+    // Roles are chosen per warp; inside warps 0 and 1 only lane 0 works.
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------ TMA producer
+            for (int p = 0; p < prm.num_problems; ++p) {
+                tma_prefetch_desc(&prm.prob[p].tmP);
+                tma_prefetch_desc(&prm.prob[p].tmQ);
+            }
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t armed = 0;                 // bit s: slot s armed at least once
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x) {
+                const TileCoord tc = tile_coord(prm, tile);
+                const Problem& P = prm.prob[tc.p];
+                const uint32_t bytes = A_BYTES + static_cast<uint32_t>(P.bn) * BK;
+                for (int kb = 0; kb < P.k_blocks; ++kb) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
+                        ok = false;
+                        abort_pipeline(abort_flag, prm.err);
+                        break;
+                    }
+                    mbar_arrive_expect_tx(full_bar(stage), bytes);
+                    const uint32_t sa = smem_base + stage * STAGE_BYTES;
+                    tma_load_2d(sa, &P.tmP, full_bar(stage), kb * BK, tc.m_blk * BM);
+                    tma_load_2d(sa + A_BYTES, &P.tmQ, full_bar(stage), kb * BK, tc.n_blk * P.bn);
+                    armed |= 1u << stage;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
                 }
             }
-        }
-        if (!ok) {
-            // let the copies already in flight land before the CTA exits:
-            // the latest arming of slot s has parity `phase` if s < stage
-            // (armed in the current round), else `phase ^ 1`
-            const volatile int never = 0;
-            for (int s = 0; s < STAGES; ++s) {
-                if (!(armed >> s & 1u))
-                    continue;
-                const uint32_t last_parity = (s < stage) ? phase : (phase ^ 1u);
-                mbar_wait(full_bar(s), last_parity, &never);
+            if (!ok) {
+                // let the copies already in flight land before the CTA exits:
+                // the latest arming of slot s has parity `phase` if s < stage
+                // (armed in the current round), else `phase ^ 1`
+                const volatile int never = 0;
+                for (int s = 0; s < STAGES; ++s) {
+                    if (!(armed >> s & 1u))
+                        continue;
+                    const uint32_t last_parity = (s < stage) ? phase : (phase ^ 1u);
+                    mbar_wait(full_bar(s), last_parity, &never);
+                }
             }
         }
     } else if (warp == 1) {
