@@ -232,12 +232,12 @@ def config(size, ws):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=16384)
-    ap.add_argument("--cpu-rows", type=int, default=128)
-    ap.add_argument("--cpu-cols", type=int, default=1024)
+    ap.add_argument("--cpu-rows", type=int, default=512)
+    ap.add_argument("--cpu-cols", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -61,7 +61,7 @@ def _dev(t: torch.Tensor, name: str, dtype: torch.dtype, dims: int):
 
 
 def _ld(t: torch.Tensor) -> int:
-    return t.stride(0) if t.dim() == 2 and t.size(0) > 1 else t.size(-1)
+    return t.stride(0) if t.dim() == 2 else t.size(-1)
 
 
 def _p(t: Optional[torch.Tensor]):

@@ -42,11 +42,21 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;      // 48 KB
 constexpr int TMEM_COLS = 2 * BN_MAX;
 constexpr int NUM_THREADS = 192;
 constexpr int GROUP_M = 8;                          // raster: 8 M-blocks per band
+// 2:4-sparse tiles: per stage the kept A codes (128 rows x 64 bytes, 64-byte
+// swizzle) and the metadata (128 rows x 16 bytes) share the A region; the
+// metadata is copied into a ring of TMEM columns [240, 256) (4 columns per
+// stage), so sparse tiles use N <= 240 and leave those columns free.
+constexpr int SP_A_BYTES = BM * BK / 2;             // 8 KB
+constexpr int SP_META_BYTES = BM * BK / 8;          // 2 KB
+constexpr int META_COL0 = 240;
+constexpr int SPARSE_BN_MAX = 240;
+static_assert(META_COL0 + 4 * STAGES <= BN_MAX, "metadata ring must fit beside accumulator 0");
 constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers*/;
 
 struct Problem {
     CUtensorMap tmP;        // P [rows_p, K] codes, box {128, 128}
     CUtensorMap tmQ;        // Q [rows_q, K] codes, box {128, bn}
+    CUtensorMap tmE;        // sparse only: metadata [rows_p, K/8], box {16, 128}
     const float* sp;        // scale of P rows (mode sp_mode)
     const float* sq;        // scale of Q rows
     void* C;
@@ -58,6 +68,7 @@ struct Problem {
     int trans_out;          // 0: C[i * ldc + j]; 1: C[j * ldc + i]  (i: P row, j: Q row)
     int vec_store;          // 16-byte stores allowed in the non-transposed path
     int bn;
+    int sparse;             // P holds kept codes [rows_p, K/2] + metadata in tmE
     int m_blocks, n_blocks, k_blocks;
     int tile_start;
     uint32_t idesc;
@@ -220,6 +231,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
             for (int p = 0; p < prm.num_problems; ++p) {
                 tma_prefetch_desc(&prm.prob[p].tmP);
                 tma_prefetch_desc(&prm.prob[p].tmQ);
+                if (prm.prob[p].sparse)
+                    tma_prefetch_desc(&prm.prob[p].tmE);
             }
             int stage = 0;
             uint32_t phase = 0;
@@ -228,7 +241,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
             for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x) {
                 const TileCoord tc = tile_coord(prm, tile);
                 const Problem& P = prm.prob[tc.p];
-                const uint32_t bytes = A_BYTES + static_cast<uint32_t>(P.bn) * BK;
+                const uint32_t bytes = (P.sparse ? SP_A_BYTES + SP_META_BYTES : A_BYTES) +
+                                       static_cast<uint32_t>(P.bn) * BK;
                 for (int kb = 0; kb < P.k_blocks; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
                         ok = false;
@@ -237,7 +251,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
                     }
                     mbar_arrive_expect_tx(full_bar(stage), bytes);
                     const uint32_t sa = smem_base + stage * STAGE_BYTES;
-                    tma_load_2d(sa, &P.tmP, full_bar(stage), kb * BK, tc.m_blk * BM);
+                    if (P.sparse) {
+                        tma_load_2d(sa, &P.tmP, full_bar(stage), kb * (BK / 2), tc.m_blk * BM);
+                        tma_load_2d(sa + SP_A_BYTES, &P.tmE, full_bar(stage), kb * (BK / 8),
+                                    tc.m_blk * BM);
+                    } else {
+                        tma_load_2d(sa, &P.tmP, full_bar(stage), kb * BK, tc.m_blk * BM);
+                    }
                     tma_load_2d(sa + A_BYTES, &P.tmQ, full_bar(stage), kb * BK, tc.n_blk * P.bn);
                     armed |= 1u << stage;
                     if (++stage == STAGES) {
@@ -285,13 +305,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_base + stage * STAGE_BYTES;
-                    const uint64_t adesc = sdesc_kmajor_sw128(sa);
                     const uint64_t bdesc = sdesc_kmajor_sw128(sa + A_BYTES);
+                    if (P.sparse) {
+                        // metadata of this k-block -> TMEM slot of this stage
+                        // (tcgen05.cp and the MMAs below execute in issue order)
+                        const uint32_t meta = tmem_base + static_cast<uint32_t>(META_COL0 + 4 * stage);
+                        tmem_cp_128x128b(meta, sdesc_rows16_noswizzle(sa + SP_A_BYTES));
+                        const uint64_t adesc = sdesc_kmajor_sw64(sa);
 #pragma unroll
-                    for (int k = 0; k < BK / 32; ++k) {
-                        // advance the start address by 32 bytes (K = 32 codes)
-                        mma_f8f6f4(d_tmem, adesc + 2u * k, bdesc + 2u * k, P.idesc,
-                                   (kb | k) != 0 ? 1u : 0u);
+                        for (int k = 0; k < BK / 64; ++k) {
+                            // logical K = 64 per MMA: 32 kept A bytes, 64 B bytes,
+                            // 64 metadata bits (two TMEM columns)
+                            mma_sp_f8f6f4(d_tmem, adesc + 2u * k, bdesc + 4u * k, meta + 2u * k,
+                                          P.idesc, (kb | k) != 0 ? 1u : 0u);
+                        }
+                    } else {
+                        const uint64_t adesc = sdesc_kmajor_sw128(sa);
+#pragma unroll
+                        for (int k = 0; k < BK / 32; ++k) {
+                            // advance the start address by 32 bytes (K = 32 codes)
+                            mma_f8f6f4(d_tmem, adesc + 2u * k, bdesc + 2u * k, P.idesc,
+                                       (kb | k) != 0 ? 1u : 0u);
+                        }
                     }
                     mma_commit(empty_bar(stage));
                     if (++stage == STAGES) {
@@ -370,36 +405,39 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 // 2-D map over a byte matrix [rows, cols] with row stride ld bytes; box
-// {128 bytes, box_rows}, 128-byte swizzle, out-of-range elements read as 0.
+// {box_cols bytes, box_rows}; out-of-range elements read as 0.
 bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
-              int box_rows)
+              int box_cols, int box_rows, CUtensorMapSwizzle swizzle)
 {
     auto fn = encode_fn();
     if (!fn)
         return false;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld)};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides,
-                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-int pick_bn(int64_t rows_q)
+// N of the MMA tile for a problem whose N side has rows_q rows.
+int pick_bn(int64_t rows_q, int bn_max)
 {
-    if (rows_q <= 16) return 16;
-    if (rows_q <= 32) return 32;
-    if (rows_q <= 64) return 64;
-    if (rows_q <= 128) return 128;
-    return 256;
+    int bn = 256;
+    if (rows_q <= 16) bn = 16;
+    else if (rows_q <= 32) bn = 32;
+    else if (rows_q <= 64) bn = 64;
+    else if (rows_q <= 128) bn = 128;
+    return bn < bn_max ? bn : bn_max;
 }
 
 // One GEMM in the kernel's (P, Q) roles.
 struct Job {
     int64_t rows_p, rows_q, K;
-    const uint8_t* P;
+    const uint8_t* P;       // dense codes, or kept codes [rows_p, K/2] when E != nullptr
+    const uint8_t* E;       // 2:4 metadata [rows_p, K/8], or nullptr for dense
     int64_t ldp;
     const uint8_t* Q;
     int64_t ldq;
@@ -414,26 +452,42 @@ struct Job {
     int trans_out;
 };
 
-int validate_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
-                   const uint8_t* B, int64_t ldb, const float* a_scale, int a_mode,
-                   const float* b_scale, int b_mode, void* C, int64_t ldc, int out_dtype)
+// Argument checks shared by every entry point.  `sparse`: A is the kept-code
+// array [M, K/2] (contiguous) and A_meta the metadata [M, K/8] (contiguous).
+int validate(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* A_meta,
+             bool sparse, const uint8_t* B, int64_t ldb, const float* a_scale, int a_mode,
+             const float* b_scale, int b_mode, void* C, int64_t ldc, int out_dtype,
+             int out_transposed)
 {
     if (M < 0 || N < 0 || K < 0)
         return FP8_ERR_INVALID;
     if ((a_mode != 0 && a_mode != 1) || (b_mode != 0 && b_mode != 1) ||
-        (out_dtype != 0 && out_dtype != 1))
+        (out_dtype != 0 && out_dtype != 1) || (out_transposed != 0 && out_transposed != 1))
         return FP8_ERR_INVALID;
     if (M == 0 || N == 0)
         return FP8_OK;
     if (!C || !a_scale || !b_scale)
         return FP8_ERR_INVALID;
-    if (K > 0 && (!A || !B))
-        return FP8_ERR_INVALID;
-    if (K > 0 && (lda < K || ldb < K))
+    if (ldc < (out_transposed ? M : N))
         return FP8_ERR_SHAPE;
     if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
         return FP8_ERR_SHAPE;
-    if (K > 0 && (!aligned16(A) || !aligned16(B) || lda % 16 || ldb % 16))
+    if (K == 0)
+        return FP8_OK;
+    if (!A || !B || (sparse && !A_meta))
+        return FP8_ERR_INVALID;
+    if (sparse) {
+        if (K % BK != 0)
+            return FP8_ERR_SHAPE;
+        if (ldb < K)
+            return FP8_ERR_SHAPE;
+        if (!aligned16(A) || !aligned16(A_meta) || !aligned16(B) || ldb % 16)
+            return FP8_ERR_ALIGN;
+        return FP8_OK;
+    }
+    if (lda < K || ldb < K)
+        return FP8_ERR_SHAPE;
+    if (!aligned16(A) || !aligned16(B) || lda % 16 || ldb % 16)
         return FP8_ERR_ALIGN;
     return FP8_OK;
 }
@@ -442,8 +496,15 @@ int validate_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t ld
 int fill_problem(Problem& pr, const Job& j, int bn)
 {
     memset(&pr, 0, sizeof(pr));
-    if (!make_map(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BM) ||
-        !make_map(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, bn))
+    pr.sparse = j.E != nullptr;
+    if (pr.sparse) {
+        if (!make_map(&pr.tmP, j.P, j.rows_p, j.K / 2, j.K / 2, BK / 2, BM, CU_TENSOR_MAP_SWIZZLE_64B) ||
+            !make_map(&pr.tmE, j.E, j.rows_p, j.K / 8, j.K / 8, BK / 8, BM, CU_TENSOR_MAP_SWIZZLE_NONE))
+            return FP8_ERR_CUDA;
+    } else if (!make_map(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BK, BM, CU_TENSOR_MAP_SWIZZLE_128B)) {
+        return FP8_ERR_CUDA;
+    }
+    if (!make_map(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, CU_TENSOR_MAP_SWIZZLE_128B))
         return FP8_ERR_CUDA;
     pr.sp = j.sp;
     pr.sq = j.sq;
@@ -463,7 +524,7 @@ int fill_problem(Problem& pr, const Job& j, int bn)
     pr.m_blocks = static_cast<int>((j.rows_p + BM - 1) / BM);
     pr.n_blocks = static_cast<int>((j.rows_q + bn - 1) / bn);
     pr.k_blocks = static_cast<int>((j.K + BK - 1) / BK);
-    pr.idesc = idesc_e4m3_f32(BM, bn);
+    pr.idesc = idesc_e4m3_f32(BM, bn, pr.sparse != 0, 0);
     return FP8_OK;
 }
 
@@ -504,26 +565,28 @@ int launch(Params<MAXP>& prm, cudaStream_t st)
     return FP8_OK;
 }
 
-// Map a user-level GEMM (A [M,K], B [N,K], C [M,N]) onto (P, Q) roles.  Small
-// M goes to the MMA N side (Q = A, P = B) and the output is written
-// transposed back into C.
-Job make_job(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B,
-             int64_t ldb, const float* a_scale, int a_mode, const float* b_scale, int b_mode,
-             float alpha, void* C, int64_t ldc, int out_dtype, int out_transposed, bool allow_swap)
+// Map a user-level GEMM (A [M,K], B [N,K], C [M,N] or C^T) onto (P, Q)
+// roles.  A dense product with small M puts A on the MMA N side (Q = A,
+// P = B) and writes the output transposed back; a sparse A always stays on
+// the MMA M side (the tensor core takes sparsity on that operand only).
+Job make_job(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
+             const uint8_t* A_meta, const uint8_t* B, int64_t ldb, const float* a_scale, int a_mode,
+             const float* b_scale, int b_mode, float alpha, void* C, int64_t ldc, int out_dtype,
+             int out_transposed)
 {
     Job j{};
-    const bool swap = allow_swap && M <= 128 && N > M;
+    const bool swap = A_meta == nullptr && M <= 128 && N > M;
     j.K = K;
     j.alpha = alpha;
     j.C = C;
     j.ldc = ldc;
     j.out_bf16 = out_dtype;
     if (!swap) {
-        j.rows_p = M, j.P = A, j.ldp = lda, j.sp = a_scale, j.sp_mode = a_mode;
+        j.rows_p = M, j.P = A, j.E = A_meta, j.ldp = lda, j.sp = a_scale, j.sp_mode = a_mode;
         j.rows_q = N, j.Q = B, j.ldq = ldb, j.sq = b_scale, j.sq_mode = b_mode;
         j.trans_out = out_transposed;
     } else {
-        j.rows_p = N, j.P = B, j.ldp = ldb, j.sp = b_scale, j.sp_mode = b_mode;
+        j.rows_p = N, j.P = B, j.E = nullptr, j.ldp = ldb, j.sp = b_scale, j.sp_mode = b_mode;
         j.rows_q = M, j.Q = A, j.ldq = lda, j.sq = a_scale, j.sq_mode = a_mode;
         j.trans_out = !out_transposed;
     }
@@ -539,22 +602,20 @@ extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A,
                               int out_dtype, fp8_stream_t stream)
 {
     using namespace gb300;
-    int rc = validate_dense(M, N, K, A, lda, B, ldb, a_scale, a_mode, b_scale, b_mode, C, ldc,
-                            out_dtype);
+    int rc = validate(M, N, K, A, lda, nullptr, false, B, ldb, a_scale, a_mode, b_scale, b_mode, C,
+                      ldc, out_dtype, 0);
     if (rc != FP8_OK || M == 0 || N == 0)
         return rc;
-    if (ldc < N)
-        return FP8_ERR_SHAPE;
     if (!device_supported())
         return FP8_ERR_UNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (K == 0)
         return write_zeros(C, ldc, M, N, out_dtype, st);
-    Job j = make_job(M, N, K, A, lda, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C, ldc,
-                     out_dtype, 0, true);
+    Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
+                     ldc, out_dtype, 0);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
-    rc = fill_problem(prm.prob[0], j, pick_bn(j.rows_q));
+    rc = fill_problem(prm.prob[0], j, pick_bn(j.rows_q, BN_MAX));
     if (rc != FP8_OK)
         return rc;
     prm.num_problems = 1;
@@ -567,10 +628,26 @@ extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t*
                                  float alpha, void* C, int64_t ldc, int out_dtype,
                                  int out_transposed, fp8_stream_t stream)
 {
-    (void)M, (void)N, (void)K, (void)a_vals, (void)a_meta, (void)B, (void)ldb, (void)a_scale;
-    (void)a_mode, (void)b_scale, (void)b_mode, (void)alpha, (void)C, (void)ldc, (void)out_dtype;
-    (void)out_transposed, (void)stream;
-    return FP8_ERR_UNSUPPORTED;
+    using namespace gb300;
+    int rc = validate(M, N, K, a_vals, K / 2, a_meta, true, B, ldb, a_scale, a_mode, b_scale,
+                      b_mode, C, ldc, out_dtype, out_transposed);
+    if (rc != FP8_OK || M == 0 || N == 0)
+        return rc;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (K == 0)
+        return out_transposed ? write_zeros(C, ldc, N, M, out_dtype, st)
+                              : write_zeros(C, ldc, M, N, out_dtype, st);
+    Job j = make_job(M, N, K, a_vals, K / 2, a_meta, B, ldb, a_scale, a_mode, b_scale, b_mode,
+                     alpha, C, ldc, out_dtype, out_transposed);
+    Params<1> prm;
+    memset(&prm, 0, sizeof(prm));
+    rc = fill_problem(prm.prob[0], j, pick_bn(j.rows_q, SPARSE_BN_MAX));
+    if (rc != FP8_OK)
+        return rc;
+    prm.num_problems = 1;
+    return launch(prm, st);
 }
 
 extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_problems,
@@ -581,25 +658,28 @@ extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_proble
         return FP8_ERR_INVALID;
     if (num_problems > FP8_GROUPED_MAX_PROBLEMS)
         return FP8_ERR_SHAPE;
+    bool any_sparse = false;
+    for (int i = 0; i < num_problems; ++i) {
+        const fp8_gemm_problem& g = problems[i];
+        const bool sp = g.A_meta != nullptr;
+        int rc = validate(g.M, g.N, g.K, g.A, sp ? g.K / 2 : g.lda, g.A_meta, sp, g.B, g.ldb,
+                          g.a_scale, g.a_mode, g.b_scale, g.b_mode, g.C, g.ldc, g.out_dtype,
+                          g.out_transposed);
+        if (rc != FP8_OK)
+            return rc;
+        any_sparse |= sp && g.M > 0 && g.N > 0 && g.K > 0;
+    }
+    if (num_problems == 0)
+        return FP8_OK;
     if (!device_supported())
         return FP8_ERR_UNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // a launch holding a sparse problem keeps TMEM columns [240, 256) for the
+    // metadata ring, so every tile in it has N <= 240
+    const int bn_max = any_sparse ? SPARSE_BN_MAX : BN_MAX;
     static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
     memset(&prm, 0, sizeof(prm));
     int n = 0;
-    for (int i = 0; i < num_problems; ++i) {
-        const fp8_gemm_problem& g = problems[i];
-        if (g.A_meta != nullptr)
-            return FP8_ERR_UNSUPPORTED;
-        int rc = validate_dense(g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.a_scale, g.a_mode,
-                                g.b_scale, g.b_mode, g.C, g.ldc, g.out_dtype);
-        if (rc != FP8_OK)
-            return rc;
-        if (g.M == 0 || g.N == 0)
-            continue;
-        if (g.ldc < (g.out_transposed ? g.M : g.N) || (g.out_transposed != 0 && g.out_transposed != 1))
-            return FP8_ERR_SHAPE;
-    }
     for (int i = 0; i < num_problems; ++i) {
         const fp8_gemm_problem& g = problems[i];
         if (g.M == 0 || g.N == 0)
@@ -611,9 +691,11 @@ extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_proble
                 return rc;
             continue;
         }
-        Job j = make_job(g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.a_scale, g.a_mode, g.b_scale,
-                         g.b_mode, g.alpha, g.C, g.ldc, g.out_dtype, g.out_transposed, true);
-        int rc = fill_problem(prm.prob[n], j, pick_bn(j.rows_q));
+        const bool sp = g.A_meta != nullptr;
+        Job j = make_job(g.M, g.N, g.K, g.A, sp ? g.K / 2 : g.lda, g.A_meta, g.B, g.ldb, g.a_scale,
+                         g.a_mode, g.b_scale, g.b_mode, g.alpha, g.C, g.ldc, g.out_dtype,
+                         g.out_transposed);
+        int rc = fill_problem(prm.prob[n], j, pick_bn(j.rows_q, bn_max));
         if (rc != FP8_OK)
             return rc;
         ++n;

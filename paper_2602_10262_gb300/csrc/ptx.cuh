@@ -221,6 +221,40 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr)
     return d;
 }
 
+// Same for a K-major tile with 64-byte swizzle: rows of 64 bytes, 8-row
+// atoms of 512 bytes.
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>(1u) << 16;
+    d |= static_cast<uint64_t>(512u >> 4) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(4u) << 61;
+    return d;
+}
+
+// Unswizzled row-major rows of 16 bytes (one 8 x 16-byte core matrix per 8
+// rows, consecutive core matrices 128 bytes apart): the source layout of a
+// 128 x 128-bit tcgen05.cp.
+__device__ __forceinline__ uint64_t sdesc_rows16_noswizzle(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>(1u) << 16;
+    d |= static_cast<uint64_t>(128u >> 4) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    return d;
+}
+
+// Shared memory -> tensor memory: 128 rows x 128 bits, row i to lane i,
+// four consecutive 32-bit columns from taddr.  Ordered with the tcgen05.mma
+// instructions this thread issues afterwards.
+__device__ __forceinline__ void tmem_cp_128x128b(uint32_t taddr, uint64_t sdesc)
+{
+    asm volatile("tcgen05.cp.cta_group::1.128x128b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
 // Instruction descriptor, kind::f8f6f4: E4M3 A and B, both K-major, F32
 // accumulator, M x N tile.
 //   bits 0-1 sparsity selector, bit 2 sparse flag, bits 4-5 D format (1 = F32),

@@ -26,12 +26,22 @@ def _cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def _codes(a):
+    """Device copy of a code matrix with its row stride padded to a multiple
+    of 16 bytes (the TMA row-stride rule); the view has the original shape."""
+    M, K = a.shape
+    ld = max(16, (K + 15) // 16 * 16)
+    t = torch.zeros((M, ld), dtype=torch.uint8, device="cuda")
+    t[:, :K] = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t[:, :K]
+
+
 def _ones(n=1):
     return torch.ones(n, dtype=torch.float32, device="cuda")
 
 
 def _gemm(gb, A, B, dA, a_mode, dB, b_mode, alpha, out_dtype):
-    C = gb.gemm_fp8_dense(_cuda(A), _cuda(B), _cuda(dA), a_mode, _cuda(dB), b_mode, alpha,
+    C = gb.gemm_fp8_dense(_codes(A), _codes(B), _cuda(dA), a_mode, _cuda(dB), b_mode, alpha,
                           out_dtype)
     torch.cuda.synchronize()
     assert gb.fp8_last_device_error() == 0
