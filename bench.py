@@ -227,6 +227,155 @@ def config(size, ws):
             "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"}
 
 
+# ------------------------------------------------------------------ serving
+
+class ServingBench:
+    """Poisson stream of FP8 GEMM requests from two tenants against resident
+    weights, served by the library's request server in continuous-batching
+    mode and in per-call mode (one quantise + one GEMM launch per request).
+
+    Tenant 0 (latency): M log-uniform in [1, 64]; tenant 1 (throughput): M
+    log-uniform in [64, 4096]; (N, K) uniform over {4096, 8192, 14336}^2;
+    half the requests use the 2:4-sparse copy of the weight.  Inputs are
+    seeded synthetic fp32 (seed 2 for the trace)."""
+
+    SIZES = (4096, 8192, 14336)
+
+    def __init__(self, dev, gb):
+        self.gb, self.dev = gb, dev
+        g = torch.Generator(device=dev).manual_seed(workloads.SEED_REQUESTS)
+        self.weights = {}
+        for N in self.SIZES:
+            for K in self.SIZES:
+                w = torch.randn((N, K), generator=g, device=dev, dtype=torch.float32)
+                Wd, dW = gb.fp8_quantize_e4m3(w, 1)
+                vals, meta = gb.prune24_compress(Wd)
+                self.weights[(N, K)] = (Wd, dW, vals, meta)
+                del w
+        self.X = torch.randn((4096, max(self.SIZES)), generator=g, device=dev, dtype=torch.float32)
+        self.arena = torch.empty((1 << 30,), dtype=torch.bfloat16, device=dev)
+        self.arena_pos = 0
+        torch.cuda.synchronize()
+
+    def trace(self, n, seed):
+        rng = np.random.default_rng(seed)
+        tenant = rng.integers(0, 2, n)
+        u = rng.random(n)
+        M = np.where(tenant == 0, np.round(2.0 ** (u * 6.0)), np.round(2.0 ** (6.0 + u * 6.0)))
+        N = rng.choice(self.SIZES, n)
+        K = rng.choice(self.SIZES, n)
+        sparse = rng.random(n) < 0.5
+        gap = rng.exponential(1.0, n)           # unit-rate Poisson arrivals, scaled later
+        return [dict(tenant=int(t), M=int(m), N=int(nn), K=int(k), sparse=bool(sp), gap=float(gp))
+                for t, m, nn, k, sp, gp in zip(tenant, M, N, K, sparse, gap)]
+
+    def _out(self, M, N):
+        n = M * N
+        if self.arena_pos + n > self.arena.numel():
+            self.arena_pos = 0
+        o = self.arena[self.arena_pos:self.arena_pos + n]
+        self.arena_pos += (n + 127) // 128 * 128
+        return o.data_ptr()
+
+    def _server(self, batching):
+        from paper_2602_10262_gb300.server import Server
+        sms = self.gb.fp8_device_sm_count()
+        srv = Server(num_tenants=2, latency_tenant=0, batching=batching,
+                     bulk_max_ctas=max(sms - 24, 1) if batching else 0, pool_bytes=4 << 30)
+        handles = {}
+        for (N, K), (Wd, dW, vals, meta) in self.weights.items():
+            handles[(N, K, False)] = srv.register_weight(N, K, Wd, dW, 1)
+            handles[(N, K, True)] = srv.register_weight(N, K, vals, dW, 1, W_meta=meta)
+        return srv, handles
+
+    def run(self, reqs, batching, rate=None):
+        """Submit `reqs` (all at once when rate is None, else Poisson at
+        `rate` requests/s); returns per-request (latency_us, tenant, flops)
+        and the makespan in microseconds."""
+        srv, handles = self._server(batching)
+        ld = self.X.stride(0)
+        try:
+            times = None
+            if rate is not None:
+                times = np.cumsum([r["gap"] for r in reqs]) / rate * 1e6
+            t0 = srv.now_us() + 1000.0
+            tickets = []
+            for i, r in enumerate(reqs):
+                if times is not None:
+                    target = t0 + times[i]
+                    while srv.now_us() < target:
+                        pass
+                out = self._out(r["M"], r["N"])
+                tickets.append(srv.submit(r["tenant"], handles[(r["N"], r["K"], r["sparse"])],
+                                          r["M"], self.X.data_ptr(), ld, out, r["N"]))
+            res = [srv.wait(t, 60) for t in tickets]
+            stats = srv.stats()
+        finally:
+            srv.close()
+        if any(x is None or x.status != 0 for x in res):
+            raise RuntimeError("serving request failed")
+        lat = np.array([x.t_end_us - x.t_submit_us for x in res])
+        first = min(x.t_submit_us for x in res)
+        last = max(x.t_end_us for x in res)
+        return lat, last - first, stats, res
+
+    @staticmethod
+    def flops(reqs):
+        return sum(2.0 * r["M"] * r["N"] * r["K"] for r in reqs)
+
+    def isolated(self, reqs):
+        """Latency of each request run alone (per-call server, one at a time)."""
+        srv, handles = self._server(False)
+        ld = self.X.stride(0)
+        out = []
+        try:
+            for r in reqs:
+                t = srv.submit(r["tenant"], handles[(r["N"], r["K"], r["sparse"])], r["M"],
+                               self.X.data_ptr(), ld, self._out(r["M"], r["N"]), r["N"])
+                x = srv.wait(t, 60)
+                out.append(x.t_end_us - x.t_submit_us)
+        finally:
+            srv.close()
+        return np.array(out)
+
+
+def serving_report(gb, dev, n_cap=1500, n_load=1500, load=0.8):
+    sb = ServingBench(dev, gb)
+    cap_reqs = sb.trace(n_cap, workloads.SEED_REQUESTS + 1)
+    cap = {}
+    for mode, batching in (("batched", True), ("per_call", False)):
+        sb.run(cap_reqs[:64], batching)                      # warm-up
+        _, span, stats, _ = sb.run(cap_reqs, batching)
+        cap[mode] = {"tflops": sb.flops(cap_reqs) / (span * 1e-6) / 1e12,
+                     "req_per_s": n_cap / (span * 1e-6),
+                     "kernel_launches": stats["kernel_launches"], "batches": stats["batches"]}
+    rate = load * min(cap["batched"]["req_per_s"], cap["per_call"]["req_per_s"])
+    reqs = sb.trace(n_load, workloads.SEED_REQUESTS)
+    iso = sb.isolated(reqs)
+    tenant = np.array([r["tenant"] for r in reqs])
+    out = {"workload": "Poisson two-tenant GEMM stream, M log-uniform [1,4096], "
+                       "(N,K) in {4096,8192,14336}^2, 50% 2:4-sparse weights",
+           "offered_load": f"{load} x per-call capacity = {rate:.0f} req/s",
+           "capacity": cap}
+    for mode, batching in (("batched", True), ("per_call", False)):
+        lat, span, stats, res = sb.run(reqs, batching, rate)
+        slow = iso / lat
+        x = [float(np.mean(slow[tenant == t])) for t in (0, 1)]
+        mean_lat = [float(np.mean(lat[tenant == t])) for t in (0, 1)]
+        out[mode] = {
+            "p50_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 50)) for t in (0, 1)},
+            "p99_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 99)) for t in (0, 1)},
+            "p99_all_us": float(np.percentile(lat, 99)),
+            "tflops": sb.flops(reqs) / (span * 1e-6) / 1e12,
+            "jain": (sum(x) ** 2) / (2 * sum(v * v for v in x)),
+            "fairness_1_minus_range_over_mean": 1.0 - (max(mean_lat) - min(mean_lat)) / np.mean(mean_lat),
+            "fairness_min_over_max": min(mean_lat) / max(mean_lat),
+            "mean_batch": float(np.mean([r.batch_size for r in res])),
+            "kernel_launches": stats["kernel_launches"],
+        }
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def main():
@@ -240,6 +389,7 @@ def main():
     ap.add_argument("--cpu-cols", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -390,6 +540,12 @@ def main():
                "ms_per_step": ms_e2e / n_e2e, "steps": n_e2e,
                "path": "pinned host fp32 -> H2D -> C ABI (quantize, prune, dense, sparse) -> D2H bf16"}
 
+    # ---------------------------------------------------------------- serving
+    serving = None
+    if not args.no_serving:
+        del x_h, w_h
+        serving = serving_report(gb, dev)
+
     # ---------------------------------------------------------------- CPU oracle
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -408,7 +564,7 @@ def main():
             "config": config(S, ws),
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "stages": stages, "sparse_path": sparse_ok,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks.summary(),
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks.summary(), "serving": serving,
         }
         print(json.dumps(line))
     return 0

@@ -84,6 +84,22 @@ int fp8_device_sm_count(void);
 int fp8_quantize_e4m3(const float *x, int64_t rows, int64_t cols, int64_t ldx, int scale_mode,
                       uint8_t *q, int64_t ldq, float *dequant_scale, fp8_stream_t stream);
 
+/* Per-row quantisation (scale_mode 1 above) of up to FP8_QUANT_GROUPED_MAX
+ * independent fp32 matrices in one launch; each job follows the conventions
+ * of fp8_quantize_e4m3 (FP8_ERR_SHAPE for more jobs).  Used by the request
+ * server to quantise a whole batch of activations at once. */
+#define FP8_QUANT_GROUPED_MAX 32
+
+typedef struct {
+    const float *x;          /* device fp32 [rows, cols], row stride ldx */
+    int64_t rows, cols, ldx;
+    uint8_t *q;              /* device codes [rows, cols], row stride ldq */
+    int64_t ldq;
+    float *dequant_scale;    /* device fp32 [rows] */
+} fp8_quant_job;
+
+int fp8_quantize_e4m3_rows_grouped(const fp8_quant_job *jobs, int num_jobs, fp8_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * 2:4 prune + compress (row a3).  Paper: section 2 "Structured Sparsity",
  * section 6 (2 of every 4 consecutive elements along K are zero; the paper
@@ -177,6 +193,125 @@ typedef struct {
 } fp8_gemm_problem;
 
 int gemm_fp8_grouped(const fp8_gemm_problem *problems, int num_problems, fp8_stream_t stream);
+
+/* As gemm_fp8_grouped, with the persistent grid capped at max_ctas CTAs
+ * (one per SM; max_ctas <= 0 means every SM).  Leaving SMs free lets work on
+ * another stream (a latency-sensitive tenant) run beside this launch — the
+ * occupancy-aware co-scheduling the paper recommends in section 8.2.  The
+ * results do not depend on max_ctas. */
+int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int max_ctas,
+                        fp8_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Request server (row a8): continuous batching of FP8 GEMM requests.
+ * Paper: sections 5 and 6.2 (concurrent GEMMs on separate hardware queues:
+ * overlap, fairness, per-stream latency) and the section 8.2 guidance
+ * (continuous batching, occupancy-aware co-scheduling, sparsity under
+ * concurrency).
+ *
+ * A request multiplies activations x (device fp32 [M, K], quantised per row
+ * by the server) with a registered resident weight W (E4M3 [N, K], dense or
+ * 2:4-compressed, with its dequantisation factors) into out (device [M, N],
+ * fp32 or bf16): out = alpha * dX[m] * dW[n] * dec(X) dec(W)^T.
+ *
+ * A scheduler thread owns the GPU work.  Each tenant has its own CUDA stream;
+ * the latency tenant's stream has the highest priority.  Whenever one of a
+ * tenant's in-flight slots frees, the requests that arrived meanwhile (FIFO,
+ * up to max_batch) are admitted if their workspace (M x K codes + M scales)
+ * fits in the server's device pool, quantised by one grouped launch and
+ * multiplied by one grouped persistent GEMM launch.  Bulk tenants' GEMMs may
+ * be capped at bulk_max_ctas CTAs so latency work runs beside them.  With
+ * batching = 0 every request is launched on its own as soon as it is
+ * admitted (one quantise + one GEMM launch per request: the per-call
+ * baseline).  A request's result does not depend on what it was batched
+ * with.
+ *
+ * Thread safety: submit, poll, wait and stats may be called from any
+ * threads; register_weight must not race with submit; destroy must not race
+ * with anything.  The caller owns x, out and the weight buffers and keeps
+ * them alive until the request (or the server) is done.
+ * ------------------------------------------------------------------------- */
+#define FP8_SERVER_MAX_TENANTS 8
+
+typedef struct {
+    int num_tenants;          /* 1..FP8_SERVER_MAX_TENANTS */
+    int latency_tenant;       /* tenant given the high-priority stream (-1: none) */
+    int batching;             /* 1: continuous batching; 0: one launch per request */
+    int max_batch;            /* requests per batch, 1..FP8_GROUPED_MAX_PROBLEMS (0: max) */
+    int max_inflight;         /* in-flight batches per tenant (0: 2) */
+    int bulk_max_ctas;        /* CTA cap for non-latency tenants' GEMMs (0: all SMs) */
+    size_t pool_bytes;        /* workspace pool; 0: free HBM minus reserve_bytes */
+    size_t reserve_bytes;     /* HBM left untouched when sizing the pool (0: 1 GiB) */
+} fp8_server_config;
+
+typedef struct fp8_server fp8_server;
+
+typedef struct {
+    int tenant;
+    uint64_t weight;          /* handle from fp8_server_register_weight */
+    int64_t M;                /* rows of x and out */
+    const float *x;           /* device fp32 [M, K], row stride ldx */
+    int64_t ldx;
+    void *out;                /* device [M, N], row stride ldo elements */
+    int64_t ldo;
+    int out_dtype;            /* 0 fp32, 1 bf16 */
+    float alpha;
+} fp8_request;
+
+typedef struct {
+    int status;               /* FP8_OK or the error that ended the request */
+    int batch_size;           /* requests in the launch that carried it */
+    double t_submit_us;       /* host clock, microseconds since server creation */
+    double t_launch_us;       /* when its batch was enqueued */
+    double t_end_us;          /* when the GPU finished its batch */
+} fp8_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed, rejected;
+    uint64_t batches, kernel_launches, max_batch_seen;
+    size_t pool_bytes, pool_in_use, pool_high_water;
+} fp8_server_stats;
+
+/* Creates the server on the current device.  FP8_ERR_OOM if the pool cannot
+ * be allocated. */
+int fp8_server_create(const fp8_server_config *cfg, fp8_server **out);
+
+/* Host-only server for capacity planning and tests: no device work; a batch
+ * takes launch_us + us_per_gflop * (its GFLOP) of simulated time, and with
+ * fail_every > 0 every fail_every-th launch fails with FP8_ERR_CUDA (the
+ * failure is reported on each request of that batch). */
+int fp8_server_create_simulated(const fp8_server_config *cfg, double launch_us,
+                                double us_per_gflop, int fail_every, fp8_server **out);
+
+/* Finishes in-flight batches, fails queued requests with FP8_ERR_INVALID,
+ * frees the pool and streams. */
+int fp8_server_destroy(fp8_server *srv);
+
+/* Registers a resident weight: W E4M3 [N, K] (row stride ldw) for dense, or
+ * the 2:4 pair (W = kept codes [N, K/2], W_meta = metadata [N, K/8], K %
+ * 128 == 0) when W_meta != NULL; w_scale fp32 [1] (w_mode 0) or [N]
+ * (w_mode 1).  K % 16 == 0. */
+int fp8_server_register_weight(fp8_server *srv, int64_t N, int64_t K, const uint8_t *W, int64_t ldw,
+                               const uint8_t *W_meta, const float *w_scale, int w_mode,
+                               uint64_t *handle);
+
+/* Queues a request; *ticket identifies it.  FP8_ERR_OOM if its workspace
+ * can never fit in the pool; FP8_ERR_INVALID / FP8_ERR_SHAPE for bad
+ * arguments. */
+int fp8_server_submit(fp8_server *srv, const fp8_request *req, uint64_t *ticket);
+
+/* FP8_PENDING while the request runs; otherwise fills *res, forgets the
+ * ticket and returns the request's status (FP8_ERR_INVALID for an unknown
+ * ticket). */
+int fp8_server_poll(fp8_server *srv, uint64_t ticket, fp8_result *res);
+
+/* As poll, blocking up to timeout_s seconds (FP8_PENDING on expiry). */
+int fp8_server_wait(fp8_server *srv, uint64_t ticket, fp8_result *res, double timeout_s);
+
+int fp8_server_get_stats(fp8_server *srv, fp8_server_stats *stats);
+
+/* Microseconds since the server was created (the clock of fp8_result). */
+double fp8_server_now_us(fp8_server *srv);
 
 #ifdef __cplusplus
 }

@@ -35,6 +35,40 @@ class FP8Problem(ctypes.Structure):
     ]
 
 
+class FP8QuantJob(ctypes.Structure):
+    """Mirror of ``fp8_quant_job``."""
+    _fields_ = [("x", P), ("rows", I64), ("cols", I64), ("ldx", I64), ("q", P), ("ldq", I64),
+                ("dequant_scale", P)]
+
+
+class FP8ServerConfig(ctypes.Structure):
+    """Mirror of ``fp8_server_config``."""
+    _fields_ = [("num_tenants", I32), ("latency_tenant", I32), ("batching", I32),
+                ("max_batch", I32), ("max_inflight", I32), ("bulk_max_ctas", I32),
+                ("pool_bytes", ctypes.c_size_t), ("reserve_bytes", ctypes.c_size_t)]
+
+
+class FP8Request(ctypes.Structure):
+    """Mirror of ``fp8_request``."""
+    _fields_ = [("tenant", I32), ("weight", ctypes.c_uint64), ("M", I64), ("x", P), ("ldx", I64),
+                ("out", P), ("ldo", I64), ("out_dtype", I32), ("alpha", F32)]
+
+
+class FP8Result(ctypes.Structure):
+    """Mirror of ``fp8_result``."""
+    _fields_ = [("status", I32), ("batch_size", I32), ("t_submit_us", ctypes.c_double),
+                ("t_launch_us", ctypes.c_double), ("t_end_us", ctypes.c_double)]
+
+
+class FP8ServerStats(ctypes.Structure):
+    """Mirror of ``fp8_server_stats``."""
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("max_batch_seen", ctypes.c_uint64), ("pool_bytes", ctypes.c_size_t),
+                ("pool_in_use", ctypes.c_size_t), ("pool_high_water", ctypes.c_size_t)]
+
+
 SIGNATURES = {
     "fp8_status_string": (ctypes.c_char_p, [I32]),
     "fp8_last_device_error": (I32, [P]),
@@ -45,6 +79,19 @@ SIGNATURES = {
     "gemm_fp8_dense": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32, P]),
     "gemm_fp8_sparse24": (I32, [I64, I64, I64, P, P, P, I64, P, I32, P, I32, F32, P, I64, I32, I32, P]),
     "gemm_fp8_grouped": (I32, [ctypes.POINTER(FP8Problem), I32, P]),
+    "gemm_fp8_grouped_ex": (I32, [ctypes.POINTER(FP8Problem), I32, I32, P]),
+    "fp8_quantize_e4m3_rows_grouped": (I32, [ctypes.POINTER(FP8QuantJob), I32, P]),
+    "fp8_server_create": (I32, [ctypes.POINTER(FP8ServerConfig), ctypes.POINTER(P)]),
+    "fp8_server_create_simulated": (I32, [ctypes.POINTER(FP8ServerConfig), ctypes.c_double,
+                                          ctypes.c_double, I32, ctypes.POINTER(P)]),
+    "fp8_server_destroy": (I32, [P]),
+    "fp8_server_register_weight": (I32, [P, I64, I64, P, I64, P, P, I32,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "fp8_server_submit": (I32, [P, ctypes.POINTER(FP8Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "fp8_server_poll": (I32, [P, ctypes.c_uint64, ctypes.POINTER(FP8Result)]),
+    "fp8_server_wait": (I32, [P, ctypes.c_uint64, ctypes.POINTER(FP8Result), ctypes.c_double]),
+    "fp8_server_get_stats": (I32, [P, ctypes.POINTER(FP8ServerStats)]),
+    "fp8_server_now_us": (ctypes.c_double, [P]),
 }
 
 

@@ -537,7 +537,7 @@ int write_zeros(void* C, int64_t ldc, int64_t rows, int64_t cols, int out_bf16, 
 }
 
 template <int MAXP>
-int launch(Params<MAXP>& prm, cudaStream_t st)
+int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas = 0)
 {
     static std::once_flag attr_once[64];
     int dev = 0;
@@ -559,7 +559,9 @@ int launch(Params<MAXP>& prm, cudaStream_t st)
     if (tiles == 0)
         return FP8_OK;
     prm.err = device_error_word();
-    const int grid = std::min(tiles, sm_count());
+    int grid = std::min(tiles, sm_count());
+    if (max_ctas > 0)
+        grid = std::min(grid, max_ctas);
     gemm_fp8_kernel<MAXP><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(prm);
     GB_CUDA_OK(cudaGetLastError());
     return FP8_OK;
@@ -653,6 +655,12 @@ extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t*
 extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_problems,
                                 fp8_stream_t stream)
 {
+    return gemm_fp8_grouped_ex(problems, num_problems, 0, stream);
+}
+
+extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_problems,
+                                   int max_ctas, fp8_stream_t stream)
+{
     using namespace gb300;
     if (num_problems < 0 || (num_problems > 0 && !problems))
         return FP8_ERR_INVALID;
@@ -703,5 +711,5 @@ extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_proble
     prm.num_problems = n;
     if (n == 0)
         return FP8_OK;
-    return launch(prm, st);
+    return launch(prm, st, max_ctas);
 }

@@ -7,6 +7,9 @@
 // row (an L2 hit: the rows in flight are far smaller than L2) and writes the
 // codes.  HBM traffic: 4 bytes read + 1 byte written per element.
 //
+// fp8_quantize_e4m3_rows_grouped runs the per-row path for up to 32
+// independent matrices in one launch (job table in the kernel parameters).
+//
 // Per tensor (scale_mode 0): a grid-stride amax kernel folds into the
 // dequant_scale[0] slot with atomicMax, an encode kernel reads it, and a
 // one-thread kernel turns the slot into d = amax / 448.
@@ -73,6 +76,35 @@ __device__ __forceinline__ void scale_from_amax(uint32_t amax_bits, float& s, fl
     }
 }
 
+// One row: amax (CTA reduction), scale, codes.  vec: the row allows 16-byte
+// loads and 4-byte stores (x 16-aligned, q 4-aligned).
+__device__ __forceinline__ void quantize_row(const float* __restrict__ xr, int64_t cols,
+                                             uint8_t* __restrict__ qr, float* __restrict__ d_out,
+                                             int vec, int* err, uint32_t* red)
+{
+    const int64_t nvec = vec ? cols / 4 : 0;
+    uint32_t m = 0;
+    for (int64_t i = threadIdx.x; i < nvec; i += kThreads) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(xr) + i);
+        m = max(m, max(max(abs_bits(v.x), abs_bits(v.y)), max(abs_bits(v.z), abs_bits(v.w))));
+    }
+    for (int64_t c = nvec * 4 + threadIdx.x; c < cols; c += kThreads)
+        m = max(m, abs_bits(xr[c]));
+    m = block_max_u32(m, red);
+    if (m >= kInfBits && threadIdx.x == 0)
+        report_device_error(err, FP8_ERR_NONFINITE);
+    float s, dq;
+    scale_from_amax(m, s, dq);
+    if (threadIdx.x == 0)
+        *d_out = dq;
+    for (int64_t i = threadIdx.x; i < nvec; i += kThreads) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(xr) + i);
+        reinterpret_cast<uint32_t*>(qr)[i] = enc4(v, s);
+    }
+    for (int64_t c = nvec * 4 + threadIdx.x; c < cols; c += kThreads)
+        qr[c] = static_cast<uint8_t>(enc2(__fmul_rn(xr[c], s), 0.0f) & 0xFFu);
+}
+
 // vec: x rows and q rows allow 16-byte loads / 4-byte stores (x 16-aligned,
 // ldx % 4 == 0, q 4-aligned, ldq % 4 == 0).
 __global__ void __launch_bounds__(kThreads) quant_row_kernel(const float* __restrict__ x,
@@ -82,30 +114,33 @@ __global__ void __launch_bounds__(kThreads) quant_row_kernel(const float* __rest
                                                              int vec, int* err)
 {
     __shared__ uint32_t red[kThreads / 32];
-    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        const float* xr = x + r * ldx;
-        uint8_t* qr = q + r * ldq;
-        const int64_t nvec = vec ? cols / 4 : 0;
-        uint32_t m = 0;
-        for (int64_t i = threadIdx.x; i < nvec; i += kThreads) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(xr) + i);
-            m = max(m, max(max(abs_bits(v.x), abs_bits(v.y)), max(abs_bits(v.z), abs_bits(v.w))));
-        }
-        for (int64_t c = nvec * 4 + threadIdx.x; c < cols; c += kThreads)
-            m = max(m, abs_bits(xr[c]));
-        m = block_max_u32(m, red);
-        if (m >= kInfBits && threadIdx.x == 0)
-            report_device_error(err, FP8_ERR_NONFINITE);
-        float s, dq;
-        scale_from_amax(m, s, dq);
-        if (threadIdx.x == 0)
-            d[r] = dq;
-        for (int64_t i = threadIdx.x; i < nvec; i += kThreads) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(xr) + i);
-            reinterpret_cast<uint32_t*>(qr)[i] = enc4(v, s);
-        }
-        for (int64_t c = nvec * 4 + threadIdx.x; c < cols; c += kThreads)
-            qr[c] = static_cast<uint8_t>(enc2(__fmul_rn(xr[c], s), 0.0f) & 0xFFu);
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+        quantize_row(x + r * ldx, cols, q + r * ldq, d + r, vec, err, red);
+}
+
+// Many independent per-row quantisations in one launch: the job table is
+// passed by value; CTA b takes global row b (rows of job j follow those of
+// job j - 1).
+struct RowJobs {
+    fp8_quant_job job[FP8_QUANT_GROUPED_MAX];
+    int64_t row_start[FP8_QUANT_GROUPED_MAX + 1];
+    int vec[FP8_QUANT_GROUPED_MAX];
+    int n;
+};
+
+__global__ void __launch_bounds__(kThreads) quant_rows_grouped_kernel(const __grid_constant__ RowJobs jobs,
+                                                                      int* err)
+{
+    __shared__ uint32_t red[kThreads / 32];
+    const int64_t total = jobs.row_start[jobs.n];
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        int j = 0;
+        while (j + 1 < jobs.n && jobs.row_start[j + 1] <= g)
+            ++j;
+        const fp8_quant_job& J = jobs.job[j];
+        const int64_t r = g - jobs.row_start[j];
+        quantize_row(J.x + r * J.ldx, J.cols, J.q + r * J.ldq, J.dequant_scale + r, jobs.vec[j], err,
+                     red);
     }
 }
 
@@ -214,6 +249,49 @@ extern "C" int fp8_quantize_e4m3(const float* x, int64_t rows, int64_t cols, int
                                                                           ldq, vec, slot);
     GB_CUDA_OK(cudaGetLastError());
     quant_finalize_kernel<<<1, 1, 0, st>>>(slot, err);
+    GB_CUDA_OK(cudaGetLastError());
+    return FP8_OK;
+}
+
+extern "C" int fp8_quantize_e4m3_rows_grouped(const fp8_quant_job* jobs, int num_jobs,
+                                              fp8_stream_t stream)
+{
+    using namespace gb300;
+    if (num_jobs < 0 || (num_jobs > 0 && !jobs))
+        return FP8_ERR_INVALID;
+    if (num_jobs > FP8_QUANT_GROUPED_MAX)
+        return FP8_ERR_SHAPE;
+    RowJobs rj;
+    memset(&rj, 0, sizeof(rj));
+    int64_t rows = 0;
+    for (int i = 0; i < num_jobs; ++i) {
+        const fp8_quant_job& J = jobs[i];
+        if (J.rows < 0 || J.cols < 0)
+            return FP8_ERR_INVALID;
+        if (J.rows == 0 || J.cols == 0)
+            continue;
+        if (!J.x || !J.q || !J.dequant_scale)
+            return FP8_ERR_INVALID;
+        if (J.ldx < J.cols || J.ldq < J.cols)
+            return FP8_ERR_SHAPE;
+        if ((reinterpret_cast<uintptr_t>(J.x) & 3u) ||
+            (reinterpret_cast<uintptr_t>(J.dequant_scale) & 3u))
+            return FP8_ERR_ALIGN;
+        const int k = rj.n++;
+        rj.job[k] = J;
+        rj.row_start[k] = rows;
+        rj.vec[k] = aligned16(J.x) && (J.ldx % 4 == 0) &&
+                    (reinterpret_cast<uintptr_t>(J.q) % 4 == 0) && (J.ldq % 4 == 0);
+        rows += J.rows;
+    }
+    rj.row_start[rj.n] = rows;
+    if (rows == 0)
+        return FP8_OK;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    const int64_t grid = rows < 65535LL * 8 ? rows : 65535LL * 8;
+    quant_rows_grouped_kernel<<<static_cast<unsigned>(grid), kThreads, 0,
+                                reinterpret_cast<cudaStream_t>(stream)>>>(rj, device_error_word());
     GB_CUDA_OK(cudaGetLastError());
     return FP8_OK;
 }

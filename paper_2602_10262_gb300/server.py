@@ -1,0 +1,143 @@
+"""Python handle for the library's request server (fp8_server_* in the C ABI).
+
+Argument marshalling only: the queues, admission, batching and GPU work live
+in csrc/server.cpp.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import _lib
+
+PENDING = 1
+
+
+class ServerError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.load().fp8_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+@dataclass
+class Result:
+    status: int
+    batch_size: int
+    t_submit_us: float
+    t_launch_us: float
+    t_end_us: float
+
+    @property
+    def latency_us(self) -> float:
+        return self.t_end_us - self.t_submit_us
+
+
+def _result(r: _lib.FP8Result) -> Result:
+    return Result(r.status, r.batch_size, r.t_submit_us, r.t_launch_us, r.t_end_us)
+
+
+class Server:
+    """fp8_server: continuous batching of FP8 GEMM requests on one GPU, or a
+    host-only simulation when ``simulate=(launch_us, us_per_gflop,
+    fail_every)`` is given."""
+
+    def __init__(self, num_tenants: int = 2, latency_tenant: int = 0, batching: bool = True,
+                 max_batch: int = 0, max_inflight: int = 0, bulk_max_ctas: int = 0,
+                 pool_bytes: int = 0, reserve_bytes: int = 0, simulate=None):
+        self.lib = _lib.load()
+        cfg = _lib.FP8ServerConfig(num_tenants, latency_tenant, int(bool(batching)), max_batch,
+                                   max_inflight, bulk_max_ctas, pool_bytes, reserve_bytes)
+        h = ctypes.c_void_p()
+        if simulate is None:
+            rc = self.lib.fp8_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        else:
+            launch_us, us_per_gflop, fail_every = simulate
+            rc = self.lib.fp8_server_create_simulated(ctypes.byref(cfg), float(launch_us),
+                                                      float(us_per_gflop), int(fail_every),
+                                                      ctypes.byref(h))
+        if rc != 0:
+            raise ServerError(rc, "fp8_server_create")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            self.lib.fp8_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register_weight(self, N: int, K: int, W, w_scale, w_mode: int, W_meta=None,
+                        ldw: Optional[int] = None) -> int:
+        """W / W_meta / w_scale: CUDA tensors (kept alive by the server object)
+        or raw integer device addresses."""
+        def ptr(t):
+            if t is None:
+                return None
+            if isinstance(t, torch.Tensor):
+                self._keep.append(t)
+                return t.data_ptr()
+            return int(t)
+        if ldw is None:
+            ldw = W.stride(0) if isinstance(W, torch.Tensor) and W_meta is None else K
+        hdl = ctypes.c_uint64()
+        rc = self.lib.fp8_server_register_weight(self.h, N, K, ptr(W), ldw, ptr(W_meta),
+                                                 ptr(w_scale), w_mode, ctypes.byref(hdl))
+        if rc != 0:
+            raise ServerError(rc, "fp8_server_register_weight")
+        return hdl.value
+
+    def submit(self, tenant: int, weight: int, M: int, x, ldx: int, out, ldo: int,
+               out_dtype: int = 1, alpha: float = 1.0) -> int:
+        """x / out: device addresses (int) or CUDA tensors."""
+        xp = x.data_ptr() if isinstance(x, torch.Tensor) else int(x)
+        op = out.data_ptr() if isinstance(out, torch.Tensor) else int(out)
+        req = _lib.FP8Request(tenant, weight, M, xp, ldx, op, ldo, out_dtype, alpha)
+        t = ctypes.c_uint64()
+        rc = self.lib.fp8_server_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if rc != 0:
+            raise ServerError(rc, "fp8_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else a Result (status may be an error)."""
+        r = _lib.FP8Result()
+        rc = self.lib.fp8_server_poll(self.h, ticket, ctypes.byref(r))
+        if rc == PENDING:
+            return None
+        if rc != 0 and r.status == 0:
+            raise ServerError(rc, "fp8_server_poll")
+        return _result(r)
+
+    def wait(self, ticket: int, timeout_s: float = 30.0):
+        r = _lib.FP8Result()
+        rc = self.lib.fp8_server_wait(self.h, ticket, ctypes.byref(r), float(timeout_s))
+        if rc == PENDING:
+            return None
+        if rc != 0 and r.status == 0:
+            raise ServerError(rc, "fp8_server_wait")
+        return _result(r)
+
+    def stats(self) -> dict:
+        s = _lib.FP8ServerStats()
+        rc = self.lib.fp8_server_get_stats(self.h, ctypes.byref(s))
+        if rc != 0:
+            raise ServerError(rc, "fp8_server_get_stats")
+        return {name: getattr(s, name) for name, _ in s._fields_}
+
+    def now_us(self) -> float:
+        return float(self.lib.fp8_server_now_us(self.h))
