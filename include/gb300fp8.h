@@ -202,6 +202,15 @@ int gemm_fp8_grouped(const fp8_gemm_problem *problems, int num_problems, fp8_str
 int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int max_ctas,
                         fp8_stream_t stream);
 
+/* Process-wide tile configuration of the GEMM kernels, for tuning and tests.
+ * mt: 128-row MMA halves per CTA tile: 1 (128 x N tiles, double-buffered
+ * accumulators), 2 (256 x N tiles: two MMAs share each B tile, a third fewer
+ * operand bytes per FLOP), 0 = chosen per launch (2 when every problem fills
+ * 256-row tiles with N tiles >= 128 wide and there are at least as many tiles
+ * as SMs).  group_m: M-blocks per raster band (0 = 8).  Results do not depend
+ * on either.  Affects launches enqueued after the call, from any thread. */
+int fp8_gemm_set_tile_config(int mt, int group_m);
+
 /* ---------------------------------------------------------------------------
  * Request server (row a8): continuous batching of FP8 GEMM requests.
  * Paper: sections 5 and 6.2 (concurrent GEMMs on separate hardware queues:

@@ -19,7 +19,7 @@ from . import _lib
 __all__ = [
     "Fp8Error", "library", "fp8_quantize_e4m3", "prune24_compress", "prune24_decompress",
     "gemm_fp8_dense", "gemm_fp8_sparse24", "gemm_fp8_grouped", "fp8_last_device_error",
-    "fp8_device_sm_count", "OUT_F32", "OUT_BF16",
+    "fp8_device_sm_count", "fp8_gemm_set_tile_config", "OUT_F32", "OUT_BF16",
 ]
 
 OUT_F32 = 0
@@ -75,6 +75,12 @@ def fp8_last_device_error(stream=None) -> int:
 
 def fp8_device_sm_count() -> int:
     return int(library().fp8_device_sm_count())
+
+
+def fp8_gemm_set_tile_config(mt: int = 0, group_m: int = 0) -> None:
+    """Force the GEMM tile shape (mt 1 or 2 row-halves per tile, raster band
+    height group_m); 0 restores the per-launch choice."""
+    _check(library().fp8_gemm_set_tile_config(int(mt), int(group_m)), "fp8_gemm_set_tile_config")
 
 
 def fp8_quantize_e4m3(x: torch.Tensor, scale_mode: int, q: Optional[torch.Tensor] = None,

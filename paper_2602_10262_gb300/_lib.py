@@ -81,6 +81,7 @@ SIGNATURES = {
     "gemm_fp8_grouped": (I32, [ctypes.POINTER(FP8Problem), I32, P]),
     "gemm_fp8_grouped_ex": (I32, [ctypes.POINTER(FP8Problem), I32, I32, P]),
     "fp8_quantize_e4m3_rows_grouped": (I32, [ctypes.POINTER(FP8QuantJob), I32, P]),
+    "fp8_gemm_set_tile_config": (I32, [I32, I32]),
     "fp8_server_create": (I32, [ctypes.POINTER(FP8ServerConfig), ctypes.POINTER(P)]),
     "fp8_server_create_simulated": (I32, [ctypes.POINTER(FP8ServerConfig), ctypes.c_double,
                                           ctypes.c_double, I32, ctypes.POINTER(P)]),

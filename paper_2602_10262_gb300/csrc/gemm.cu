@@ -21,6 +21,7 @@
 // (P = B, Q = A) so that the long side fills the 128-row MMA and the output
 // is written transposed.
 #include <algorithm>
+#include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -32,31 +33,44 @@
 namespace gb300 {
 namespace {
 
-constexpr int BM = 128;
-constexpr int BK = 128;
+constexpr int BM = 128;                   // rows of one MMA (M = 128, cta_group::1)
+constexpr int BK = 128;                   // codes per k-block (one 128-byte swizzle row)
 constexpr int BN_MAX = 256;
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK;                    // 16 KB
-constexpr int B_BYTES = BN_MAX * BK;                // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;      // 48 KB
-constexpr int TMEM_COLS = 2 * BN_MAX;
-constexpr int NUM_THREADS = 192;
-constexpr int GROUP_M = 8;                          // raster: 8 M-blocks per band
-// 2:4-sparse tiles: per stage the kept A codes (128 rows x 64 bytes, 64-byte
-// swizzle) and the metadata (128 rows x 16 bytes) share the A region; the
-// metadata is copied into a ring of TMEM columns [240, 256) (4 columns per
-// stage), so sparse tiles use N <= 240 and leave those columns free.
-constexpr int SP_A_BYTES = BM * BK / 2;             // 8 KB
-constexpr int SP_META_BYTES = BM * BK / 8;          // 2 KB
-constexpr int META_COL0 = 240;
+constexpr int B_BYTES = BN_MAX * BK;      // 32 KB: B tile of a stage
+constexpr int TMEM_COLS = 512;
+constexpr int GROUP_M_DEFAULT = 8;        // raster: M-blocks per band
+// 2:4-sparse tiles: per stage and per 128-row half, the kept A codes (128 rows
+// x 64 bytes, 64-byte swizzle) and the metadata (128 rows x 16 bytes) share the
+// A region; the metadata is copied into a ring of TMEM columns [240, 256) of
+// that half's accumulator block (4 columns per stage), so sparse tiles use
+// N <= 240.
+constexpr int SP_META_COL0 = 240;
 constexpr int SPARSE_BN_MAX = 240;
-static_assert(META_COL0 + 4 * STAGES <= BN_MAX, "metadata ring must fit beside accumulator 0");
-constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers*/;
+
+// MT = 128-row MMA halves per CTA tile.
+//  MT = 1: tile 128 x bn, 4 stages of 48 KB, two accumulators (cols 0 / 256)
+//          so the epilogue of tile i overlaps the MMAs of tile i + 1;
+//  MT = 2: tile 256 x bn, 3 stages of 64 KB; two MMAs per k-step share the B
+//          tile (a third fewer operand bytes per FLOP), one accumulator
+//          spanning all 512 columns (rows 0-127 in cols 0-255, rows 128-255
+//          in cols 256-511).
+template <int MT>
+struct Cfg {
+    static constexpr int kStages = MT == 2 ? 3 : 4;
+    static constexpr int kABytes = MT * BM * BK;                 // A region of a stage
+    static constexpr int kStageBytes = kABytes + B_BYTES;
+    static constexpr int kAcc = MT == 2 ? 1 : 2;                  // accumulator buffers
+    static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
+    static constexpr int kSpABytes = MT * BM * BK / 2;           // kept codes of a stage
+    static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
+    static_assert(SP_META_COL0 + 4 * kStages <= BN_MAX, "metadata ring must fit beside the accumulator");
+    static_assert(kSpABytes + MT * BM * BK / 8 <= kABytes, "sparse A + metadata fit the A region");
+};
 
 struct Problem {
-    CUtensorMap tmP;        // P [rows_p, K] codes, box {128, 128}
+    CUtensorMap tmP;        // P [rows_p, K] codes, box {128, 128 * MT}
     CUtensorMap tmQ;        // Q [rows_q, K] codes, box {128, bn}
-    CUtensorMap tmE;        // sparse only: metadata [rows_p, K/8], box {16, 128}
+    CUtensorMap tmE;        // sparse only: metadata [rows_p, K/8], box {16, 128 * MT}
     const float* sp;        // scale of P rows (mode sp_mode)
     const float* sq;        // scale of Q rows
     void* C;
@@ -79,6 +93,7 @@ struct Params {
     Problem prob[MAXP];
     int num_problems;
     int total_tiles;
+    int group_m;
     int* err;
 };
 
@@ -95,10 +110,11 @@ __device__ __forceinline__ TileCoord tile_coord(const Params<MAXP>& prm, int til
         ++p;
     const Problem& P = prm.prob[p];
     const int lt = tile - P.tile_start;
-    const int per_band = GROUP_M * P.n_blocks;
+    const int gm = prm.group_m;
+    const int per_band = gm * P.n_blocks;
     const int band = lt / per_band;
-    const int first_m = band * GROUP_M;
-    const int rows_in_band = min(P.m_blocks - first_m, GROUP_M);
+    const int first_m = band * gm;
+    const int rows_in_band = min(P.m_blocks - first_m, gm);
     const int r = lt - band * per_band;
     return {p, first_m + r % rows_in_band, r / rows_in_band};
 }
@@ -122,9 +138,9 @@ __device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_
         const float sj = (j < rows_q) ? __ldg(P.sq + (P.sq_mode ? j : 0)) : 0.0f;
         v[t] = __fmul_rn(__fmul_rn(__uint_as_float(r[t]), fi), sj);
     }
+    if (!row_ok)
+        return;
     if (!P.trans_out) {
-        if (!row_ok)
-            return;
         if (P.out_bf16) {
             __nv_bfloat16* c = static_cast<__nv_bfloat16*>(P.C) + static_cast<long long>(i) * P.ldc + j0;
             if (P.vec_store && j0 + 16 <= rows_q) {
@@ -157,8 +173,6 @@ __device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_
             }
         }
     } else {
-        if (!row_ok)
-            return;
         // C[j, i]: for a fixed j the 32 lanes write 32 consecutive i
         if (P.out_bf16) {
             __nv_bfloat16* c = static_cast<__nv_bfloat16*>(P.C) + i;
@@ -178,37 +192,40 @@ __device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_
 
 // ---------------------------------------------------------------- kernel
 
-template <int MAXP>
-__global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_constant__ Params<MAXP> prm)
+template <int MAXP, int MT>
+__global__ void __launch_bounds__(Cfg<MT>::kThreads, 1)
+    gemm_fp8_kernel(const __grid_constant__ Params<MAXP> prm)
 {
+    using C = Cfg<MT>;
+    constexpr int S = C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-    // bar[0..S) full, bar[S..2S) empty, bar[2S..2S+2) tmem_full,
-    // bar[2S+2..2S+4) tmem_empty, bar[2S+4] drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2 * STAGES + 5);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * C::kStageBytes);
+    // bar[0..S) full, bar[S..2S) empty, then kAcc tmem_full, kAcc tmem_empty,
+    // then drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2 * S + 2 * C::kAcc + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const uint32_t smem_base = smem_u32(smem);
     const uint32_t bar_base = smem_u32(bar);
     auto full_bar = [&](int s) { return bar_base + 8u * s; };
-    auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
-    auto tfull_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + b); };
-    auto tempty_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + 2 + b); };
-    const uint32_t drain_bar = bar_base + 8u * (2 * STAGES + 4);
+    auto empty_bar = [&](int s) { return bar_base + 8u * (S + s); };
+    auto tfull_bar = [&](int b) { return bar_base + 8u * (2 * S + b); };
+    auto tempty_bar = [&](int b) { return bar_base + 8u * (2 * S + C::kAcc + b); };
+    const uint32_t drain_bar = bar_base + 8u * (2 * S + 2 * C::kAcc);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < C::kAcc; ++b) {
             mbar_init(tfull_bar(b), 1);
-            mbar_init(tempty_bar(b), 128);
+            mbar_init(tempty_bar(b), 128 * MT);
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -241,8 +258,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
             for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x) {
                 const TileCoord tc = tile_coord(prm, tile);
                 const Problem& P = prm.prob[tc.p];
-                const uint32_t bytes = (P.sparse ? SP_A_BYTES + SP_META_BYTES : A_BYTES) +
-                                       static_cast<uint32_t>(P.bn) * BK;
+                const uint32_t a_bytes = P.sparse ? C::kSpABytes + MT * BM * BK / 8 : C::kABytes;
+                const uint32_t bytes = a_bytes + static_cast<uint32_t>(P.bn) * BK;
+                const int row0 = tc.m_blk * BM * MT;
                 for (int kb = 0; kb < P.k_blocks; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
                         ok = false;
@@ -250,17 +268,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
                         break;
                     }
                     mbar_arrive_expect_tx(full_bar(stage), bytes);
-                    const uint32_t sa = smem_base + stage * STAGE_BYTES;
+                    const uint32_t sa = smem_base + stage * C::kStageBytes;
                     if (P.sparse) {
-                        tma_load_2d(sa, &P.tmP, full_bar(stage), kb * (BK / 2), tc.m_blk * BM);
-                        tma_load_2d(sa + SP_A_BYTES, &P.tmE, full_bar(stage), kb * (BK / 8),
-                                    tc.m_blk * BM);
+                        tma_load_2d(sa, &P.tmP, full_bar(stage), kb * (BK / 2), row0);
+                        tma_load_2d(sa + C::kSpABytes, &P.tmE, full_bar(stage), kb * (BK / 8), row0);
                     } else {
-                        tma_load_2d(sa, &P.tmP, full_bar(stage), kb * BK, tc.m_blk * BM);
+                        tma_load_2d(sa, &P.tmP, full_bar(stage), kb * BK, row0);
                     }
-                    tma_load_2d(sa + A_BYTES, &P.tmQ, full_bar(stage), kb * BK, tc.n_blk * P.bn);
+                    tma_load_2d(sa + C::kABytes, &P.tmQ, full_bar(stage), kb * BK, tc.n_blk * P.bn);
                     armed |= 1u << stage;
-                    if (++stage == STAGES) {
+                    if (++stage == S) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -271,7 +288,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
                 // the latest arming of slot s has parity `phase` if s < stage
                 // (armed in the current round), else `phase ^ 1`
                 const volatile int never = 0;
-                for (int s = 0; s < STAGES; ++s) {
+                for (int s = 0; s < S; ++s) {
                     if (!(armed >> s & 1u))
                         continue;
                     const uint32_t last_parity = (s < stage) ? phase : (phase ^ 1u);
@@ -289,13 +306,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
             for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x, ++local) {
                 const TileCoord tc = tile_coord(prm, tile);
                 const Problem& P = prm.prob[tc.p];
-                const int acc = local & 1;
-                const uint32_t acc_phase = (local >> 1) & 1;
+                const int acc = local % C::kAcc;
+                const uint32_t acc_phase = (local / C::kAcc) & 1;
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag)) {
                     abort_pipeline(abort_flag, prm.err);
                     break;
                 }
                 tc_fence_after();
+                // half h of the tile accumulates into columns d_tmem + 256 h
                 const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN_MAX);
                 for (int kb = 0; kb < P.k_blocks; ++kb) {
                     if (!mbar_wait(full_bar(stage), phase, abort_flag)) {
@@ -304,32 +322,45 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_base + stage * STAGE_BYTES;
-                    const uint64_t bdesc = sdesc_kmajor_sw128(sa + A_BYTES);
+                    const uint32_t sa = smem_base + stage * C::kStageBytes;
+                    const uint64_t bdesc = sdesc_kmajor_sw128(sa + C::kABytes);
                     if (P.sparse) {
                         // metadata of this k-block -> TMEM slot of this stage
                         // (tcgen05.cp and the MMAs below execute in issue order)
-                        const uint32_t meta = tmem_base + static_cast<uint32_t>(META_COL0 + 4 * stage);
-                        tmem_cp_128x128b(meta, sdesc_rows16_noswizzle(sa + SP_A_BYTES));
-                        const uint64_t adesc = sdesc_kmajor_sw64(sa);
+                        const uint32_t sm_meta = sa + C::kSpABytes;
+#pragma unroll
+                        for (int h = 0; h < MT; ++h) {
+                            const uint32_t meta = tmem_base + static_cast<uint32_t>(
+                                                                  h * BN_MAX + SP_META_COL0 + 4 * stage);
+                            tmem_cp_128x128b(meta, sdesc_rows16_noswizzle(sm_meta + h * BM * 16));
+                        }
 #pragma unroll
                         for (int k = 0; k < BK / 64; ++k) {
-                            // logical K = 64 per MMA: 32 kept A bytes, 64 B bytes,
-                            // 64 metadata bits (two TMEM columns)
-                            mma_sp_f8f6f4(d_tmem, adesc + 2u * k, bdesc + 4u * k, meta + 2u * k,
-                                          P.idesc, (kb | k) != 0 ? 1u : 0u);
+#pragma unroll
+                            for (int h = 0; h < MT; ++h) {
+                                // logical K = 64 per MMA: 32 kept A bytes, 64 B
+                                // bytes, 64 metadata bits (two TMEM columns)
+                                const uint64_t adesc = sdesc_kmajor_sw64(sa + h * BM * 64);
+                                const uint32_t meta = tmem_base + static_cast<uint32_t>(
+                                                                      h * BN_MAX + SP_META_COL0 + 4 * stage);
+                                mma_sp_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 4u * k,
+                                              meta + 2u * k, P.idesc, (kb | k) != 0 ? 1u : 0u);
+                            }
                         }
                     } else {
-                        const uint64_t adesc = sdesc_kmajor_sw128(sa);
 #pragma unroll
                         for (int k = 0; k < BK / 32; ++k) {
-                            // advance the start address by 32 bytes (K = 32 codes)
-                            mma_f8f6f4(d_tmem, adesc + 2u * k, bdesc + 2u * k, P.idesc,
-                                       (kb | k) != 0 ? 1u : 0u);
+#pragma unroll
+                            for (int h = 0; h < MT; ++h) {
+                                // advance the start address by 32 bytes (K = 32 codes)
+                                const uint64_t adesc = sdesc_kmajor_sw128(sa + h * BM * BK);
+                                mma_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 2u * k,
+                                           P.idesc, (kb | k) != 0 ? 1u : 0u);
+                            }
                         }
                     }
                     mma_commit(empty_bar(stage));
-                    if (++stage == STAGES) {
+                    if (++stage == S) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -344,14 +375,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
         }
     } else {
         // ---------------------------------------------------- epilogue
+        // warp w reads TMEM lanes 32 (w % 4) .. of half (w - 2) / 4
         const int quarter = warp & 3;
-        const int row = quarter * 32 + lane;
+        const int half = (warp - 2) >> 2;
+        const int row = half * BM + quarter * 32 + lane;
         int local = 0;
         for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++local) {
             const TileCoord tc = tile_coord(prm, tile);
             const Problem& P = prm.prob[tc.p];
-            const int acc = local & 1;
-            const uint32_t acc_phase = (local >> 1) & 1;
+            const int acc = local % C::kAcc;
+            const uint32_t acc_phase = (local / C::kAcc) & 1;
             // the whole warp takes the same branch (tcgen05.ld is warp-collective)
             const bool got = mbar_wait(tfull_bar(acc), acc_phase, abort_flag);
             if (!__all_sync(0xFFFFFFFFu, got)) {
@@ -359,11 +392,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) gemm_fp8_kernel(const __grid_c
                 break;
             }
             tc_fence_after();
-            const int i = tc.m_blk * BM + row;
+            const int i = tc.m_blk * BM * MT + row;
             const bool row_ok = i < P.rows_p;
             const float fi = row_ok ? __fmul_rn(P.alpha, __ldg(P.sp + (P.sp_mode ? i : 0))) : 0.0f;
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                   static_cast<uint32_t>(acc * BN_MAX);
+                                   static_cast<uint32_t>((acc + half) * BN_MAX);
             const int jbase = tc.n_blk * P.bn;
             for (int c0 = 0; c0 < P.bn; c0 += 16) {
                 uint32_t r[16];
@@ -492,16 +525,17 @@ int validate(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, con
     return FP8_OK;
 }
 
-// Fill one problem entry.  Returns FP8_OK or an error.
-int fill_problem(Problem& pr, const Job& j, int bn)
+// Fill one problem entry for a launch with MT row-halves per tile.
+int fill_problem(Problem& pr, const Job& j, int bn, int mt)
 {
     memset(&pr, 0, sizeof(pr));
     pr.sparse = j.E != nullptr;
+    const int box_p = BM * mt;
     if (pr.sparse) {
-        if (!make_map(&pr.tmP, j.P, j.rows_p, j.K / 2, j.K / 2, BK / 2, BM, CU_TENSOR_MAP_SWIZZLE_64B) ||
-            !make_map(&pr.tmE, j.E, j.rows_p, j.K / 8, j.K / 8, BK / 8, BM, CU_TENSOR_MAP_SWIZZLE_NONE))
+        if (!make_map(&pr.tmP, j.P, j.rows_p, j.K / 2, j.K / 2, BK / 2, box_p, CU_TENSOR_MAP_SWIZZLE_64B) ||
+            !make_map(&pr.tmE, j.E, j.rows_p, j.K / 8, j.K / 8, BK / 8, box_p, CU_TENSOR_MAP_SWIZZLE_NONE))
             return FP8_ERR_CUDA;
-    } else if (!make_map(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BK, BM, CU_TENSOR_MAP_SWIZZLE_128B)) {
+    } else if (!make_map(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BK, box_p, CU_TENSOR_MAP_SWIZZLE_128B)) {
         return FP8_ERR_CUDA;
     }
     if (!make_map(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, CU_TENSOR_MAP_SWIZZLE_128B))
@@ -521,7 +555,7 @@ int fill_problem(Problem& pr, const Job& j, int bn)
     const int esz = j.out_bf16 ? 2 : 4;
     pr.vec_store = aligned16(j.C) && ((j.ldc * esz) % 16 == 0);
     pr.bn = bn;
-    pr.m_blocks = static_cast<int>((j.rows_p + BM - 1) / BM);
+    pr.m_blocks = static_cast<int>((j.rows_p + box_p - 1) / box_p);
     pr.n_blocks = static_cast<int>((j.rows_q + bn - 1) / bn);
     pr.k_blocks = static_cast<int>((j.K + BK - 1) / BK);
     pr.idesc = idesc_e4m3_f32(BM, bn, pr.sparse != 0, 0);
@@ -536,8 +570,8 @@ int write_zeros(void* C, int64_t ldc, int64_t rows, int64_t cols, int out_bf16, 
     return FP8_OK;
 }
 
-template <int MAXP>
-int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas = 0)
+template <int MAXP, int MT>
+int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas)
 {
     static std::once_flag attr_once[64];
     int dev = 0;
@@ -546,8 +580,8 @@ int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas = 0)
         return FP8_ERR_UNSUPPORTED;
     cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once[dev], [&] {
-        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MT>::kSmem);
     });
     GB_CUDA_OK(attr_err);
     int tiles = 0;
@@ -562,9 +596,47 @@ int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas = 0)
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
-    gemm_fp8_kernel<MAXP><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(prm);
+    gemm_fp8_kernel<MAXP, MT><<<grid, Cfg<MT>::kThreads, Cfg<MT>::kSmem, st>>>(prm);
     GB_CUDA_OK(cudaGetLastError());
     return FP8_OK;
+}
+
+// Tile shape of a launch: MT = 2 (256-row tiles, a third fewer operand bytes
+// per FLOP) when every problem fills 256-row tiles with a wide N tile and
+// there are at least as many such tiles as SMs; otherwise MT = 1 (more,
+// smaller tiles: skinny and small problems keep every SM busy).
+std::atomic<int> g_force_mt{0};
+std::atomic<int> g_force_group_m{0};
+
+int choose_mt(const Job* jobs, const int* bns, int n)
+{
+    const int forced = g_force_mt.load(std::memory_order_relaxed);
+    if (forced == 1 || forced == 2)
+        return forced;
+    int64_t tiles2 = 0;
+    for (int i = 0; i < n; ++i) {
+        if (jobs[i].rows_p <= BM || bns[i] < 128)
+            return 1;
+        tiles2 += ((jobs[i].rows_p + 2 * BM - 1) / (2 * BM)) * ((jobs[i].rows_q + bns[i] - 1) / bns[i]);
+    }
+    return tiles2 >= sm_count() ? 2 : 1;
+}
+
+// Fill the table for `n` jobs and launch the kernel variant that fits them.
+template <int MAXP>
+int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_ctas,
+             cudaStream_t st)
+{
+    const int mt = choose_mt(jobs, bns, n);
+    for (int i = 0; i < n; ++i) {
+        int rc = fill_problem(prm.prob[i], jobs[i], bns[i], mt);
+        if (rc != FP8_OK)
+            return rc;
+    }
+    prm.num_problems = n;
+    const int gm = g_force_group_m.load(std::memory_order_relaxed);
+    prm.group_m = gm > 0 ? gm : GROUP_M_DEFAULT;
+    return mt == 2 ? launch<MAXP, 2>(prm, st, max_ctas) : launch<MAXP, 1>(prm, st, max_ctas);
 }
 
 // Map a user-level GEMM (A [M,K], B [N,K], C [M,N] or C^T) onto (P, Q)
@@ -615,13 +687,10 @@ extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A,
         return write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
                      ldc, out_dtype, 0);
+    const int bn = pick_bn(j.rows_q, BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
-    rc = fill_problem(prm.prob[0], j, pick_bn(j.rows_q, BN_MAX));
-    if (rc != FP8_OK)
-        return rc;
-    prm.num_problems = 1;
-    return launch(prm, st);
+    return run_jobs(prm, &j, &bn, 1, 0, st);
 }
 
 extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t* a_vals,
@@ -643,13 +712,10 @@ extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t*
                               : write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, a_vals, K / 2, a_meta, B, ldb, a_scale, a_mode, b_scale, b_mode,
                      alpha, C, ldc, out_dtype, out_transposed);
+    const int bn = pick_bn(j.rows_q, SPARSE_BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
-    rc = fill_problem(prm.prob[0], j, pick_bn(j.rows_q, SPARSE_BN_MAX));
-    if (rc != FP8_OK)
-        return rc;
-    prm.num_problems = 1;
-    return launch(prm, st);
+    return run_jobs(prm, &j, &bn, 1, 0, st);
 }
 
 extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_problems,
@@ -687,6 +753,8 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
     const int bn_max = any_sparse ? SPARSE_BN_MAX : BN_MAX;
     static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
     memset(&prm, 0, sizeof(prm));
+    Job jobs[FP8_GROUPED_MAX_PROBLEMS];
+    int bns[FP8_GROUPED_MAX_PROBLEMS];
     int n = 0;
     for (int i = 0; i < num_problems; ++i) {
         const fp8_gemm_problem& g = problems[i];
@@ -700,16 +768,22 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
             continue;
         }
         const bool sp = g.A_meta != nullptr;
-        Job j = make_job(g.M, g.N, g.K, g.A, sp ? g.K / 2 : g.lda, g.A_meta, g.B, g.ldb, g.a_scale,
-                         g.a_mode, g.b_scale, g.b_mode, g.alpha, g.C, g.ldc, g.out_dtype,
-                         g.out_transposed);
-        int rc = fill_problem(prm.prob[n], j, pick_bn(j.rows_q, bn_max));
-        if (rc != FP8_OK)
-            return rc;
+        jobs[n] = make_job(g.M, g.N, g.K, g.A, sp ? g.K / 2 : g.lda, g.A_meta, g.B, g.ldb,
+                           g.a_scale, g.a_mode, g.b_scale, g.b_mode, g.alpha, g.C, g.ldc,
+                           g.out_dtype, g.out_transposed);
+        bns[n] = pick_bn(jobs[n].rows_q, bn_max);
         ++n;
     }
-    prm.num_problems = n;
     if (n == 0)
         return FP8_OK;
-    return launch(prm, st, max_ctas);
+    return run_jobs(prm, jobs, bns, n, max_ctas, st);
+}
+
+extern "C" int fp8_gemm_set_tile_config(int mt, int group_m)
+{
+    if (mt < 0 || mt > 2 || group_m < 0 || group_m > 4096)
+        return FP8_ERR_INVALID;
+    gb300::g_force_mt.store(mt);
+    gb300::g_force_group_m.store(group_m);
+    return FP8_OK;
 }

@@ -166,3 +166,24 @@ def test_grouped_equals_single_bitwise(gb, orc):
     assert gb.fp8_last_device_error() == 0
     for C, Cs in zip(outs, singles):
         assert torch.equal(C, Cs)
+
+
+@pytest.fixture()
+def tile_cfg(gb):
+    yield gb.fp8_gemm_set_tile_config
+    gb.fp8_gemm_set_tile_config(0, 0)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 256), (300, 520, 700), (1000, 1500, 1024),
+                                   (16, 1024, 512), (129, 256, 4100)])
+@pytest.mark.parametrize("gm", [0, 1, 3])
+def test_tile_configs_bitwise_equal_and_correct(gb, orc, tile_cfg, M, N, K, gm):
+    """256-row tiles (mt=2) and 128-row tiles (mt=1), any raster band height:
+    the same per-element K order, so bitwise equal results."""
+    A, dA, B, dB = _quantized(M, N, K, 1, 1, orc, seed=M + N)
+    outs = []
+    for mt in (1, 2):
+        tile_cfg(mt, gm)
+        outs.append(_gemm(gb, A, B, dA, 1, dB, 1, 1.0, gb.OUT_F32))
+    assert np.array_equal(outs[0], outs[1])
+    parity.check_fp32(outs[1], orc.gemm(A, B, dA, 1, dB, 1))

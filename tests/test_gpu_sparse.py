@@ -136,3 +136,31 @@ def test_grouped_mixed_equals_single_bitwise(gb, orc):
     assert gb.fp8_last_device_error() == 0
     for i, (C, Cs) in enumerate(zip(outs, singles)):
         assert torch.equal(C, Cs), i
+
+
+@pytest.fixture()
+def tile_cfg(gb):
+    yield gb.fp8_gemm_set_tile_config
+    gb.fp8_gemm_set_tile_config(0, 0)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 256), (300, 520, 768), (1000, 1500, 1024),
+                                   (600, 17, 4096)])
+def test_sparse_tile_configs_bitwise_equal_and_correct(gb, orc, tile_cfg, M, N, K):
+    vals, meta, dA, B, dB = _pruned(M, N, K, orc, M + 3)
+    outs = []
+    for mt in (1, 2):
+        tile_cfg(mt, 0)
+        outs.append(_sparse(gb, vals, meta, B, dA, 1, dB, 1, 1.0, gb.OUT_F32))
+    assert np.array_equal(outs[0], outs[1])
+    parity.check_fp32(outs[1], orc.gemm_sparse24(vals, meta, B, K, dA, 1, dB, 1))
+
+
+def test_sparse_small_integers_mt2_bit_exact(gb, orc, tile_cfg):
+    A = workloads.small_int_codes((384, 1024), seed=77)
+    B = workloads.small_int_codes((300, 1024), seed=78)
+    vals, meta = orc.prune24(A)
+    one = np.ones(1, np.float32)
+    tile_cfg(2, 0)
+    C = _sparse(gb, vals, meta, B, one, 0, one, 0, 1.0, gb.OUT_F32)
+    assert np.array_equal(C.astype(np.float64), orc.gemm_sparse24(vals, meta, B, 1024, one, 0, one, 0))
