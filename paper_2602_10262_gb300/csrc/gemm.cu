@@ -62,7 +62,9 @@ struct Cfg {
     static constexpr int kAcc = MT == 2 ? 1 : 2;                  // accumulator buffers
     static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
     static constexpr int kSpABytes = MT * BM * BK / 2;           // kept codes of a stage
-    static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
+    static constexpr int kEpiWarps = 4 * MT;
+    static constexpr int kEpiBytes = kEpiWarps * 32 * 128;       // 32 rows x 128 B per warp
+    static constexpr int kSmem = 1024 + kStages * kStageBytes + 256 + kEpiBytes;
     static_assert(SP_META_COL0 + 4 * kStages <= BN_MAX, "metadata ring must fit beside the accumulator");
     static_assert(kSpABytes + MT * BM * BK / 8 <= kABytes, "sparse A + metadata fit the A region");
 };
@@ -190,6 +192,84 @@ __device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_
     }
 }
 
+// Coalesced epilogue for a row-major output (trans_out == 0, 16-byte stores
+// allowed).  The warp owns 32 tile rows (TMEM lanes); per chunk of 128 bytes
+// of output columns (64 bf16 or 32 fp32) each thread scales its row's
+// accumulators, packs them and writes the 128 bytes into the warp's staging
+// buffer (16-byte pieces XOR-swizzled by row: conflict-free on both sides);
+// then 8 lanes per row copy 4 rows x 128 contiguous bytes per instruction.
+template <int ESZ>
+__device__ __forceinline__ void epilogue_rows_coalesced(const Problem& P, uint32_t taddr, int row0,
+                                                        float fi, int jbase, uint8_t* buf, int lane)
+{
+    constexpr int CW = 128 / ESZ;                     // columns per chunk
+    const int rows_q = P.rows_q;
+    for (int c0 = 0; c0 < P.bn; c0 += CW) {
+        const int cw = min(CW, P.bn - c0);           // multiple of 16
+        // column scales of the chunk: lane l holds columns c0 + l and c0 + 32 + l
+        float s_lo = 0.0f, s_hi = 0.0f;
+        {
+            const int j = jbase + c0 + lane;
+            if (j < rows_q)
+                s_lo = __ldg(P.sq + (P.sq_mode ? j : 0));
+            if (CW > 32 && j + 32 < rows_q)
+                s_hi = __ldg(P.sq + (P.sq_mode ? j + 32 : 0));
+        }
+        uint32_t packed[32];
+#pragma unroll
+        for (int q = 0; q < CW; q += 16) {
+            if (q < cw) {
+                uint32_t r[16];
+                tmem_ld_32x32b_x16(taddr + c0 + q, r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int t = 0; t < 16; t += 2) {
+                    const int c = q + t;                      // compile-time column in chunk
+                    const float s0 = __shfl_sync(0xFFFFFFFFu, c < 32 ? s_lo : s_hi, c & 31);
+                    const float s1 = __shfl_sync(0xFFFFFFFFu, c + 1 < 32 ? s_lo : s_hi, (c + 1) & 31);
+                    const float v0 = __fmul_rn(__fmul_rn(__uint_as_float(r[t]), fi), s0);
+                    const float v1 = __fmul_rn(__fmul_rn(__uint_as_float(r[t + 1]), fi), s1);
+                    if (ESZ == 2) {
+                        __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                        packed[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+                    } else {
+                        packed[c] = __float_as_uint(v0);
+                        packed[c + 1] = __float_as_uint(v1);
+                    }
+                }
+            }
+        }
+        const int nck = cw * ESZ / 16;                   // 16-byte pieces per row
+        uint8_t* my_row = buf + lane * 128;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < nck)
+                *reinterpret_cast<uint4*>(my_row + ((k ^ (lane & 7)) << 4)) =
+                    make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+        __syncwarp();
+        const int k = lane & 7;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int r = it * 4 + (lane >> 3);
+            const int gi = row0 + r;
+            if (k < nck && gi < P.rows_p) {
+                const uint4 val = *reinterpret_cast<const uint4*>(buf + r * 128 + ((k ^ (r & 7)) << 4));
+                const int gj = jbase + c0 + k * (16 / ESZ);
+                uint8_t* dst = static_cast<uint8_t*>(P.C) + (static_cast<long long>(gi) * P.ldc + gj) * ESZ;
+                if (gj + 16 / ESZ <= rows_q) {
+                    *reinterpret_cast<uint4*>(dst) = val;
+                } else {
+                    const uint8_t* src = reinterpret_cast<const uint8_t*>(&val);
+                    for (int e = 0; e < 16 / ESZ && gj + e < rows_q; ++e)
+                        for (int b = 0; b < ESZ; ++b)
+                            dst[e * ESZ + b] = src[e * ESZ + b];
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------- kernel
 
 template <int MAXP, int MT>
@@ -206,6 +286,7 @@ __global__ void __launch_bounds__(Cfg<MT>::kThreads, 1)
     // then drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2 * S + 2 * C::kAcc + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint8_t* epi_smem = smem + S * C::kStageBytes + 256;      // epilogue staging, per warp
 
     const uint32_t smem_base = smem_u32(smem);
     const uint32_t bar_base = smem_u32(bar);
@@ -398,11 +479,20 @@ __global__ void __launch_bounds__(Cfg<MT>::kThreads, 1)
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>((acc + half) * BN_MAX);
             const int jbase = tc.n_blk * P.bn;
-            for (int c0 = 0; c0 < P.bn; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld_32x32b_x16(taddr + c0, r);
-                tmem_ld_wait();
-                store_chunk16(P, i, row_ok, fi, jbase + c0, r);
+            if (!P.trans_out && P.vec_store) {
+                uint8_t* buf = epi_smem + (warp - 2) * 32 * 128;
+                const int row0 = i - lane;
+                if (P.out_bf16)
+                    epilogue_rows_coalesced<2>(P, taddr, row0, fi, jbase, buf, lane);
+                else
+                    epilogue_rows_coalesced<4>(P, taddr, row0, fi, jbase, buf, lane);
+            } else {
+                for (int c0 = 0; c0 < P.bn; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld_32x32b_x16(taddr + c0, r);
+                    tmem_ld_wait();
+                    store_chunk16(P, i, row_ok, fi, jbase + c0, r);
+                }
             }
             tc_fence_before();
             mbar_arrive(tempty_bar(acc));

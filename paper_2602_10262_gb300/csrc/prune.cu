@@ -1,10 +1,10 @@
 // 2:4 prune + compress (prune24_compress) and its inverse.
 //
-// One thread takes 32 input bytes (eight groups of four codes): two 16-byte
-// loads, a branch-free rank selection per group, one 16-byte store of the
-// kept codes and one 4-byte store of the eight metadata nibbles.  Rows whose
-// length or alignment does not allow the vector path fall back to one group
-// per iteration.  Bandwidth-bound: 1 byte read, 0.625 bytes written per
+// Vector path: a thread takes chunks of 32 input bytes (eight groups of four
+// codes): two 16-byte loads, a branch-free rank selection per group, one
+// 16-byte store of the kept codes and one 4-byte store of the eight metadata
+// nibbles.  Rows whose length or alignment does not allow it fall back to one
+// metadata byte per iteration.  Bandwidth-bound: 1 byte read, 0.625 bytes written per
 // element; no allocation, one launch.
 #include "common.cuh"
 
@@ -33,37 +33,63 @@ __device__ __forceinline__ uint32_t select_group(uint32_t w)
     return vals | ((i0 | (i1 << 2)) << 16);
 }
 
-// vec: K % 32 == 0, a 16-aligned, lda % 16 == 0, outputs 16-aligned.
-__global__ void __launch_bounds__(kThreads) prune24_kernel(const uint8_t* __restrict__ a,
-                                                           int64_t M, int64_t K, int64_t lda,
-                                                           uint8_t* __restrict__ vals,
-                                                           uint8_t* __restrict__ meta, int vec)
+// Vector path: K % 32 == 0, a 16-aligned, lda % 16 == 0, outputs 16-aligned.
+// blockIdx.y walks rows; each thread takes kChunks chunks of 32 codes spaced
+// kThreads apart in the row, issues all loads first, then selects and
+// stores (16 bytes of kept codes + 4 bytes of metadata per chunk).
+constexpr int kChunks = 4;
+
+__global__ void __launch_bounds__(kThreads) prune24_vec_kernel(const uint8_t* __restrict__ a,
+                                                               int64_t M, int64_t K, int64_t lda,
+                                                               uint8_t* __restrict__ vals,
+                                                               uint8_t* __restrict__ meta)
 {
-    const int64_t ldv = K / 2, ldm = (K + 7) / 8;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
-    const int64_t tid = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
-    if (vec) {
-        const int64_t chunks = K / 32;                  // 32 codes per thread
-        for (int64_t i = tid; i < M * chunks; i += stride) {
-            const int64_t r = i / chunks, c = i - r * chunks;
-            const uint4* src = reinterpret_cast<const uint4*>(a + r * lda + c * 32);
-            const uint4 x0 = __ldg(src), x1 = __ldg(src + 1);
-            const uint32_t w[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    const int chunks = static_cast<int>(K / 32);
+    const int64_t ldv = K / 2, ldm = K / 8;
+    const int c_first = blockIdx.x * (kThreads * kChunks) + threadIdx.x;
+    for (int64_t r = blockIdx.y; r < M; r += gridDim.y) {
+        const uint4* src = reinterpret_cast<const uint4*>(a + r * lda);
+        uint4 x[kChunks][2];
+#pragma unroll
+        for (int u = 0; u < kChunks; ++u) {
+            const int c = c_first + u * kThreads;
+            if (c < chunks) {
+                x[u][0] = __ldg(src + 2 * c);
+                x[u][1] = __ldg(src + 2 * c + 1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kChunks; ++u) {
+            const int c = c_first + u * kThreads;
+            if (c >= chunks)
+                continue;
+            const uint32_t w[8] = {x[u][0].x, x[u][0].y, x[u][0].z, x[u][0].w,
+                                   x[u][1].x, x[u][1].y, x[u][1].z, x[u][1].w};
             uint32_t v[4] = {0, 0, 0, 0};
             uint32_t nib = 0;
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
-                const uint32_t s = select_group(w[g]);
-                v[g / 2] |= (s & 0xFFFFu) << (16 * (g % 2));
-                nib |= (s >> 16) << (4 * g);
+                const uint32_t sel = select_group(w[g]);
+                v[g / 2] |= (sel & 0xFFFFu) << (16 * (g % 2));
+                nib |= (sel >> 16) << (4 * g);
             }
             *reinterpret_cast<uint4*>(vals + r * ldv + c * 16) = make_uint4(v[0], v[1], v[2], v[3]);
             *reinterpret_cast<uint32_t*>(meta + r * ldm + c * 4) = nib;
         }
-        return;
     }
-    // scalar path: one metadata byte (two groups, or one at an odd tail) per
-    // iteration so that no two threads write the same byte
+}
+
+// Scalar path (any K % 4 == 0 and any alignment): one metadata byte (two
+// groups, or one at an odd tail) per iteration so that no two threads write
+// the same byte.
+__global__ void __launch_bounds__(kThreads) prune24_kernel(const uint8_t* __restrict__ a,
+                                                           int64_t M, int64_t K, int64_t lda,
+                                                           uint8_t* __restrict__ vals,
+                                                           uint8_t* __restrict__ meta)
+{
+    const int64_t ldv = K / 2, ldm = (K + 7) / 8;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
     for (int64_t i = tid; i < M * ldm; i += stride) {
         const int64_t r = i / ldm, b = i - r * ldm;
         uint8_t out = 0;
@@ -73,10 +99,10 @@ __global__ void __launch_bounds__(kThreads) prune24_kernel(const uint8_t* __rest
                 break;
             const uint8_t* p = a + r * lda + 4 * g;
             const uint32_t w = p[0] | (p[1] << 8) | (p[2] << 16) | (static_cast<uint32_t>(p[3]) << 24);
-            const uint32_t s = select_group(w);
-            vals[r * ldv + 2 * g] = static_cast<uint8_t>(s & 0xFFu);
-            vals[r * ldv + 2 * g + 1] = static_cast<uint8_t>((s >> 8) & 0xFFu);
-            out |= static_cast<uint8_t>(((s >> 16) & 0xFu) << (4 * h));
+            const uint32_t sel = select_group(w);
+            vals[r * ldv + 2 * g] = static_cast<uint8_t>(sel & 0xFFu);
+            vals[r * ldv + 2 * g + 1] = static_cast<uint8_t>((sel >> 8) & 0xFFu);
+            out |= static_cast<uint8_t>(((sel >> 16) & 0xFu) << (4 * h));
         }
         meta[r * ldm + b] = out;
     }
@@ -131,11 +157,17 @@ extern "C" int prune24_compress(const uint8_t* a, int64_t M, int64_t K, int64_t 
         return FP8_ERR_SHAPE;
     if (!device_supported())
         return FP8_ERR_UNSUPPORTED;
-    const int vec = (K % 32 == 0) && aligned16(a) && (lda % 16 == 0) && aligned16(a_vals) &&
-                    aligned16(a_meta);
-    const int64_t items = vec ? M * (K / 32) : M * ((K + 7) / 8);
-    prune24_kernel<<<grid_for(items), kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        a, M, K, lda, a_vals, a_meta, vec);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool vec = (K % 32 == 0) && aligned16(a) && (lda % 16 == 0) && aligned16(a_vals) &&
+                     aligned16(a_meta);
+    if (vec) {
+        const int64_t chunks = K / 32;
+        const unsigned gx = static_cast<unsigned>((chunks + kThreads * kChunks - 1) / (kThreads * kChunks));
+        const unsigned gy = static_cast<unsigned>(M < 65535 ? M : 65535);
+        prune24_vec_kernel<<<dim3(gx, gy), kThreads, 0, st>>>(a, M, K, lda, a_vals, a_meta);
+    } else {
+        prune24_kernel<<<grid_for(M * ((K + 7) / 8)), kThreads, 0, st>>>(a, M, K, lda, a_vals, a_meta);
+    }
     GB_CUDA_OK(cudaGetLastError());
     return FP8_OK;
 }
