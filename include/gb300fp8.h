@@ -207,8 +207,9 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * accumulators), 2 (256 x N tiles: two MMAs share each B tile, a third fewer
  * operand bytes per FLOP), 0 = chosen per launch (2 when every problem fills
  * 256-row tiles with N tiles >= 128 wide and there are at least as many tiles
- * as SMs).  group_m: M-blocks per raster band (0 = 8).  Results do not depend
- * on either.  Affects launches enqueued after the call, from any thread. */
+ * as SMs; a launch mixing dense and sparse problems always uses 1).
+ * group_m: M-blocks per raster band (0 = 16).  Results do not depend on
+ * either.  Affects launches enqueued after the call, from any thread. */
 int fp8_gemm_set_tile_config(int mt, int group_m);
 
 /* ---------------------------------------------------------------------------

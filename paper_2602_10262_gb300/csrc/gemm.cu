@@ -38,35 +38,44 @@ constexpr int BK = 128;                   // codes per k-block (one 128-byte swi
 constexpr int BN_MAX = 256;
 constexpr int B_BYTES = BN_MAX * BK;      // 32 KB: B tile of a stage
 constexpr int TMEM_COLS = 512;
-constexpr int GROUP_M_DEFAULT = 8;        // raster: M-blocks per band
-// 2:4-sparse tiles: per stage and per 128-row half, the kept A codes (128 rows
-// x 64 bytes, 64-byte swizzle) and the metadata (128 rows x 16 bytes) share the
-// A region; the metadata is copied into a ring of TMEM columns [240, 256) of
-// that half's accumulator block (4 columns per stage), so sparse tiles use
-// N <= 240.
-constexpr int SP_META_COL0 = 240;
+constexpr int GROUP_M_DEFAULT = 16;       // raster: M-blocks per band
+// 2:4-sparse tiles: per stage the kept A codes (rows x 64 bytes, 64-byte
+// swizzle) and the metadata (rows x 16 bytes) fill the A region; the metadata
+// of each 128-row half is copied into a ring of TMEM columns beside that
+// half's accumulator (4 columns per stage).
 constexpr int SPARSE_BN_MAX = 240;
+constexpr int SPARSE_BN_MAX_MT2 = 224;
 
 // MT = 128-row MMA halves per CTA tile.
-//  MT = 1: tile 128 x bn, 4 stages of 48 KB, two accumulators (cols 0 / 256)
-//          so the epilogue of tile i overlaps the MMAs of tile i + 1;
-//  MT = 2: tile 256 x bn, 3 stages of 64 KB; two MMAs per k-step share the B
-//          tile (a third fewer operand bytes per FLOP), one accumulator
-//          spanning all 512 columns (rows 0-127 in cols 0-255, rows 128-255
-//          in cols 256-511).
-template <int MT>
+//  MT = 1: tile 128 x bn, 4 stages of 48 KB (dense and sparse problems alike),
+//          two accumulators (cols 0 / 256) so the epilogue of tile i overlaps
+//          the MMAs of tile i + 1; metadata ring at cols 240..255, bn <= 240
+//          for sparse problems;
+//  MT = 2: tile 256 x bn; two MMAs per k-step share the B tile (a third fewer
+//          operand bytes per FLOP); one accumulator spanning all 512 columns
+//          (rows 0-127 in cols 0-255, rows 128-255 in cols 256-511).  Dense
+//          launches (SP = false): 3 stages of 64 KB.  Sparse launches
+//          (SP = true): 4 stages of 48 KB (20 KB kept codes + metadata, 28 KB
+//          B with bn <= 224), metadata rings at cols 224..239 of each half.
+template <int MT, bool SP = false>
 struct Cfg {
-    static constexpr int kStages = MT == 2 ? 3 : 4;
-    static constexpr int kABytes = MT * BM * BK;                 // A region of a stage
-    static constexpr int kStageBytes = kABytes + B_BYTES;
+    static constexpr bool kSparse2 = MT == 2 && SP;
+    static constexpr int kStages = (MT == 2 && !SP) ? 3 : 4;
+    static constexpr int kABytes = MT == 1 ? BM * BK : (SP ? 2 * BM * (BK / 2 + BK / 8) : 2 * BM * BK);
+    static constexpr int kBBytes = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : B_BYTES;
+    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : SPARSE_BN_MAX;
     static constexpr int kAcc = MT == 2 ? 1 : 2;                  // accumulator buffers
     static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
     static constexpr int kSpABytes = MT * BM * BK / 2;           // kept codes of a stage
     static constexpr int kEpiWarps = 4 * MT;
     static constexpr int kEpiBytes = kEpiWarps * 32 * 128;       // 32 rows x 128 B per warp
     static constexpr int kSmem = 1024 + kStages * kStageBytes + 256 + kEpiBytes;
-    static_assert(SP_META_COL0 + 4 * kStages <= BN_MAX, "metadata ring must fit beside the accumulator");
-    static_assert(kSpABytes + MT * BM * BK / 8 <= kABytes, "sparse A + metadata fit the A region");
+    static_assert(kMetaCol0 + 4 * kStages <= BN_MAX, "metadata ring must fit beside the accumulator");
+    static_assert(kSpABytes + MT * BM * BK / 8 <= kABytes || (MT == 2 && !SP),
+                  "sparse A + metadata fit the A region");
+    static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "swizzle atoms stay aligned");
+    static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 
 struct Problem {
@@ -272,11 +281,11 @@ __device__ __forceinline__ void epilogue_rows_coalesced(const Problem& P, uint32
 
 // ---------------------------------------------------------------- kernel
 
-template <int MAXP, int MT>
-__global__ void __launch_bounds__(Cfg<MT>::kThreads, 1)
+template <int MAXP, int MT, bool SP>
+__global__ void __launch_bounds__(Cfg<MT, SP>::kThreads, 1)
     gemm_fp8_kernel(const __grid_constant__ Params<MAXP> prm)
 {
-    using C = Cfg<MT>;
+    using C = Cfg<MT, SP>;
     constexpr int S = C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -412,7 +421,7 @@ __global__ void __launch_bounds__(Cfg<MT>::kThreads, 1)
 #pragma unroll
                         for (int h = 0; h < MT; ++h) {
                             const uint32_t meta = tmem_base + static_cast<uint32_t>(
-                                                                  h * BN_MAX + SP_META_COL0 + 4 * stage);
+                                                                  h * BN_MAX + C::kMetaCol0 + 4 * stage);
                             tmem_cp_128x128b(meta, sdesc_rows16_noswizzle(sm_meta + h * BM * 16));
                         }
 #pragma unroll
@@ -423,7 +432,7 @@ __global__ void __launch_bounds__(Cfg<MT>::kThreads, 1)
                                 // bytes, 64 metadata bits (two TMEM columns)
                                 const uint64_t adesc = sdesc_kmajor_sw64(sa + h * BM * 64);
                                 const uint32_t meta = tmem_base + static_cast<uint32_t>(
-                                                                      h * BN_MAX + SP_META_COL0 + 4 * stage);
+                                                                      h * BN_MAX + C::kMetaCol0 + 4 * stage);
                                 mma_sp_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 4u * k,
                                               meta + 2u * k, P.idesc, (kb | k) != 0 ? 1u : 0u);
                             }
@@ -660,9 +669,10 @@ int write_zeros(void* C, int64_t ldc, int64_t rows, int64_t cols, int out_bf16, 
     return FP8_OK;
 }
 
-template <int MAXP, int MT>
+template <int MAXP, int MT, bool SP>
 int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas)
 {
+    using C = Cfg<MT, SP>;
     static std::once_flag attr_once[64];
     int dev = 0;
     GB_CUDA_OK(cudaGetDevice(&dev));
@@ -670,8 +680,8 @@ int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas)
         return FP8_ERR_UNSUPPORTED;
     cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once[dev], [&] {
-        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MT>::kSmem);
+        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     });
     GB_CUDA_OK(attr_err);
     int tiles = 0;
@@ -686,20 +696,26 @@ int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas)
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
-    gemm_fp8_kernel<MAXP, MT><<<grid, Cfg<MT>::kThreads, Cfg<MT>::kSmem, st>>>(prm);
+    gemm_fp8_kernel<MAXP, MT, SP><<<grid, C::kThreads, C::kSmem, st>>>(prm);
     GB_CUDA_OK(cudaGetLastError());
     return FP8_OK;
 }
 
 // Tile shape of a launch: MT = 2 (256-row tiles, a third fewer operand bytes
-// per FLOP) when every problem fills 256-row tiles with a wide N tile and
-// there are at least as many such tiles as SMs; otherwise MT = 1 (more,
-// smaller tiles: skinny and small problems keep every SM busy).
+// per FLOP) when every problem fills 256-row tiles with a wide N tile, there
+// are at least as many such tiles as SMs and the problems are all dense or
+// all sparse; otherwise MT = 1 (more, smaller tiles: skinny and small
+// problems keep every SM busy).
 std::atomic<int> g_force_mt{0};
 std::atomic<int> g_force_group_m{0};
 
 int choose_mt(const Job* jobs, const int* bns, int n)
 {
+    int n_sparse = 0;
+    for (int i = 0; i < n; ++i)
+        n_sparse += jobs[i].E != nullptr;
+    if (n_sparse != 0 && n_sparse != n)
+        return 1;                                // dense and sparse share only the MT = 1 layout
     const int forced = g_force_mt.load(std::memory_order_relaxed);
     if (forced == 1 || forced == 2)
         return forced;
@@ -714,19 +730,25 @@ int choose_mt(const Job* jobs, const int* bns, int n)
 
 // Fill the table for `n` jobs and launch the kernel variant that fits them.
 template <int MAXP>
-int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_ctas,
+int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int max_ctas,
              cudaStream_t st)
 {
-    const int mt = choose_mt(jobs, bns, n);
+    const int mt = choose_mt(jobs, bns_in, n);
+    const bool sparse = n > 0 && jobs[0].E != nullptr;     // all alike when mt == 2
     for (int i = 0; i < n; ++i) {
-        int rc = fill_problem(prm.prob[i], jobs[i], bns[i], mt);
+        int bn = bns_in[i];
+        if (mt == 2 && sparse)
+            bn = std::min(bn, SPARSE_BN_MAX_MT2);
+        int rc = fill_problem(prm.prob[i], jobs[i], bn, mt);
         if (rc != FP8_OK)
             return rc;
     }
     prm.num_problems = n;
     const int gm = g_force_group_m.load(std::memory_order_relaxed);
     prm.group_m = gm > 0 ? gm : GROUP_M_DEFAULT;
-    return mt == 2 ? launch<MAXP, 2>(prm, st, max_ctas) : launch<MAXP, 1>(prm, st, max_ctas);
+    if (mt == 1)
+        return launch<MAXP, 1, false>(prm, st, max_ctas);
+    return sparse ? launch<MAXP, 2, true>(prm, st, max_ctas) : launch<MAXP, 2, false>(prm, st, max_ctas);
 }
 
 // Map a user-level GEMM (A [M,K], B [N,K], C [M,N] or C^T) onto (P, Q)

@@ -16,19 +16,24 @@ constexpr int kThreads = 256;
 // One group of four codes (byte i of w = element i).  Element j outranks
 // element i when key_j > key_i, or key_j == key_i and j < i (key = code &
 // 0x7F).  The two elements outranked by fewer than two others are kept.
-// Returns the two kept codes in the low 16 bits (lower index first) and the
-// nibble i0 | i1 << 2 in bits 16..19.
+// Byte-parallel: rotating the keys by d = 1, 2, 3 places key_{(i+d)%4} in
+// byte i; (i + d) % 4 < i exactly for the bytes of tie_d.  Returns the two
+// kept codes in the low 16 bits (lower index first) and the nibble
+// i0 | i1 << 2 in bits 16..19.
 __device__ __forceinline__ uint32_t select_group(uint32_t w)
 {
-    const uint32_t k0 = w & 0x7Fu, k1 = (w >> 8) & 0x7Fu, k2 = (w >> 16) & 0x7Fu,
-                   k3 = (w >> 24) & 0x7Fu;
-    const uint32_t r0 = (k1 > k0) + (k2 > k0) + (k3 > k0);
-    const uint32_t r1 = (k0 >= k1) + (k2 > k1) + (k3 > k1);
-    const uint32_t r2 = (k0 >= k2) + (k1 >= k2) + (k3 > k2);
-    const uint32_t r3 = (k0 >= k3) + (k1 >= k3) + (k2 >= k3);
-    const uint32_t keep = (r0 < 2u) | ((r1 < 2u) << 1) | ((r2 < 2u) << 2) | ((r3 < 2u) << 3);
-    const uint32_t i0 = __ffs(keep) - 1;
-    const uint32_t i1 = 31 - __clz(keep);
+    const uint32_t k = w & 0x7F7F7F7Fu;
+    const uint32_t r1 = __byte_perm(k, 0u, 0x0321);
+    const uint32_t r2 = __byte_perm(k, 0u, 0x1032);
+    const uint32_t r3 = __byte_perm(k, 0u, 0x2103);
+    const uint32_t o1 = __vcmpgtu4(r1, k) | (__vcmpeq4(r1, k) & 0xFF000000u);
+    const uint32_t o2 = __vcmpgtu4(r2, k) | (__vcmpeq4(r2, k) & 0xFFFF0000u);
+    const uint32_t o3 = __vcmpgtu4(r3, k) | (__vcmpeq4(r3, k) & 0xFFFFFF00u);
+    const uint32_t rank = (o1 & 0x01010101u) + (o2 & 0x01010101u) + (o3 & 0x01010101u);
+    const uint32_t keep = __vcmpltu4(rank, 0x02020202u);               // 0xFF per kept byte
+    const uint32_t bits = ((keep & 0x08040201u) * 0x01010101u) >> 24;  // kept byte i -> bit i
+    const uint32_t i0 = __ffs(bits) - 1;
+    const uint32_t i1 = 31 - __clz(bits);
     const uint32_t vals = __byte_perm(w, 0u, i0 | (i1 << 4)) & 0xFFFFu;
     return vals | ((i0 | (i1 << 2)) << 16);
 }
