@@ -1,8 +1,8 @@
 // 2:4 prune + compress (prune24_compress) and its inverse.
 //
-// Vector path: a thread takes chunks of 32 input bytes (eight groups of four
-// codes): two 16-byte loads, a branch-free rank selection per group, one
-// 16-byte store of the kept codes and one 4-byte store of the eight metadata
+// Vector path: a thread takes pieces of 16 input bytes (four groups of four
+// codes): one 16-byte load, a branch-free rank selection per group, an
+// 8-byte store of the kept codes and a 2-byte store of the four metadata
 // nibbles.  Rows whose length or alignment does not allow it fall back to one
 // metadata byte per iteration.  Bandwidth-bound: 1 byte read, 0.625 bytes written per
 // element; no allocation, one launch.
@@ -38,48 +38,41 @@ __device__ __forceinline__ uint32_t select_group(uint32_t w)
     return vals | ((i0 | (i1 << 2)) << 16);
 }
 
-// Vector path: K % 32 == 0, a 16-aligned, lda % 16 == 0, outputs 16-aligned.
-// blockIdx.y walks rows; each thread takes kChunks chunks of 32 codes spaced
-// kThreads apart in the row, issues all loads first, then selects and
-// stores (16 bytes of kept codes + 4 bytes of metadata per chunk).
-constexpr int kChunks = 4;
+// Vector path: K % 16 == 0, a 16-aligned with lda % 16 == 0, vals 8-aligned,
+// meta 2-aligned.  blockIdx.y walks rows.  A thread takes kPieces pieces of
+// 16 codes (four groups) spaced kThreads apart, so each load instruction of
+// a warp reads 512 contiguous bytes; all loads are issued before any
+// selection.  Per piece: 8 bytes of kept codes and 16 bits of metadata.
+constexpr int kPieces = 4;
 
 __global__ void __launch_bounds__(kThreads) prune24_vec_kernel(const uint8_t* __restrict__ a,
                                                                int64_t M, int64_t K, int64_t lda,
                                                                uint8_t* __restrict__ vals,
                                                                uint8_t* __restrict__ meta)
 {
-    const int chunks = static_cast<int>(K / 32);
+    const int pieces = static_cast<int>(K / 16);
     const int64_t ldv = K / 2, ldm = K / 8;
-    const int c_first = blockIdx.x * (kThreads * kChunks) + threadIdx.x;
+    const int p_first = blockIdx.x * (kThreads * kPieces) + threadIdx.x;
     for (int64_t r = blockIdx.y; r < M; r += gridDim.y) {
         const uint4* src = reinterpret_cast<const uint4*>(a + r * lda);
-        uint4 x[kChunks][2];
+        uint4 x[kPieces];
 #pragma unroll
-        for (int u = 0; u < kChunks; ++u) {
-            const int c = c_first + u * kThreads;
-            if (c < chunks) {
-                x[u][0] = __ldg(src + 2 * c);
-                x[u][1] = __ldg(src + 2 * c + 1);
-            }
+        for (int u = 0; u < kPieces; ++u) {
+            const int p = p_first + u * kThreads;
+            if (p < pieces)
+                x[u] = __ldg(src + p);
         }
 #pragma unroll
-        for (int u = 0; u < kChunks; ++u) {
-            const int c = c_first + u * kThreads;
-            if (c >= chunks)
+        for (int u = 0; u < kPieces; ++u) {
+            const int p = p_first + u * kThreads;
+            if (p >= pieces)
                 continue;
-            const uint32_t w[8] = {x[u][0].x, x[u][0].y, x[u][0].z, x[u][0].w,
-                                   x[u][1].x, x[u][1].y, x[u][1].z, x[u][1].w};
-            uint32_t v[4] = {0, 0, 0, 0};
-            uint32_t nib = 0;
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const uint32_t sel = select_group(w[g]);
-                v[g / 2] |= (sel & 0xFFFFu) << (16 * (g % 2));
-                nib |= (sel >> 16) << (4 * g);
-            }
-            *reinterpret_cast<uint4*>(vals + r * ldv + c * 16) = make_uint4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<uint32_t*>(meta + r * ldm + c * 4) = nib;
+            const uint32_t s0 = select_group(x[u].x), s1 = select_group(x[u].y);
+            const uint32_t s2 = select_group(x[u].z), s3 = select_group(x[u].w);
+            const uint2 v = make_uint2((s0 & 0xFFFFu) | (s1 << 16), (s2 & 0xFFFFu) | (s3 << 16));
+            const uint32_t nib = (s0 >> 16) | ((s1 >> 16) << 4) | ((s2 >> 16) << 8) | ((s3 >> 16) << 12);
+            *reinterpret_cast<uint2*>(vals + r * ldv + p * 8) = v;
+            *reinterpret_cast<uint16_t*>(meta + r * ldm + p * 2) = static_cast<uint16_t>(nib);
         }
     }
 }
@@ -163,11 +156,12 @@ extern "C" int prune24_compress(const uint8_t* a, int64_t M, int64_t K, int64_t 
     if (!device_supported())
         return FP8_ERR_UNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const bool vec = (K % 32 == 0) && aligned16(a) && (lda % 16 == 0) && aligned16(a_vals) &&
-                     aligned16(a_meta);
+    const bool vec = (K % 16 == 0) && aligned16(a) && (lda % 16 == 0) &&
+                     (reinterpret_cast<uintptr_t>(a_vals) % 8 == 0) &&
+                     (reinterpret_cast<uintptr_t>(a_meta) % 2 == 0);
     if (vec) {
-        const int64_t chunks = K / 32;
-        const unsigned gx = static_cast<unsigned>((chunks + kThreads * kChunks - 1) / (kThreads * kChunks));
+        const int64_t pieces = K / 16;
+        const unsigned gx = static_cast<unsigned>((pieces + kThreads * kPieces - 1) / (kThreads * kPieces));
         const unsigned gy = static_cast<unsigned>(M < 65535 ? M : 65535);
         prune24_vec_kernel<<<dim3(gx, gy), kThreads, 0, st>>>(a, M, K, lda, a_vals, a_meta);
     } else {

@@ -23,7 +23,8 @@ def _ties(a):
     return a
 
 
-@pytest.mark.parametrize("shape", [(1, 4), (3, 36), (7, 1028), (128, 256), (257, 4096), (64, 100)])
+@pytest.mark.parametrize("shape", [(1, 4), (3, 36), (5, 48), (7, 1028), (33, 1040), (128, 256),
+                                   (257, 4096), (64, 100), (2, 16)])
 def test_parity(gb, orc, shape):
     a = _ties(workloads.random_codes(shape, seed=shape[1]))
     v, m = gb.prune24_compress(torch.from_numpy(a).cuda())
