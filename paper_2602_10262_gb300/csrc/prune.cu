@@ -15,25 +15,22 @@ constexpr int kThreads = 256;
 
 // One group of four codes (byte i of w = element i).  Element j outranks
 // element i when key_j > key_i, or key_j == key_i and j < i (key = code &
-// 0x7F).  The two elements outranked by fewer than two others are kept.
-// Byte-parallel: rotating the keys by d = 1, 2, 3 places key_{(i+d)%4} in
-// byte i; (i + d) % 4 < i exactly for the bytes of tie_d.  Returns the two
-// kept codes in the low 16 bits (lower index first) and the nibble
-// i0 | i1 << 2 in bits 16..19.
+// 0x7F); the two highest-ranked elements are kept.  score_i = key_i * 4 +
+// (3 - i) orders the elements exactly that way and makes every score
+// distinct, so the kept pair is the top two of four scores: a two-round
+// max/min tournament.  Returns the two kept codes in the low 16 bits (lower
+// index first) and the nibble i0 | i1 << 2 in bits 16..19.
 __device__ __forceinline__ uint32_t select_group(uint32_t w)
 {
-    const uint32_t k = w & 0x7F7F7F7Fu;
-    const uint32_t r1 = __byte_perm(k, 0u, 0x0321);
-    const uint32_t r2 = __byte_perm(k, 0u, 0x1032);
-    const uint32_t r3 = __byte_perm(k, 0u, 0x2103);
-    const uint32_t o1 = __vcmpgtu4(r1, k) | (__vcmpeq4(r1, k) & 0xFF000000u);
-    const uint32_t o2 = __vcmpgtu4(r2, k) | (__vcmpeq4(r2, k) & 0xFFFF0000u);
-    const uint32_t o3 = __vcmpgtu4(r3, k) | (__vcmpeq4(r3, k) & 0xFFFFFF00u);
-    const uint32_t rank = (o1 & 0x01010101u) + (o2 & 0x01010101u) + (o3 & 0x01010101u);
-    const uint32_t keep = __vcmpltu4(rank, 0x02020202u);               // 0xFF per kept byte
-    const uint32_t bits = ((keep & 0x08040201u) * 0x01010101u) >> 24;  // kept byte i -> bit i
-    const uint32_t i0 = __ffs(bits) - 1;
-    const uint32_t i1 = 31 - __clz(bits);
+    const uint32_t s0 = ((w << 2) & 0x1FCu) | 3u;
+    const uint32_t s1 = ((w >> 6) & 0x1FCu) | 2u;
+    const uint32_t s2 = ((w >> 14) & 0x1FCu) | 1u;
+    const uint32_t s3 = (w >> 22) & 0x1FCu;
+    const uint32_t a = max(s0, s1), b = min(s0, s1), c = max(s2, s3), d = min(s2, s3);
+    const uint32_t t1 = max(a, c);
+    const uint32_t t2 = max(min(a, c), max(b, d));
+    const uint32_t i0 = 3u - max(t1 & 3u, t2 & 3u);
+    const uint32_t i1 = 3u - min(t1 & 3u, t2 & 3u);
     const uint32_t vals = __byte_perm(w, 0u, i0 | (i1 << 4)) & 0xFFFFu;
     return vals | ((i0 | (i1 << 2)) << 16);
 }
