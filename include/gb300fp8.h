@@ -212,6 +212,45 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * either.  Affects launches enqueued after the call, from any thread. */
 int fp8_gemm_set_tile_config(int mt, int group_m);
 
+/* Autotuner: times every candidate tile configuration (mt in {1, 2}, raster
+ * band group_m in {2, 4, 8, 16, 32}) of this exact problem list on `stream`
+ * (iters timed launches each, after one warm-up; the problems' outputs are
+ * written each time), records the fastest in the process-wide tile cache
+ * under the list's shape signature (sizes, dense/sparse, output type and
+ * layout, max_ctas) and returns it.  Later launches with the same signature
+ * (grouped or single calls) use the cached choice unless
+ * fp8_gemm_set_tile_config forces one.  Synchronises `stream`. */
+typedef struct {
+    int mt;
+    int group_m;
+    float ms_per_launch;
+} fp8_tile_config;
+
+int gemm_fp8_grouped_autotune(const fp8_gemm_problem *problems, int num_problems, int max_ctas,
+                              int iters, fp8_stream_t stream, fp8_tile_config *best);
+
+/* Persist / restore / empty the tile cache (a text file, one signature per
+ * line).  Loading merges into the current cache; a malformed file changes
+ * nothing and returns FP8_ERR_INVALID. */
+int gemm_fp8_tune_cache_save(const char *path);
+int gemm_fp8_tune_cache_load(const char *path);
+int gemm_fp8_tune_cache_clear(void);
+
+/* CUDA-graph form of a grouped launch.  create builds a one-node graph for
+ * the problem list (every problem needs K > 0; FP8_ERR_SHAPE otherwise);
+ * update swaps in a list with the same shape signature (new pointers,
+ * scales, alpha) by rewriting the kernel node's parameters, without
+ * re-capturing (FP8_ERR_SHAPE if the signature differs); launch replays it
+ * on a stream.  The graph holds no pointer to the caller's problem array. */
+typedef struct fp8_grouped_graph fp8_grouped_graph;
+
+int gemm_fp8_grouped_graph_create(const fp8_gemm_problem *problems, int num_problems, int max_ctas,
+                                  fp8_grouped_graph **out);
+int gemm_fp8_grouped_graph_update(fp8_grouped_graph *graph, const fp8_gemm_problem *problems,
+                                  int num_problems);
+int gemm_fp8_grouped_graph_launch(fp8_grouped_graph *graph, fp8_stream_t stream);
+int gemm_fp8_grouped_graph_destroy(fp8_grouped_graph *graph);
+
 /* ---------------------------------------------------------------------------
  * Request server (row a8): continuous batching of FP8 GEMM requests.
  * Paper: sections 5 and 6.2 (concurrent GEMMs on separate hardware queues:

@@ -19,7 +19,9 @@ from . import _lib
 __all__ = [
     "Fp8Error", "library", "fp8_quantize_e4m3", "prune24_compress", "prune24_decompress",
     "gemm_fp8_dense", "gemm_fp8_sparse24", "gemm_fp8_grouped", "fp8_last_device_error",
-    "fp8_device_sm_count", "fp8_gemm_set_tile_config", "OUT_F32", "OUT_BF16",
+    "fp8_device_sm_count", "fp8_gemm_set_tile_config", "gemm_fp8_grouped_autotune",
+    "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
+    "GroupedGraph", "OUT_F32", "OUT_BF16",
 ]
 
 OUT_F32 = 0
@@ -192,3 +194,59 @@ def gemm_fp8_grouped(problems: Sequence[_lib.FP8Problem], stream=None) -> None:
     arr = (_lib.FP8Problem * len(problems))(*problems)
     rc = library().gemm_fp8_grouped(arr, len(problems), _stream(stream))
     _check(rc, "gemm_fp8_grouped")
+
+
+def gemm_fp8_grouped_autotune(problems: Sequence[_lib.FP8Problem], max_ctas: int = 0,
+                              iters: int = 3, stream=None) -> dict:
+    """Time every tile configuration for this problem list, cache the fastest
+    and return it as {"mt", "group_m", "ms_per_launch"}."""
+    arr = (_lib.FP8Problem * len(problems))(*problems)
+    best = _lib.FP8TileConfig()
+    rc = library().gemm_fp8_grouped_autotune(arr, len(problems), int(max_ctas), int(iters),
+                                             _stream(stream), ctypes.byref(best))
+    _check(rc, "gemm_fp8_grouped_autotune")
+    return {"mt": best.mt, "group_m": best.group_m, "ms_per_launch": best.ms_per_launch}
+
+
+def gemm_fp8_tune_cache_save(path: str) -> None:
+    _check(library().gemm_fp8_tune_cache_save(path.encode()), "gemm_fp8_tune_cache_save")
+
+
+def gemm_fp8_tune_cache_load(path: str) -> None:
+    _check(library().gemm_fp8_tune_cache_load(path.encode()), "gemm_fp8_tune_cache_load")
+
+
+def gemm_fp8_tune_cache_clear() -> None:
+    _check(library().gemm_fp8_tune_cache_clear(), "gemm_fp8_tune_cache_clear")
+
+
+class GroupedGraph:
+    """A grouped launch captured as a CUDA graph (gemm_fp8_grouped_graph_*)."""
+
+    def __init__(self, problems: Sequence[_lib.FP8Problem], max_ctas: int = 0):
+        self.lib = library()
+        arr = (_lib.FP8Problem * len(problems))(*problems)
+        h = ctypes.c_void_p()
+        _check(self.lib.gemm_fp8_grouped_graph_create(arr, len(problems), int(max_ctas),
+                                                      ctypes.byref(h)), "gemm_fp8_grouped_graph_create")
+        self.h = h
+
+    def update(self, problems: Sequence[_lib.FP8Problem]) -> None:
+        arr = (_lib.FP8Problem * len(problems))(*problems)
+        _check(self.lib.gemm_fp8_grouped_graph_update(self.h, arr, len(problems)),
+               "gemm_fp8_grouped_graph_update")
+
+    def launch(self, stream=None) -> None:
+        _check(self.lib.gemm_fp8_grouped_graph_launch(self.h, _stream(stream)),
+               "gemm_fp8_grouped_graph_launch")
+
+    def close(self) -> None:
+        if self.h:
+            self.lib.gemm_fp8_grouped_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

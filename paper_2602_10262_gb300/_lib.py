@@ -41,6 +41,11 @@ class FP8QuantJob(ctypes.Structure):
                 ("dequant_scale", P)]
 
 
+class FP8TileConfig(ctypes.Structure):
+    """Mirror of ``fp8_tile_config``."""
+    _fields_ = [("mt", I32), ("group_m", I32), ("ms_per_launch", F32)]
+
+
 class FP8ServerConfig(ctypes.Structure):
     """Mirror of ``fp8_server_config``."""
     _fields_ = [("num_tenants", I32), ("latency_tenant", I32), ("batching", I32),
@@ -82,6 +87,15 @@ SIGNATURES = {
     "gemm_fp8_grouped_ex": (I32, [ctypes.POINTER(FP8Problem), I32, I32, P]),
     "fp8_quantize_e4m3_rows_grouped": (I32, [ctypes.POINTER(FP8QuantJob), I32, P]),
     "fp8_gemm_set_tile_config": (I32, [I32, I32]),
+    "gemm_fp8_grouped_autotune": (I32, [ctypes.POINTER(FP8Problem), I32, I32, I32, P,
+                                        ctypes.POINTER(FP8TileConfig)]),
+    "gemm_fp8_tune_cache_save": (I32, [ctypes.c_char_p]),
+    "gemm_fp8_tune_cache_load": (I32, [ctypes.c_char_p]),
+    "gemm_fp8_tune_cache_clear": (I32, []),
+    "gemm_fp8_grouped_graph_create": (I32, [ctypes.POINTER(FP8Problem), I32, I32, ctypes.POINTER(P)]),
+    "gemm_fp8_grouped_graph_update": (I32, [P, ctypes.POINTER(FP8Problem), I32]),
+    "gemm_fp8_grouped_graph_launch": (I32, [P, P]),
+    "gemm_fp8_grouped_graph_destroy": (I32, [P]),
     "fp8_server_create": (I32, [ctypes.POINTER(FP8ServerConfig), ctypes.POINTER(P)]),
     "fp8_server_create_simulated": (I32, [ctypes.POINTER(FP8ServerConfig), ctypes.c_double,
                                           ctypes.c_double, I32, ctypes.POINTER(P)]),

@@ -22,10 +22,14 @@
 // is written transposed.
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <map>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "ptx.cuh"
@@ -669,8 +673,14 @@ int write_zeros(void* C, int64_t ldc, int64_t rows, int64_t cols, int out_bf16, 
     return FP8_OK;
 }
 
+// Kernel variant, grid and shared memory of one launch.
+struct Plan {
+    const void* func = nullptr;
+    int grid = 0, threads = 0, smem = 0;
+};
+
 template <int MAXP, int MT, bool SP>
-int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas)
+int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
 {
     using C = Cfg<MT, SP>;
     static std::once_flag attr_once[64];
@@ -690,65 +700,137 @@ int launch(Params<MAXP>& prm, cudaStream_t st, int max_ctas)
         tiles += prm.prob[p].m_blocks * prm.prob[p].n_blocks;
     }
     prm.total_tiles = tiles;
-    if (tiles == 0)
-        return FP8_OK;
     prm.err = device_error_word();
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
-    gemm_fp8_kernel<MAXP, MT, SP><<<grid, C::kThreads, C::kSmem, st>>>(prm);
-    GB_CUDA_OK(cudaGetLastError());
+    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP>);
+    out->grid = grid;
+    out->threads = C::kThreads;
+    out->smem = C::kSmem;
     return FP8_OK;
 }
 
-// Tile shape of a launch: MT = 2 (256-row tiles, a third fewer operand bytes
-// per FLOP) when every problem fills 256-row tiles with a wide N tile, there
-// are at least as many such tiles as SMs and the problems are all dense or
-// all sparse; otherwise MT = 1 (more, smaller tiles: skinny and small
-// problems keep every SM busy).
+template <int MAXP>
+int launch_plan(Params<MAXP>& prm, const Plan& pl, cudaStream_t st)
+{
+    if (pl.grid == 0)
+        return FP8_OK;
+    void* args[] = {&prm};
+    GB_CUDA_OK(cudaLaunchKernel(pl.func, dim3(pl.grid), dim3(pl.threads), args,
+                                static_cast<size_t>(pl.smem), st));
+    return FP8_OK;
+}
+
+// ---------------------------------------------------------------- tile choice
+
 std::atomic<int> g_force_mt{0};
 std::atomic<int> g_force_group_m{0};
 
-int choose_mt(const Job* jobs, const int* bns, int n)
+struct TileChoice {
+    int mt = 0;        // 0: not set
+    int group_m = 0;
+};
+
+// Shape signature of a launch: what the best tile choice depends on.
+std::vector<int64_t> signature(const Job* jobs, const int* bns, int n, int max_ctas)
 {
-    int n_sparse = 0;
-    for (int i = 0; i < n; ++i)
-        n_sparse += jobs[i].E != nullptr;
-    if (n_sparse != 0 && n_sparse != n)
-        return 1;                                // dense and sparse share only the MT = 1 layout
-    const int forced = g_force_mt.load(std::memory_order_relaxed);
-    if (forced == 1 || forced == 2)
-        return forced;
-    int64_t tiles2 = 0;
+    std::vector<int64_t> k;
+    k.reserve(2 + 7 * n);
+    k.push_back(n);
+    k.push_back(max_ctas);
     for (int i = 0; i < n; ++i) {
-        if (jobs[i].rows_p <= BM || bns[i] < 128)
-            return 1;
-        tiles2 += ((jobs[i].rows_p + 2 * BM - 1) / (2 * BM)) * ((jobs[i].rows_q + bns[i] - 1) / bns[i]);
+        const Job& j = jobs[i];
+        k.insert(k.end(), {j.rows_p, j.rows_q, j.K, j.E != nullptr, bns[i], j.out_bf16, j.trans_out});
     }
-    return tiles2 >= sm_count() ? 2 : 1;
+    return k;
 }
 
-// Fill the table for `n` jobs and launch the kernel variant that fits them.
-template <int MAXP>
-int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int max_ctas,
-             cudaStream_t st)
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, TileChoice> g_tuned;
+
+bool mixed_kinds(const Job* jobs, int n)
 {
-    const int mt = choose_mt(jobs, bns_in, n);
+    for (int i = 1; i < n; ++i)
+        if ((jobs[i].E != nullptr) != (jobs[0].E != nullptr))
+            return true;
+    return false;
+}
+
+// Tile shape of a launch, in order of precedence: an explicit choice (the
+// autotuner's candidates), the process-wide override, the autotuner's cached
+// winner for this shape signature, the heuristic.  Heuristic: MT = 2
+// (256-row tiles, a third fewer operand bytes per FLOP) when every problem
+// fills 256-row tiles with a wide N tile, there are at least as many such
+// tiles as SMs and the problems are all dense or all sparse; otherwise MT = 1
+// (more, smaller tiles keep every SM busy on skinny and small problems).
+// Dense and sparse problems share only the MT = 1 layout.
+TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const TileChoice* expl)
+{
+    TileChoice c;
+    if (expl && expl->mt) {
+        c = *expl;
+    } else {
+        c.mt = g_force_mt.load(std::memory_order_relaxed);
+        c.group_m = g_force_group_m.load(std::memory_order_relaxed);
+        if (c.mt == 0) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tuned.find(signature(jobs, bns, n, max_ctas));
+            if (it != g_tuned.end()) {
+                c.mt = it->second.mt;
+                if (c.group_m == 0)
+                    c.group_m = it->second.group_m;
+            }
+        }
+        if (c.mt == 0) {
+            int64_t tiles2 = 0;
+            bool ok2 = true;
+            for (int i = 0; i < n && ok2; ++i) {
+                if (jobs[i].rows_p <= BM || bns[i] < 128)
+                    ok2 = false;
+                tiles2 += ((jobs[i].rows_p + 2 * BM - 1) / (2 * BM)) * ((jobs[i].rows_q + bns[i] - 1) / bns[i]);
+            }
+            c.mt = ok2 && tiles2 >= sm_count() ? 2 : 1;
+        }
+    }
+    if (mixed_kinds(jobs, n))
+        c.mt = 1;
+    if (c.group_m <= 0)
+        c.group_m = GROUP_M_DEFAULT;
+    return c;
+}
+
+// Fill the table for `n` jobs and plan the kernel variant that fits them.
+template <int MAXP>
+int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int max_ctas,
+               const TileChoice* expl, Plan* pl)
+{
+    const TileChoice c = choose(jobs, bns_in, n, max_ctas, expl);
     const bool sparse = n > 0 && jobs[0].E != nullptr;     // all alike when mt == 2
     for (int i = 0; i < n; ++i) {
         int bn = bns_in[i];
-        if (mt == 2 && sparse)
+        if (c.mt == 2 && sparse)
             bn = std::min(bn, SPARSE_BN_MAX_MT2);
-        int rc = fill_problem(prm.prob[i], jobs[i], bn, mt);
+        int rc = fill_problem(prm.prob[i], jobs[i], bn, c.mt);
         if (rc != FP8_OK)
             return rc;
     }
     prm.num_problems = n;
-    const int gm = g_force_group_m.load(std::memory_order_relaxed);
-    prm.group_m = gm > 0 ? gm : GROUP_M_DEFAULT;
-    if (mt == 1)
-        return launch<MAXP, 1, false>(prm, st, max_ctas);
-    return sparse ? launch<MAXP, 2, true>(prm, st, max_ctas) : launch<MAXP, 2, false>(prm, st, max_ctas);
+    prm.group_m = c.group_m;
+    if (c.mt == 1)
+        return plan<MAXP, 1, false>(prm, max_ctas, pl);
+    return sparse ? plan<MAXP, 2, true>(prm, max_ctas, pl) : plan<MAXP, 2, false>(prm, max_ctas, pl);
+}
+
+template <int MAXP>
+int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_ctas,
+             cudaStream_t st, const TileChoice* expl = nullptr)
+{
+    Plan pl;
+    int rc = build_plan(prm, jobs, bns, n, max_ctas, expl, &pl);
+    if (rc != FP8_OK)
+        return rc;
+    return launch_plan(prm, pl, st);
 }
 
 // Map a user-level GEMM (A [M,K], B [N,K], C [M,N] or C^T) onto (P, Q)
@@ -836,10 +918,15 @@ extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_proble
     return gemm_fp8_grouped_ex(problems, num_problems, 0, stream);
 }
 
-extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_problems,
-                                   int max_ctas, fp8_stream_t stream)
+namespace gb300 {
+namespace {
+
+// Validate a problem list and turn it into jobs.  K == 0 problems are written
+// as zeros on `st` (when `zeros_ok`) or rejected.  *n_out: jobs produced.
+int grouped_jobs(const fp8_gemm_problem* problems, int num_problems, cudaStream_t st,
+                 bool zeros_ok, Job* jobs, int* bns, int* n_out)
 {
-    using namespace gb300;
+    *n_out = 0;
     if (num_problems < 0 || (num_problems > 0 && !problems))
         return FP8_ERR_INVALID;
     if (num_problems > FP8_GROUPED_MAX_PROBLEMS)
@@ -853,20 +940,17 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
                           g.out_transposed);
         if (rc != FP8_OK)
             return rc;
+        if (!zeros_ok && g.M > 0 && g.N > 0 && g.K == 0)
+            return FP8_ERR_SHAPE;
         any_sparse |= sp && g.M > 0 && g.N > 0 && g.K > 0;
     }
     if (num_problems == 0)
         return FP8_OK;
     if (!device_supported())
         return FP8_ERR_UNSUPPORTED;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // a launch holding a sparse problem keeps TMEM columns [240, 256) for the
-    // metadata ring, so every tile in it has N <= 240
+    // a launch holding a sparse problem keeps TMEM columns beside the
+    // accumulators for the metadata ring, so every tile in it has N <= 240
     const int bn_max = any_sparse ? SPARSE_BN_MAX : BN_MAX;
-    static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
-    memset(&prm, 0, sizeof(prm));
-    Job jobs[FP8_GROUPED_MAX_PROBLEMS];
-    int bns[FP8_GROUPED_MAX_PROBLEMS];
     int n = 0;
     for (int i = 0; i < num_problems; ++i) {
         const fp8_gemm_problem& g = problems[i];
@@ -886,9 +970,283 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
         bns[n] = pick_bn(jobs[n].rows_q, bn_max);
         ++n;
     }
+    *n_out = n;
+    return FP8_OK;
+}
+
+}  // namespace
+}  // namespace gb300
+
+extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_problems,
+                                   int max_ctas, fp8_stream_t stream)
+{
+    using namespace gb300;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Job jobs[FP8_GROUPED_MAX_PROBLEMS];
+    int bns[FP8_GROUPED_MAX_PROBLEMS];
+    int n = 0;
+    int rc = grouped_jobs(problems, num_problems, st, true, jobs, bns, &n);
+    if (rc != FP8_OK || n == 0)
+        return rc;
+    static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
+    memset(&prm, 0, sizeof(prm));
+    return run_jobs(prm, jobs, bns, n, max_ctas, st);
+}
+
+extern "C" int gemm_fp8_grouped_autotune(const fp8_gemm_problem* problems, int num_problems,
+                                         int max_ctas, int iters, fp8_stream_t stream,
+                                         fp8_tile_config* best)
+{
+    using namespace gb300;
+    if (iters <= 0)
+        return FP8_ERR_INVALID;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Job jobs[FP8_GROUPED_MAX_PROBLEMS];
+    int bns[FP8_GROUPED_MAX_PROBLEMS];
+    int n = 0;
+    int rc = grouped_jobs(problems, num_problems, st, true, jobs, bns, &n);
+    if (rc != FP8_OK)
+        return rc;
     if (n == 0)
         return FP8_OK;
-    return run_jobs(prm, jobs, bns, n, max_ctas, st);
+    static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GB_CUDA_OK(cudaEventCreate(&e0));
+    GB_CUDA_OK(cudaEventCreate(&e1));
+    TileChoice winner;
+    float best_ms = 0.0f;
+    const int mts[2] = {1, 2};
+    const int gms[5] = {2, 4, 8, 16, 32};
+    for (int mt : mts) {
+        if (mt == 2 && mixed_kinds(jobs, n))
+            continue;
+        for (int gm : gms) {
+            TileChoice c;
+            c.mt = mt;
+            c.group_m = gm;
+            memset(&prm, 0, sizeof(prm));
+            rc = run_jobs(prm, jobs, bns, n, max_ctas, st, &c);            // warm-up
+            for (int it = 0; rc == FP8_OK && it < iters; ++it) {
+                if (it == 0 && cudaEventRecord(e0, st) != cudaSuccess)
+                    rc = FP8_ERR_CUDA;
+                if (rc == FP8_OK)
+                    rc = run_jobs(prm, jobs, bns, n, max_ctas, st, &c);
+            }
+            float ms = 0.0f;
+            if (rc == FP8_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                 cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = FP8_ERR_CUDA;
+            if (rc != FP8_OK)
+                break;
+            if (winner.mt == 0 || ms < best_ms) {
+                winner = c;
+                best_ms = ms;
+            }
+        }
+        if (rc != FP8_OK)
+            break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FP8_OK)
+        return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[signature(jobs, bns, n, max_ctas)] = winner;
+    }
+    if (best) {
+        best->mt = winner.mt;
+        best->group_m = winner.group_m;
+        best->ms_per_launch = best_ms / static_cast<float>(iters);
+    }
+    return FP8_OK;
+}
+
+extern "C" int gemm_fp8_tune_cache_save(const char* path)
+{
+    using namespace gb300;
+    if (!path)
+        return FP8_ERR_INVALID;
+    FILE* f = fopen(path, "w");
+    if (!f)
+        return FP8_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    fprintf(f, "# gb300fp8 tile cache v1: <signature length> <signature...> <mt> <group_m>\n");
+    for (const auto& kv : g_tuned) {
+        fprintf(f, "%zu", kv.first.size());
+        for (int64_t v : kv.first)
+            fprintf(f, " %lld", static_cast<long long>(v));
+        fprintf(f, " %d %d\n", kv.second.mt, kv.second.group_m);
+    }
+    fclose(f);
+    return FP8_OK;
+}
+
+extern "C" int gemm_fp8_tune_cache_load(const char* path)
+{
+    using namespace gb300;
+    if (!path)
+        return FP8_ERR_INVALID;
+    FILE* f = fopen(path, "r");
+    if (!f)
+        return FP8_ERR_INVALID;
+    std::map<std::vector<int64_t>, TileChoice> loaded;
+    char line[8192];
+    int rc = FP8_OK;
+    while (fgets(line, sizeof(line), f)) {
+        if (line[0] == '#' || line[0] == '\n')
+            continue;
+        char* p = line;
+        char* end = nullptr;
+        const long long len = strtoll(p, &end, 10);
+        if (end == p || len <= 0 || len > 2 + 7 * FP8_GROUPED_MAX_PROBLEMS) {
+            rc = FP8_ERR_INVALID;
+            break;
+        }
+        std::vector<int64_t> key;
+        for (long long i = 0; i < len && rc == FP8_OK; ++i) {
+            p = end;
+            const long long v = strtoll(p, &end, 10);
+            if (end == p)
+                rc = FP8_ERR_INVALID;
+            key.push_back(v);
+        }
+        TileChoice c;
+        p = end;
+        c.mt = static_cast<int>(strtol(p, &end, 10));
+        p = end;
+        c.group_m = static_cast<int>(strtol(p, &end, 10));
+        if (rc != FP8_OK || (c.mt != 1 && c.mt != 2) || c.group_m <= 0 || c.group_m > 4096) {
+            rc = FP8_ERR_INVALID;
+            break;
+        }
+        loaded[key] = c;
+    }
+    fclose(f);
+    if (rc != FP8_OK)
+        return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : loaded)
+        g_tuned[kv.first] = kv.second;
+    return FP8_OK;
+}
+
+extern "C" int gemm_fp8_tune_cache_clear(void)
+{
+    std::lock_guard<std::mutex> lk(gb300::g_tune_mu);
+    gb300::g_tuned.clear();
+    return FP8_OK;
+}
+
+// ---------------------------------------------------------------- CUDA graphs
+
+struct fp8_grouped_graph {
+    gb300::Params<FP8_GROUPED_MAX_PROBLEMS> prm;
+    gb300::Plan plan;
+    std::vector<int64_t> sig;
+    int max_ctas = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t node = nullptr;
+};
+
+namespace {
+
+int graph_params(fp8_grouped_graph* g, const fp8_gemm_problem* problems, int num_problems,
+                 std::vector<int64_t>* sig)
+{
+    using namespace gb300;
+    Job jobs[FP8_GROUPED_MAX_PROBLEMS];
+    int bns[FP8_GROUPED_MAX_PROBLEMS];
+    int n = 0;
+    int rc = grouped_jobs(problems, num_problems, nullptr, false, jobs, bns, &n);
+    if (rc != FP8_OK)
+        return rc;
+    if (n == 0)
+        return FP8_ERR_SHAPE;
+    *sig = signature(jobs, bns, n, g->max_ctas);
+    memset(&g->prm, 0, sizeof(g->prm));
+    return build_plan(g->prm, jobs, bns, n, g->max_ctas, nullptr, &g->plan);
+}
+
+cudaKernelNodeParams node_params(fp8_grouped_graph* g, void** args)
+{
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(g->plan.func);
+    kp.gridDim = dim3(g->plan.grid);
+    kp.blockDim = dim3(g->plan.threads);
+    kp.sharedMemBytes = static_cast<unsigned>(g->plan.smem);
+    args[0] = &g->prm;
+    kp.kernelParams = args;
+    return kp;
+}
+
+}  // namespace
+
+extern "C" int gemm_fp8_grouped_graph_create(const fp8_gemm_problem* problems, int num_problems,
+                                             int max_ctas, fp8_grouped_graph** out)
+{
+    if (!out)
+        return FP8_ERR_INVALID;
+    auto* g = new fp8_grouped_graph;
+    g->max_ctas = max_ctas;
+    int rc = graph_params(g, problems, num_problems, &g->sig);
+    void* args[1];
+    if (rc == FP8_OK) {
+        cudaKernelNodeParams kp = node_params(g, args);
+        if (cudaGraphCreate(&g->graph, 0) != cudaSuccess ||
+            cudaGraphAddKernelNode(&g->node, g->graph, nullptr, 0, &kp) != cudaSuccess ||
+            cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
+            rc = FP8_ERR_CUDA;
+    }
+    if (rc != FP8_OK) {
+        if (g->exec)
+            cudaGraphExecDestroy(g->exec);
+        if (g->graph)
+            cudaGraphDestroy(g->graph);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return FP8_OK;
+}
+
+extern "C" int gemm_fp8_grouped_graph_update(fp8_grouped_graph* g,
+                                             const fp8_gemm_problem* problems, int num_problems)
+{
+    if (!g)
+        return FP8_ERR_INVALID;
+    std::vector<int64_t> sig;
+    const gb300::Plan old = g->plan;
+    int rc = graph_params(g, problems, num_problems, &sig);
+    if (rc != FP8_OK)
+        return rc;
+    if (sig != g->sig || g->plan.func != old.func || g->plan.grid != old.grid)
+        return FP8_ERR_SHAPE;
+    void* args[1];
+    cudaKernelNodeParams kp = node_params(g, args);
+    if (cudaGraphExecKernelNodeSetParams(g->exec, g->node, &kp) != cudaSuccess)
+        return FP8_ERR_CUDA;
+    return FP8_OK;
+}
+
+extern "C" int gemm_fp8_grouped_graph_launch(fp8_grouped_graph* g, fp8_stream_t stream)
+{
+    if (!g)
+        return FP8_ERR_INVALID;
+    GB_CUDA_OK(cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)));
+    return FP8_OK;
+}
+
+extern "C" int gemm_fp8_grouped_graph_destroy(fp8_grouped_graph* g)
+{
+    if (!g)
+        return FP8_ERR_INVALID;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return FP8_OK;
 }
 
 extern "C" int fp8_gemm_set_tile_config(int mt, int group_m)

@@ -70,3 +70,21 @@ def test_grouped_rejects_too_many(lib):
     assert lib.gemm_fp8_grouped(arr, 33, None) == -2
     assert lib.gemm_fp8_grouped(None, 1, None) == -1
     assert lib.gemm_fp8_grouped(None, 0, None) in (0, -8)
+
+
+def test_tune_cache_file_round_trip(lib, tmp_path):
+    good = tmp_path / "tiles.txt"
+    good.write_text("# comment\n9 1 0 8192 4096 4096 0 256 1 0 2 16\n")
+    assert lib.gemm_fp8_tune_cache_clear() == 0
+    assert lib.gemm_fp8_tune_cache_load(str(good).encode()) == 0
+    out = tmp_path / "saved.txt"
+    assert lib.gemm_fp8_tune_cache_save(str(out).encode()) == 0
+    lines = [l for l in out.read_text().splitlines() if not l.startswith("#")]
+    assert lines == ["9 1 0 8192 4096 4096 0 256 1 0 2 16"]
+    for bad in ("3 1 2\n", "9 1 0 8192 4096 4096 0 256 1 0 7 16\n", "x y z\n",
+                "9 1 0 8192 4096 4096 0 256 1 0 2 0\n"):
+        f = tmp_path / "bad.txt"
+        f.write_text(bad)
+        assert lib.gemm_fp8_tune_cache_load(str(f).encode()) == -1
+    assert lib.gemm_fp8_tune_cache_load(str(tmp_path / "missing.txt").encode()) == -1
+    assert lib.gemm_fp8_tune_cache_clear() == 0
