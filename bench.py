@@ -376,6 +376,117 @@ def serving_report(gb, dev, n_cap=1500, n_load=1500, load=0.8):
     return out
 
 
+# ------------------------------------------------------------------ shape sweep
+
+def _time_ms(fn, target_s=0.15, warmup=3):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    one = max(e0.elapsed_time(e1), 1e-3)
+    n = max(3, min(200, int(target_s * 1e3 / one)))
+    e0.record()
+    for _ in range(n):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def _operands(gb, M, N, K, dev, seed):
+    g = torch.Generator(device=dev).manual_seed(seed)
+    x = torch.randn((M, K), generator=g, device=dev)
+    w = torch.randn((N, K), generator=g, device=dev)
+    A, dA = gb.fp8_quantize_e4m3(x, 1)
+    B, dB = gb.fp8_quantize_e4m3(w, 1)
+    return x, w, A, dA, B, dB
+
+
+def sweep(gb, dev):
+    """Configs 2-4: dense square and skinny vs BF16 torch.matmul, 2:4 sparse
+    vs dense on the same pruned A, the transformer layer as one grouped
+    persistent launch vs per-call."""
+    out = {"dense": [], "sparse": [], "transformer_layer": None}
+    for (M, N, K) in [(s, s, s) for s in workloads.SQUARE_SWEEP] + \
+                     [(m, workloads.SKINNY_NK, workloads.SKINNY_NK) for m in workloads.SKINNY_M]:
+        x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, M + N)
+        C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+        ms = _time_ms(lambda: gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C))
+        xb, wb = x.bfloat16(), w.bfloat16()
+        ms_bf16 = _time_ms(lambda: torch.matmul(xb, wb.T))
+        flops = 2.0 * M * N * K
+        row = {"M": M, "N": N, "K": K, "fp8_ms": ms, "fp8_tflops": flops / ms / 1e9,
+               "bf16_matmul_ms": ms_bf16, "bf16_tflops": flops / ms_bf16 / 1e9,
+               "speedup_vs_bf16": ms_bf16 / ms}
+        if M <= 128:
+            row["fp8_gbs"] = (M * K + N * K + 2 * M * N) / ms / 1e6
+        out["dense"].append(row)
+        del x, w, xb, wb, A, B, C
+        torch.cuda.empty_cache()
+    sp_shapes = [(s, s, s) for s in workloads.SPARSE_SQUARE] + [workloads.SPARSE_SKINNY, workloads.SPARSE_RECT]
+    for (M, N, K) in sp_shapes:
+        x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 7 * M + N)
+        vals, meta = gb.prune24_compress(A)
+        Ap = gb.prune24_decompress(vals, meta, K)
+        C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+        ms_sp = _time_ms(lambda: gb.gemm_fp8_sparse24(vals, meta, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C))
+        ms_d = _time_ms(lambda: gb.gemm_fp8_dense(Ap, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C))
+        ms_pr = _time_ms(lambda: gb.prune24_compress(A, vals, meta))
+        flops = 2.0 * M * N * K
+        row = {"M": M, "N": N, "K": K, "sparse_ms": ms_sp, "dense_same_pruned_ms": ms_d,
+               "sparse_tflops_dense_equiv": flops / ms_sp / 1e9, "dense_tflops": flops / ms_d / 1e9,
+               "sparse_speedup": ms_d / ms_sp, "prune_us": ms_pr * 1e3,
+               "prune_gbs": M * K * 1.625 / ms_pr / 1e6}
+        if M <= 512 and N > M:
+            # sparse weights: the [N, K] operand pruned and put on the MMA M side
+            wv, wm = gb.prune24_compress(B)
+            Bp = gb.prune24_decompress(wv, wm, K)
+            Ct = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+            ms_ws = _time_ms(lambda: gb.gemm_fp8_sparse24(wv, wm, A, dB, 1, dA, 1, 1.0, gb.OUT_BF16,
+                                                          out_transposed=True, C=Ct))
+            ms_wd = _time_ms(lambda: gb.gemm_fp8_dense(A, Bp, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=Ct))
+            row.update({"weight_sparse_ms": ms_ws, "dense_same_pruned_weight_ms": ms_wd,
+                        "weight_sparse_speedup": ms_wd / ms_ws})
+        out["sparse"].append(row)
+        del x, w, A, B, C, vals, meta, Ap
+        torch.cuda.empty_cache()
+    # transformer layer: QKV, output projection, FFN up, FFN down
+    probs, keep, flops = [], [], 0.0
+    calls_fp8, calls_bf16 = [], []
+    for i, (name, M, N, K) in enumerate(workloads.TRANSFORMER_LAYER):
+        x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 900 + i)
+        C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+        xb, wb = x.bfloat16(), w.bfloat16()
+        del x, w
+        keep += [A, dA, B, dB, C, xb, wb]
+        probs.append(gb.make_problem(A, B, dA, 1, dB, 1, C, 1.0, gb.OUT_BF16))
+        calls_fp8.append((A, B, dA, dB, C))
+        calls_bf16.append((xb, wb))
+        flops += 2.0 * M * N * K
+    tuned = gb.gemm_fp8_grouped_autotune(probs, iters=2)
+    graph = gb.GroupedGraph(probs)
+    ms_graph = _time_ms(graph.launch)
+    ms_grouped = _time_ms(lambda: gb.gemm_fp8_grouped(probs))
+    ms_percall = _time_ms(lambda: [gb.gemm_fp8_dense(a, b, da, 1, db, 1, 1.0, gb.OUT_BF16, C=c)
+                                   for a, b, da, db, c in calls_fp8])
+    ms_bf16 = _time_ms(lambda: [torch.matmul(xb, wb.T) for xb, wb in calls_bf16])
+    graph.close()
+    out["transformer_layer"] = {
+        "problems": [list(t) for t in workloads.TRANSFORMER_LAYER], "gflop": flops / 1e9,
+        "tuned_tile": tuned,
+        "grouped_graph_ms": ms_graph, "grouped_graph_tflops": flops / ms_graph / 1e9,
+        "grouped_ms": ms_grouped, "fp8_per_call_ms": ms_percall,
+        "bf16_per_call_ms": ms_bf16, "bf16_tflops": flops / ms_bf16 / 1e9,
+        "speedup_vs_bf16_per_call": ms_bf16 / ms_graph}
+    del keep
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def main():
@@ -390,6 +501,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--sweep", default=None,
+                    help="write the config 2-4 shape sweep to this JSON file and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -401,6 +514,15 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     gb.library()
+    if args.sweep:
+        res = sweep(gb, dev)
+        pk, pk_kind = peaks()
+        res["peaks"] = {"fp8_dense_tflops": pk["bf16_tflops"] * FP8_PER_BF16, "kind": pk_kind,
+                        "hbm_gbs": pk["hbm_gbs"]}
+        with open(args.sweep, "w") as f:
+            json.dump(res, f, indent=1)
+        print(json.dumps({"sweep": args.sweep}))
+        return 0
     S = args.size
     M = N = K = S
 
