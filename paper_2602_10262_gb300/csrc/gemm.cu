@@ -51,24 +51,27 @@ constexpr int SPARSE_BN_MAX = 240;
 constexpr int SPARSE_BN_MAX_MT2 = 224;
 
 // MT = 128-row MMA halves per CTA tile.
-//  MT = 1: tile 128 x bn, 4 stages of 48 KB (dense and sparse problems alike),
-//          two accumulators (cols 0 / 256) so the epilogue of tile i overlaps
-//          the MMAs of tile i + 1; metadata ring at cols 240..255, bn <= 240
-//          for sparse problems;
+//  MT = 1: tile 128 x bn (dense and sparse problems alike), two accumulators
+//          (cols 0 / 256) so the epilogue of tile i overlaps the MMAs of tile
+//          i + 1.  BNC caps bn for the launch and sizes the ring: BNC = 256,
+//          4 stages of 48 KB (metadata ring at cols 240..255, bn <= 240 for
+//          sparse problems); BNC = 128, 6 stages of 32 KB; BNC = 64, 8 stages
+//          of 24 KB (narrow N, e.g. skinny products whose small M is the MMA
+//          N: more bytes in flight per SM where few tiles exist);
 //  MT = 2: tile 256 x bn; two MMAs per k-step share the B tile (a third fewer
 //          operand bytes per FLOP); one accumulator spanning all 512 columns
 //          (rows 0-127 in cols 0-255, rows 128-255 in cols 256-511).  Dense
 //          launches (SP = false): 3 stages of 64 KB.  Sparse launches
 //          (SP = true): 4 stages of 48 KB (20 KB kept codes + metadata, 28 KB
 //          B with bn <= 224), metadata rings at cols 224..239 of each half.
-template <int MT, bool SP = false>
+template <int MT, bool SP = false, int BNC = BN_MAX>
 struct Cfg {
     static constexpr bool kSparse2 = MT == 2 && SP;
-    static constexpr int kStages = (MT == 2 && !SP) ? 3 : 4;
+    static constexpr int kStages = MT == 2 ? (SP ? 4 : 3) : (BNC == 256 ? 4 : (BNC == 128 ? 6 : 8));
     static constexpr int kABytes = MT == 1 ? BM * BK : (SP ? 2 * BM * (BK / 2 + BK / 8) : 2 * BM * BK);
-    static constexpr int kBBytes = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : B_BYTES;
+    static constexpr int kBBytes = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : BNC * BK;
     static constexpr int kStageBytes = kABytes + kBBytes;
-    static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : SPARSE_BN_MAX;
+    static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : (BNC == 256 ? SPARSE_BN_MAX : BNC);
     static constexpr int kAcc = MT == 2 ? 1 : 2;                  // accumulator buffers
     static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
     static constexpr int kSpABytes = MT * BM * BK / 2;           // kept codes of a stage
@@ -80,6 +83,8 @@ struct Cfg {
                   "sparse A + metadata fit the A region");
     static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "swizzle atoms stay aligned");
     static_assert(kSmem <= 232448, "shared memory per CTA");
+    static_assert(2 * kStages + 2 * kAcc + 1 <= 28, "barriers fit their 256-byte region");
+    static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
 };
 
 struct Problem {
@@ -285,11 +290,11 @@ __device__ __forceinline__ void epilogue_rows_coalesced(const Problem& P, uint32
 
 // ---------------------------------------------------------------- kernel
 
-template <int MAXP, int MT, bool SP>
-__global__ void __launch_bounds__(Cfg<MT, SP>::kThreads, 1)
+template <int MAXP, int MT, bool SP, int BNC>
+__global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
     gemm_fp8_kernel(const __grid_constant__ Params<MAXP> prm)
 {
-    using C = Cfg<MT, SP>;
+    using C = Cfg<MT, SP, BNC>;
     constexpr int S = C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -679,10 +684,10 @@ struct Plan {
     int grid = 0, threads = 0, smem = 0;
 };
 
-template <int MAXP, int MT, bool SP>
+template <int MAXP, int MT, bool SP, int BNC = BN_MAX>
 int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
 {
-    using C = Cfg<MT, SP>;
+    using C = Cfg<MT, SP, BNC>;
     static std::once_flag attr_once[64];
     int dev = 0;
     GB_CUDA_OK(cudaGetDevice(&dev));
@@ -690,7 +695,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
         return FP8_ERR_UNSUPPORTED;
     cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once[dev], [&] {
-        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP>,
+        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP, BNC>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     });
     GB_CUDA_OK(attr_err);
@@ -704,7 +709,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
-    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP>);
+    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC>);
     out->grid = grid;
     out->threads = C::kThreads;
     out->smem = C::kSmem;
@@ -817,8 +822,16 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
     }
     prm.num_problems = n;
     prm.group_m = c.group_m;
-    if (c.mt == 1)
-        return plan<MAXP, 1, false>(prm, max_ctas, pl);
+    if (c.mt == 1) {
+        int max_bn = 0;
+        for (int i = 0; i < n; ++i)
+            max_bn = std::max(max_bn, bns_in[i]);
+        if (max_bn <= 64)
+            return plan<MAXP, 1, false, 64>(prm, max_ctas, pl);
+        if (max_bn <= 128)
+            return plan<MAXP, 1, false, 128>(prm, max_ctas, pl);
+        return plan<MAXP, 1, false, 256>(prm, max_ctas, pl);
+    }
     return sparse ? plan<MAXP, 2, true>(prm, max_ctas, pl) : plan<MAXP, 2, false>(prm, max_ctas, pl);
 }
 
