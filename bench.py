@@ -378,23 +378,46 @@ def serving_report(gb, dev, n_cap=1500, n_load=1500, load=0.8):
 
 # ------------------------------------------------------------------ shape sweep
 
-def _time_ms(fn, target_s=0.15, warmup=3):
+def _time_ms(fn, target_s=0.15, warmup=3, reps=10, capture=True):
+    """Device time per call of fn: `reps` calls are captured in a CUDA graph
+    (the library's launches and cuBLAS both capture) and the graph is
+    replayed, so host-side call overhead does not hide in the number.
+    capture=False times fn itself (for fn that already replays a graph)."""
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
+    if not capture:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 20
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(reps):
+            fn()
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    fn()
+    g.replay()
     e1.record()
     torch.cuda.synchronize()
     one = max(e0.elapsed_time(e1), 1e-3)
     n = max(3, min(200, int(target_s * 1e3 / one)))
     e0.record()
     for _ in range(n):
-        fn()
+        g.replay()
     e1.record()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / n
+    ms = e0.elapsed_time(e1) / (n * reps)
+    del g
+    return ms
 
 
 def _operands(gb, M, N, K, dev, seed):
@@ -469,7 +492,7 @@ def sweep(gb, dev):
         flops += 2.0 * M * N * K
     tuned = gb.gemm_fp8_grouped_autotune(probs, iters=2)
     graph = gb.GroupedGraph(probs)
-    ms_graph = _time_ms(graph.launch)
+    ms_graph = _time_ms(graph.launch, capture=False)
     ms_grouped = _time_ms(lambda: gb.gemm_fp8_grouped(probs))
     ms_percall = _time_ms(lambda: [gb.gemm_fp8_dense(a, b, da, 1, db, 1, 1.0, gb.OUT_BF16, C=c)
                                    for a, b, da, db, c in calls_fp8])

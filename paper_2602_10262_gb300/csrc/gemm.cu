@@ -83,7 +83,7 @@ struct Cfg {
                   "sparse A + metadata fit the A region");
     static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "swizzle atoms stay aligned");
     static_assert(kSmem <= 232448, "shared memory per CTA");
-    static_assert(2 * kStages + 2 * kAcc + 1 <= 28, "barriers fit their 256-byte region");
+    static_assert(2 * kStages + 2 * kAcc + 3 <= 28, "barriers fit their 256-byte region");
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
 };
 
@@ -104,7 +104,11 @@ struct Problem {
     int bn;
     int sparse;             // P holds kept codes [rows_p, K/2] + metadata in tmE
     int m_blocks, n_blocks, k_blocks;
-    int tile_start;
+    int splits;             // k-slices per tile (split-K); 1 = none
+    int kb_per_split;       // k-blocks per slice
+    long long ws_off;       // split-K: first partial (floats) of this problem in the workspace
+    int ctr_off;            // split-K: first tile counter of this problem
+    int tile_start;         // first work unit (tile x slice) of this problem
     uint32_t idesc;
 };
 
@@ -115,10 +119,14 @@ struct Params {
     int total_tiles;
     int group_m;
     int* err;
+    float* ws;              // split-K partial sums (nullptr when no problem splits)
+    unsigned* ctr;          // split-K arrival counters, zero between launches
 };
 
 struct TileCoord {
     int p, m_blk, n_blk;
+    int tile;               // tile index within its problem
+    int slice;              // k-slice of the unit
 };
 
 template <int MAXP>
@@ -129,14 +137,15 @@ __device__ __forceinline__ TileCoord tile_coord(const Params<MAXP>& prm, int til
     while (p + 1 < prm.num_problems && prm.prob[p + 1].tile_start <= tile)
         ++p;
     const Problem& P = prm.prob[p];
-    const int lt = tile - P.tile_start;
+    const int unit = tile - P.tile_start;
+    const int lt = unit / P.splits;
     const int gm = prm.group_m;
     const int per_band = gm * P.n_blocks;
     const int band = lt / per_band;
     const int first_m = band * gm;
     const int rows_in_band = min(P.m_blocks - first_m, gm);
     const int r = lt - band * per_band;
-    return {p, first_m + r % rows_in_band, r / rows_in_band};
+    return {p, first_m + r % rows_in_band, r / rows_in_band, lt, unit - lt * P.splits};
 }
 
 __device__ __forceinline__ void abort_pipeline(volatile int* flag, int* err)
@@ -147,8 +156,9 @@ __device__ __forceinline__ void abort_pipeline(volatile int* flag, int* err)
 
 // ---------------------------------------------------------------- epilogue
 
-__device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_ok, float fi,
-                                              int j0, const uint32_t (&r)[16])
+// Scale 16 accumulator values (columns j0 .. j0+15 of row i) and store them.
+__device__ __forceinline__ void store_vals16(const Problem& P, int i, bool row_ok, float fi, int j0,
+                                             const float (&acc)[16])
 {
     float v[16];
     const int rows_q = P.rows_q;
@@ -156,7 +166,7 @@ __device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_
     for (int t = 0; t < 16; ++t) {
         const int j = j0 + t;
         const float sj = (j < rows_q) ? __ldg(P.sq + (P.sq_mode ? j : 0)) : 0.0f;
-        v[t] = __fmul_rn(__fmul_rn(__uint_as_float(r[t]), fi), sj);
+        v[t] = __fmul_rn(__fmul_rn(acc[t], fi), sj);
     }
     if (!row_ok)
         return;
@@ -207,6 +217,62 @@ __device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_
                 if (j0 + t < rows_q)
                     c[static_cast<long long>(j0 + t) * P.ldc] = v[t];
         }
+    }
+}
+
+__device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_ok, float fi,
+                                              int j0, const uint32_t (&r)[16])
+{
+    float acc[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+        acc[t] = __uint_as_float(r[t]);
+    store_vals16(P, i, row_ok, fi, j0, acc);
+}
+
+// Split-K, part 1: this unit's partial sums (row `row` of the tile, straight
+// from TMEM) go to its slot of the workspace.
+__device__ __forceinline__ void split_write_partial(const Problem& P, float* ws, int rows_per_tile,
+                                                    int tile, int slice, int row, uint32_t taddr)
+{
+    float* dst = ws + P.ws_off + (static_cast<long long>(tile) * P.splits + slice) * rows_per_tile * P.bn +
+                 static_cast<long long>(row) * P.bn;
+    for (int c0 = 0; c0 < P.bn; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld_32x32b_x16(taddr + c0, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            __stcg(reinterpret_cast<float4*>(dst + c0) + t,
+                   make_float4(__uint_as_float(r[4 * t]), __uint_as_float(r[4 * t + 1]),
+                               __uint_as_float(r[4 * t + 2]), __uint_as_float(r[4 * t + 3])));
+    }
+}
+
+// Split-K, part 2 (the tile's last unit only): add the partials of every
+// slice in slice order and store the scaled result.
+__device__ __forceinline__ void split_reduce_store(const Problem& P, const float* ws, int rows_per_tile,
+                                                   int tile, int row, int i, bool row_ok, float fi, int jbase)
+{
+    const float* src = ws + P.ws_off + static_cast<long long>(tile) * P.splits * rows_per_tile * P.bn +
+                       static_cast<long long>(row) * P.bn;
+    const long long slot = static_cast<long long>(rows_per_tile) * P.bn;
+    for (int c0 = 0; c0 < P.bn; c0 += 16) {
+        float acc[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            acc[t] = 0.0f;
+        for (int sl = 0; sl < P.splits; ++sl) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(src + sl * slot + c0) + t);
+                acc[4 * t] = __fadd_rn(acc[4 * t], v.x);
+                acc[4 * t + 1] = __fadd_rn(acc[4 * t + 1], v.y);
+                acc[4 * t + 2] = __fadd_rn(acc[4 * t + 2], v.z);
+                acc[4 * t + 3] = __fadd_rn(acc[4 * t + 3], v.w);
+            }
+        }
+        store_vals16(P, i, row_ok, fi, jbase + c0, acc);
     }
 }
 
@@ -301,10 +367,11 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                                                ~static_cast<uintptr_t>(1023));
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * C::kStageBytes);
     // bar[0..S) full, bar[S..2S) empty, then kAcc tmem_full, kAcc tmem_empty,
-    // then drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2 * S + 2 * C::kAcc + 1);
+    // then drain, split-K "partials written", split-K "verdict ready"
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2 * S + 2 * C::kAcc + 3);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     uint8_t* epi_smem = smem + S * C::kStageBytes + 256;      // epilogue staging, per warp
+    volatile int* split_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
     const uint32_t smem_base = smem_u32(smem);
     const uint32_t bar_base = smem_u32(bar);
@@ -313,6 +380,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
     auto tfull_bar = [&](int b) { return bar_base + 8u * (2 * S + b); };
     auto tempty_bar = [&](int b) { return bar_base + 8u * (2 * S + C::kAcc + b); };
     const uint32_t drain_bar = bar_base + 8u * (2 * S + 2 * C::kAcc);
+    const uint32_t split_written_bar = drain_bar + 8u;
+    const uint32_t split_verdict_bar = drain_bar + 16u;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -327,6 +396,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
             mbar_init(tempty_bar(b), 128 * MT);
         }
         mbar_init(drain_bar, 1);
+        mbar_init(split_written_bar, 128 * MT);
+        mbar_init(split_verdict_bar, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -360,7 +431,9 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                 const uint32_t a_bytes = P.sparse ? C::kSpABytes + MT * BM * BK / 8 : C::kABytes;
                 const uint32_t bytes = a_bytes + static_cast<uint32_t>(P.bn) * BK;
                 const int row0 = tc.m_blk * BM * MT;
-                for (int kb = 0; kb < P.k_blocks; ++kb) {
+                const int kb0 = tc.slice * P.kb_per_split;
+                const int kb1 = min(P.k_blocks, kb0 + P.kb_per_split);
+                for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
                         ok = false;
                         abort_pipeline(abort_flag, prm.err);
@@ -414,7 +487,10 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                 tc_fence_after();
                 // half h of the tile accumulates into columns d_tmem + 256 h
                 const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN_MAX);
-                for (int kb = 0; kb < P.k_blocks; ++kb) {
+                const int kb0 = tc.slice * P.kb_per_split;
+                const int kb1 = min(P.k_blocks, kb0 + P.kb_per_split);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    const uint32_t first = kb == kb0 ? 0u : 1u;     // 0: overwrite the accumulator
                     if (!mbar_wait(full_bar(stage), phase, abort_flag)) {
                         ok = false;
                         abort_pipeline(abort_flag, prm.err);
@@ -443,7 +519,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                                 const uint32_t meta = tmem_base + static_cast<uint32_t>(
                                                                       h * BN_MAX + C::kMetaCol0 + 4 * stage);
                                 mma_sp_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 4u * k,
-                                              meta + 2u * k, P.idesc, (kb | k) != 0 ? 1u : 0u);
+                                              meta + 2u * k, P.idesc, (first | k) != 0 ? 1u : 0u);
                             }
                         }
                     } else {
@@ -454,7 +530,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                                 // advance the start address by 32 bytes (K = 32 codes)
                                 const uint64_t adesc = sdesc_kmajor_sw128(sa + h * BM * BK);
                                 mma_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 2u * k,
-                                           P.idesc, (kb | k) != 0 ? 1u : 0u);
+                                           P.idesc, (first | k) != 0 ? 1u : 0u);
                             }
                         }
                     }
@@ -479,6 +555,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
         const int half = (warp - 2) >> 2;
         const int row = half * BM + quarter * 32 + lane;
         int local = 0;
+        uint32_t split_phase = 0;
         for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++local) {
             const TileCoord tc = tile_coord(prm, tile);
             const Problem& P = prm.prob[tc.p];
@@ -497,6 +574,40 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>((acc + half) * BN_MAX);
             const int jbase = tc.n_blk * P.bn;
+            if (P.splits > 1) {
+                // every epilogue thread stores its row's partials, then one
+                // thread counts this unit in; the tile's last unit reduces.
+                // (The verdict slot is rewritten only after every thread has
+                // arrived for the next split tile, i.e. after it was read.)
+                split_write_partial(P, prm.ws, BM * MT, tc.tile, tc.slice, row, taddr);
+                tc_fence_before();
+                mbar_arrive(tempty_bar(acc));          // TMEM is free; the reduction reads global memory
+                __threadfence();
+                mbar_arrive(split_written_bar);
+                if (threadIdx.x == 64) {
+                    if (mbar_wait(split_written_bar, split_phase, abort_flag)) {
+                        const unsigned prev = atomicAdd(prm.ctr + P.ctr_off + tc.tile, 1u);
+                        *split_flag = (prev == static_cast<unsigned>(P.splits - 1)) ? 1 : 0;
+                    } else {
+                        *split_flag = 0;
+                        abort_pipeline(abort_flag, prm.err);
+                    }
+                    mbar_arrive(split_verdict_bar);
+                }
+                const bool got_verdict = mbar_wait(split_verdict_bar, split_phase, abort_flag);
+                split_phase ^= 1u;
+                if (!__all_sync(0xFFFFFFFFu, got_verdict)) {
+                    abort_pipeline(abort_flag, prm.err);
+                    break;
+                }
+                if (*split_flag) {
+                    __threadfence();
+                    split_reduce_store(P, prm.ws, BM * MT, tc.tile, row, i, row_ok, fi, jbase);
+                    if (threadIdx.x == 64)
+                        prm.ctr[P.ctr_off + tc.tile] = 0u;         // ready for the next launch
+                }
+                continue;
+            }
             if (!P.trans_out && P.vec_store) {
                 uint8_t* buf = epi_smem + (warp - 2) * 32 * 128;
                 const int row0 = i - lane;
@@ -633,6 +744,28 @@ int validate(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, con
     return FP8_OK;
 }
 
+// Split-K: k-slices for a problem with too few 128-row tiles to occupy the
+// GPU.  Decided from the problem alone (its tile count at N tile width
+// pick_bn(rows_q, 256), the SM count and K), never from what it is launched
+// with, so a problem sums its K range the same way alone, grouped or under
+// any tile configuration.  Every slice gets at least two k-blocks and none is
+// empty.
+int split_count(const Job& j)
+{
+    const int sms = sm_count();
+    const int64_t bn = pick_bn(j.rows_q, BN_MAX);
+    const int64_t tiles = ((j.rows_p + BM - 1) / BM) * ((j.rows_q + bn - 1) / bn);
+    const int k_blocks = static_cast<int>((j.K + BK - 1) / BK);
+    if (tiles <= 0 || 2 * tiles > sms)
+        return 1;
+    int s = std::min<int64_t>(8, sms / tiles);
+    s = std::min(s, k_blocks / 2);
+    if (s <= 1)
+        return 1;
+    const int kbs = (k_blocks + s - 1) / s;
+    return (k_blocks + kbs - 1) / kbs;
+}
+
 // Fill one problem entry for a launch with MT row-halves per tile.
 int fill_problem(Problem& pr, const Job& j, int bn, int mt)
 {
@@ -666,6 +799,8 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt)
     pr.m_blocks = static_cast<int>((j.rows_p + box_p - 1) / box_p);
     pr.n_blocks = static_cast<int>((j.rows_q + bn - 1) / bn);
     pr.k_blocks = static_cast<int>((j.K + BK - 1) / BK);
+    pr.splits = split_count(j);
+    pr.kb_per_split = (pr.k_blocks + pr.splits - 1) / pr.splits;
     pr.idesc = idesc_e4m3_f32(BM, bn, pr.sparse != 0, 0);
     return FP8_OK;
 }
@@ -682,7 +817,26 @@ int write_zeros(void* C, int64_t ldc, int64_t rows, int64_t cols, int out_bf16, 
 struct Plan {
     const void* func = nullptr;
     int grid = 0, threads = 0, smem = 0;
+    size_t ws_floats = 0;       // split-K partials
+    size_t ctr_count = 0;       // split-K tile counters
 };
+
+// Workspace of a split-K launch: partial sums then counters.
+size_t workspace_bytes(const Plan& pl)
+{
+    if (pl.ctr_count == 0)
+        return 0;
+    return (pl.ws_floats * sizeof(float) + 255) / 256 * 256 + pl.ctr_count * sizeof(unsigned);
+}
+
+template <int MAXP>
+void bind_workspace(Params<MAXP>& prm, const Plan& pl, void* base)
+{
+    prm.ws = static_cast<float*>(base);
+    prm.ctr = base ? reinterpret_cast<unsigned*>(static_cast<uint8_t*>(base) +
+                                                 (pl.ws_floats * sizeof(float) + 255) / 256 * 256)
+                   : nullptr;
+}
 
 template <int MAXP, int MT, bool SP, int BNC = BN_MAX>
 int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
@@ -700,11 +854,22 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     });
     GB_CUDA_OK(attr_err);
     int tiles = 0;
+    long long ws = 0;
+    int ctrs = 0;
     for (int p = 0; p < prm.num_problems; ++p) {
-        prm.prob[p].tile_start = tiles;
-        tiles += prm.prob[p].m_blocks * prm.prob[p].n_blocks;
+        Problem& P = prm.prob[p];
+        P.tile_start = tiles;
+        tiles += P.m_blocks * P.n_blocks * P.splits;
+        if (P.splits > 1) {
+            P.ws_off = ws;
+            P.ctr_off = ctrs;
+            ws += static_cast<long long>(P.m_blocks) * P.n_blocks * P.splits * (BM * MT) * P.bn;
+            ctrs += P.m_blocks * P.n_blocks;
+        }
     }
     prm.total_tiles = tiles;
+    out->ws_floats = static_cast<size_t>(ws);
+    out->ctr_count = static_cast<size_t>(ctrs);
     prm.err = device_error_word();
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
@@ -835,6 +1000,9 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
     return sparse ? plan<MAXP, 2, true>(prm, max_ctas, pl) : plan<MAXP, 2, false>(prm, max_ctas, pl);
 }
 
+// Plan and launch.  A split-K launch takes its workspace from the stream-
+// ordered allocator (cudaMallocAsync / cudaFreeAsync on `st`) and zeroes the
+// counters first; the partials need no clearing.
 template <int MAXP>
 int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_ctas,
              cudaStream_t st, const TileChoice* expl = nullptr)
@@ -843,7 +1011,21 @@ int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_
     int rc = build_plan(prm, jobs, bns, n, max_ctas, expl, &pl);
     if (rc != FP8_OK)
         return rc;
-    return launch_plan(prm, pl, st);
+    const size_t bytes = workspace_bytes(pl);
+    if (bytes == 0) {
+        bind_workspace(prm, pl, nullptr);
+        return launch_plan(prm, pl, st);
+    }
+    void* buf = nullptr;
+    if (cudaMallocAsync(&buf, bytes, st) != cudaSuccess)
+        return FP8_ERR_OOM;
+    bind_workspace(prm, pl, buf);
+    rc = cudaMemsetAsync(prm.ctr, 0, pl.ctr_count * sizeof(unsigned), st) == cudaSuccess
+             ? launch_plan(prm, pl, st)
+             : FP8_ERR_CUDA;
+    if (cudaFreeAsync(buf, st) != cudaSuccess && rc == FP8_OK)
+        rc = FP8_ERR_CUDA;
+    return rc;
 }
 
 // Map a user-level GEMM (A [M,K], B [N,K], C [M,N] or C^T) onto (P, Q)
@@ -1159,6 +1341,7 @@ struct fp8_grouped_graph {
     gb300::Plan plan;
     std::vector<int64_t> sig;
     int max_ctas = 0;
+    void* ws = nullptr;         // split-K workspace owned by the graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t node = nullptr;
@@ -1180,7 +1363,10 @@ int graph_params(fp8_grouped_graph* g, const fp8_gemm_problem* problems, int num
         return FP8_ERR_SHAPE;
     *sig = signature(jobs, bns, n, g->max_ctas);
     memset(&g->prm, 0, sizeof(g->prm));
-    return build_plan(g->prm, jobs, bns, n, g->max_ctas, nullptr, &g->plan);
+    rc = build_plan(g->prm, jobs, bns, n, g->max_ctas, nullptr, &g->plan);
+    if (rc == FP8_OK)
+        bind_workspace(g->prm, g->plan, g->ws);
+    return rc;
 }
 
 cudaKernelNodeParams node_params(fp8_grouped_graph* g, void** args)
@@ -1205,6 +1391,16 @@ extern "C" int gemm_fp8_grouped_graph_create(const fp8_gemm_problem* problems, i
     auto* g = new fp8_grouped_graph;
     g->max_ctas = max_ctas;
     int rc = graph_params(g, problems, num_problems, &g->sig);
+    const size_t bytes = rc == FP8_OK ? gb300::workspace_bytes(g->plan) : 0;
+    if (bytes) {
+        // a persistent split-K workspace; its counters start (and stay) zero
+        if (cudaMalloc(&g->ws, bytes) != cudaSuccess)
+            rc = FP8_ERR_OOM;
+        else if (cudaMemset(g->ws, 0, bytes) != cudaSuccess)
+            rc = FP8_ERR_CUDA;
+        else
+            gb300::bind_workspace(g->prm, g->plan, g->ws);
+    }
     void* args[1];
     if (rc == FP8_OK) {
         cudaKernelNodeParams kp = node_params(g, args);
@@ -1218,6 +1414,8 @@ extern "C" int gemm_fp8_grouped_graph_create(const fp8_gemm_problem* problems, i
             cudaGraphExecDestroy(g->exec);
         if (g->graph)
             cudaGraphDestroy(g->graph);
+        if (g->ws)
+            cudaFree(g->ws);
         delete g;
         return rc;
     }
@@ -1258,6 +1456,8 @@ extern "C" int gemm_fp8_grouped_graph_destroy(fp8_grouped_graph* g)
         return FP8_ERR_INVALID;
     cudaGraphExecDestroy(g->exec);
     cudaGraphDestroy(g->graph);
+    if (g->ws)
+        cudaFree(g->ws);
     delete g;
     return FP8_OK;
 }

@@ -187,3 +187,27 @@ def test_tile_configs_bitwise_equal_and_correct(gb, orc, tile_cfg, M, N, K, gm):
         outs.append(_gemm(gb, A, B, dA, 1, dB, 1, 1.0, gb.OUT_F32))
     assert np.array_equal(outs[0], outs[1])
     parity.check_fp32(outs[1], orc.gemm(A, B, dA, 1, dB, 1))
+
+
+@pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (1, 8192, 2048), (1024, 1024, 1024),
+                                   (100, 300, 2000)])
+def test_split_k_repeatable_and_correct(gb, orc, M, N, K):
+    """Few 128-row tiles: K is split across CTAs (partials in a stream-ordered
+    workspace, the last unit of each tile adds them in slice order).  Calls
+    repeat bit for bit (the tile counters reset themselves) and match the
+    oracle."""
+    A, dA, B, dB = _quantized(M, N, K, 1, 1, orc, seed=M + 5)
+    C1 = _gemm(gb, A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16)
+    C2 = _gemm(gb, A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16)
+    assert np.array_equal(C1, C2)
+    ref = orc.gemm(A, B, dA, 1, dB, 1)
+    S = orc.gemm(parity.abs_codes(A), parity.abs_codes(B), dA, 1, dB, 1)
+    parity.check_bf16(C1, ref, S, K)
+
+
+def test_split_k_integers_exact(gb, orc):
+    A = workloads.small_int_codes((8, 6144), seed=91)
+    B = workloads.small_int_codes((2048, 6144), seed=92)
+    one = np.ones(1, np.float32)
+    C = _gemm(gb, A, B, one, 0, one, 0, 1.0, gb.OUT_F32)
+    assert np.array_equal(C.astype(np.float64), orc.gemm(A, B, one, 0, one, 0))

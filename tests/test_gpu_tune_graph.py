@@ -31,7 +31,7 @@ def _problems(gb, orc, shapes, seed):
     return probs, outs, keep
 
 
-SHAPES = [(1024, 768, 1024), (512, 2048, 512), (2048, 1024, 256)]
+SHAPES = [(1024, 768, 1024), (512, 2048, 512), (2048, 1024, 256), (16, 4096, 2048)]
 
 
 def test_autotune_picks_a_config_and_keeps_results(gb, orc, tmp_path):
@@ -70,10 +70,13 @@ def test_graph_launch_equals_direct_and_updates_pointers(gb, orc):
     for c in outs1 + outs2:
         c.zero_()
     g = gb.GroupedGraph(probs1)
-    g.launch()
-    torch.cuda.synchronize()
-    for a, b in zip(ref1, outs1):
-        assert torch.equal(a, b)
+    for _ in range(2):                     # replays reuse the graph's split-K workspace
+        for c in outs1:
+            c.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        for a, b in zip(ref1, outs1):
+            assert torch.equal(a, b)
     g.update(probs2)                       # same shapes, new pointers: no re-capture
     g.launch()
     torch.cuda.synchronize()
