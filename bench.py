@@ -526,6 +526,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--sweep", default=None,
                     help="write the config 2-4 shape sweep to this JSON file and exit")
+    ap.add_argument("--gemm", default=None,
+                    help="M,N,K[,sparse]: run only this GEMM (warmup + steps launches; for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -537,6 +539,22 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     gb.library()
+    if args.gemm:
+        f = args.gemm.split(",")
+        M, N, K = (int(v) for v in f[:3])
+        x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 1)
+        C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+        if len(f) > 3 and f[3] == "sparse":
+            vals, meta = gb.prune24_compress(A)
+            fn = lambda: gb.gemm_fp8_sparse24(vals, meta, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C)
+        else:
+            fn = lambda: gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C)
+        for _ in range(args.warmup + args.steps):
+            fn()
+        torch.cuda.synchronize()
+        ms = _time_ms(fn)
+        print(json.dumps({"gemm": args.gemm, "ms": ms, "tflops": 2.0 * M * N * K / ms / 1e9}))
+        return 0
     if args.sweep:
         res = sweep(gb, dev)
         pk, pk_kind = peaks()

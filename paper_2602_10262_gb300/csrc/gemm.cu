@@ -674,14 +674,20 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, in
     return r == CUDA_SUCCESS;
 }
 
-// N of the MMA tile for a problem whose N side has rows_q rows.
-int pick_bn(int64_t rows_q, int bn_max)
+// N of the MMA tile for a problem of rows_p x rows_q: the smallest of
+// {16, 32, 64, 128, 256} covering rows_q, then halved (down to 64) while the
+// problem has fewer 128-row tiles than SMs, so small problems still occupy
+// the GPU.  Depends on the problem only (not on what it is launched with).
+int pick_bn(int64_t rows_p, int64_t rows_q, int bn_max)
 {
     int bn = 256;
     if (rows_q <= 16) bn = 16;
     else if (rows_q <= 32) bn = 32;
     else if (rows_q <= 64) bn = 64;
     else if (rows_q <= 128) bn = 128;
+    const int64_t m_blocks = (rows_p + BM - 1) / BM;
+    while (bn > 64 && m_blocks * ((rows_q + bn - 1) / bn) < sm_count())
+        bn /= 2;
     return bn < bn_max ? bn : bn_max;
 }
 
@@ -744,19 +750,21 @@ int validate(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, con
     return FP8_OK;
 }
 
-// Split-K: k-slices for a problem with too few 128-row tiles to occupy the
-// GPU.  Decided from the problem alone (its tile count at N tile width
-// pick_bn(rows_q, 256), the SM count and K), never from what it is launched
-// with, so a problem sums its K range the same way alone, grouped or under
-// any tile configuration.  Every slice gets at least two k-blocks and none is
-// empty.
+// Split-K: k-slices for a narrow-N problem (N tile <= 64, i.e. a skinny
+// product whose long side alone sets the tile count) with too few tiles to
+// occupy the GPU: each SM streams operands at a fraction of HBM bandwidth,
+// so more SMs must share the long operand.  Decided from the problem alone
+// (its tile count at pick_bn(rows_p, rows_q, 256), the SM count and K),
+// never from what it is launched with, so a problem sums its K range the same
+// way alone, grouped or under any tile configuration.  Every slice gets at
+// least two k-blocks and none is empty.
 int split_count(const Job& j)
 {
     const int sms = sm_count();
-    const int64_t bn = pick_bn(j.rows_q, BN_MAX);
+    const int64_t bn = pick_bn(j.rows_p, j.rows_q, BN_MAX);
     const int64_t tiles = ((j.rows_p + BM - 1) / BM) * ((j.rows_q + bn - 1) / bn);
     const int k_blocks = static_cast<int>((j.K + BK - 1) / BK);
-    if (tiles <= 0 || 2 * tiles > sms)
+    if (bn > 64 || tiles <= 0 || 2 * tiles > sms)
         return 1;
     int s = std::min<int64_t>(8, sms / tiles);
     s = std::min(s, k_blocks / 2);
@@ -1076,7 +1084,7 @@ extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A,
         return write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
                      ldc, out_dtype, 0);
-    const int bn = pick_bn(j.rows_q, BN_MAX);
+    const int bn = pick_bn(j.rows_p, j.rows_q, BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     return run_jobs(prm, &j, &bn, 1, 0, st);
@@ -1101,7 +1109,7 @@ extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t*
                               : write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, a_vals, K / 2, a_meta, B, ldb, a_scale, a_mode, b_scale, b_mode,
                      alpha, C, ldc, out_dtype, out_transposed);
-    const int bn = pick_bn(j.rows_q, SPARSE_BN_MAX);
+    const int bn = pick_bn(j.rows_p, j.rows_q, SPARSE_BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     return run_jobs(prm, &j, &bn, 1, 0, st);
@@ -1162,7 +1170,7 @@ int grouped_jobs(const fp8_gemm_problem* problems, int num_problems, cudaStream_
         jobs[n] = make_job(g.M, g.N, g.K, g.A, sp ? g.K / 2 : g.lda, g.A_meta, g.B, g.ldb,
                            g.a_scale, g.a_mode, g.b_scale, g.b_mode, g.alpha, g.C, g.ldc,
                            g.out_dtype, g.out_transposed);
-        bns[n] = pick_bn(jobs[n].rows_q, bn_max);
+        bns[n] = pick_bn(jobs[n].rows_p, jobs[n].rows_q, bn_max);
         ++n;
     }
     *n_out = n;
