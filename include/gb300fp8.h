@@ -138,6 +138,12 @@ int prune24_decompress(const uint8_t *a_vals, const uint8_t *a_meta, int64_t M, 
  * memory accumulators); the epilogue applies the scales in FP32.
  * C: device [M, N], row stride ldc elements, out_dtype 0 = fp32,
  * 1 = bf16 (round to nearest even).
+ * Skinny products whose N-side tiles are too few to occupy the GPU are split
+ * along K over several CTAs; their FP32 partial sums go through a workspace
+ * taken from the stream-ordered allocator (cudaMallocAsync / cudaFreeAsync
+ * on `stream`) and are added in a fixed order, so results are deterministic
+ * and do not depend on how the problem is launched (FP8_ERR_OOM if that
+ * allocation fails).
  * ------------------------------------------------------------------------- */
 int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
                    const uint8_t *B, int64_t ldb, const float *a_scale, int a_mode,

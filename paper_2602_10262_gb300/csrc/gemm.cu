@@ -750,10 +750,10 @@ int validate(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, con
     return FP8_OK;
 }
 
-// Split-K: k-slices for a narrow-N problem (N tile <= 64, i.e. a skinny
-// product whose long side alone sets the tile count) with too few tiles to
-// occupy the GPU: each SM streams operands at a fraction of HBM bandwidth,
-// so more SMs must share the long operand.  Decided from the problem alone
+// Split-K: k-slices for a skinny problem (N-side extent <= 64, so its long
+// side alone sets the tile count) with too few tiles to occupy the GPU: each
+// SM streams operands at a fraction of HBM bandwidth, so more SMs must share
+// the long operand.  Decided from the problem alone
 // (its tile count at pick_bn(rows_p, rows_q, 256), the SM count and K),
 // never from what it is launched with, so a problem sums its K range the same
 // way alone, grouped or under any tile configuration.  Every slice gets at
@@ -764,7 +764,7 @@ int split_count(const Job& j)
     const int64_t bn = pick_bn(j.rows_p, j.rows_q, BN_MAX);
     const int64_t tiles = ((j.rows_p + BM - 1) / BM) * ((j.rows_q + bn - 1) / bn);
     const int k_blocks = static_cast<int>((j.K + BK - 1) / BK);
-    if (bn > 64 || tiles <= 0 || 2 * tiles > sms)
+    if (j.rows_q > 64 || tiles <= 0 || 2 * tiles > sms)
         return 1;
     int s = std::min<int64_t>(8, sms / tiles);
     s = std::min(s, k_blocks / 2);
