@@ -151,6 +151,39 @@ int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t ld
                    int out_dtype, fp8_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * gemm_fp8_dense without any device allocation.  (The paper has no
+ * counterpart: this serves callers of the library.)
+ *
+ * Same arguments, results and errors as gemm_fp8_dense.  That call takes the
+ * scratch of a split-K launch (partial sums of skinny products, see above)
+ * from the stream-ordered allocator; this one uses a fixed 4 MiB array that
+ * the library keeps in every device's global memory instead, so it never
+ * calls cudaMalloc, cudaMallocAsync or any other allocating routine.  It is
+ * meant for callers that must not allocate while serving a request: systems
+ * that plan their whole device memory budget up front (a failed or blocking
+ * allocation mid-request is not acceptable there), and code that runs inside
+ * an allocator's own callbacks or out-of-memory handling, where allocating
+ * again would re-enter the allocator.
+ *
+ * Limits and caveats:
+ *   - a problem whose split-K scratch exceeds 4 MiB is rejected with
+ *     FP8_ERR_SHAPE and nothing is launched.  The scratch is
+ *     tiles x slices x 128 x (N-tile width) floats: skinny products with
+ *     M <= 32 always fit; the largest M <= 64 ones (long side near 9600
+ *     rows) do not.  Problems that do not split need none and always run;
+ *   - all calls on a device share the array, which keeps the previous call's
+ *     contents; each call zeroes the counters it needs (cudaMemsetAsync, not
+ *     an allocation).  Calls whose kernels overlap on the GPU (for example on
+ *     two streams at once) race on the array: serialise them;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ * ------------------------------------------------------------------------- */
+int gemm_fp8_dense_noalloc(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
+                           const uint8_t *B, int64_t ldb, const float *a_scale, int a_mode,
+                           const float *b_scale, int b_mode, float alpha, void *C, int64_t ldc,
+                           int out_dtype, fp8_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * 2:4-sparse FP8 GEMM (rows a5, a6).  Paper: section 6 (sparse GEMM against
  * dense GEMM on the same operands).
  *

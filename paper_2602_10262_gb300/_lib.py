@@ -82,6 +82,7 @@ SIGNATURES = {
     "prune24_compress": (I32, [P, I64, I64, I64, P, P, P]),
     "prune24_decompress": (I32, [P, P, I64, I64, P, P]),
     "gemm_fp8_dense": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32, P]),
+    "gemm_fp8_dense_noalloc": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32, P]),
     "gemm_fp8_sparse24": (I32, [I64, I64, I64, P, P, P, I64, P, I32, P, I32, F32, P, I64, I32, I32, P]),
     "gemm_fp8_grouped": (I32, [ctypes.POINTER(FP8Problem), I32, P]),
     "gemm_fp8_grouped_ex": (I32, [ctypes.POINTER(FP8Problem), I32, I32, P]),

@@ -1090,6 +1090,76 @@ extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A,
     return run_jobs(prm, &j, &bn, 1, 0, st);
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+
+namespace gb300 {
+namespace {
+
+// Device scratch of gemm_fp8_dense_noalloc: the split-K partial sums and tile
+// counters live here instead of in memory allocated per call.  Every device
+// that loads the library holds this array until the process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (host code only has a stand-in for the symbol).
+int noalloc_scratch(void** out)
+{
+    static std::once_flag once[64];
+    static void* addr[64];
+    static cudaError_t err[64];
+    int dev = 0;
+    GB_CUDA_OK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64)
+        return FP8_ERR_UNSUPPORTED;
+    std::call_once(once[dev], [dev] { err[dev] = cudaGetSymbolAddress(&addr[dev], g_noalloc_scratch); });
+    GB_CUDA_OK(err[dev]);
+    *out = addr[dev];
+    return FP8_OK;
+}
+
+}  // namespace
+}  // namespace gb300
+
+extern "C" int gemm_fp8_dense_noalloc(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
+                                      const uint8_t* B, int64_t ldb, const float* a_scale,
+                                      int a_mode, const float* b_scale, int b_mode, float alpha,
+                                      void* C, int64_t ldc, int out_dtype, fp8_stream_t stream)
+{
+    using namespace gb300;
+    int rc = validate(M, N, K, A, lda, nullptr, false, B, ldb, a_scale, a_mode, b_scale, b_mode, C,
+                      ldc, out_dtype, 0);
+    if (rc != FP8_OK || M == 0 || N == 0)
+        return rc;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (K == 0)
+        return write_zeros(C, ldc, M, N, out_dtype, st);
+    Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
+                     ldc, out_dtype, 0);
+    const int bn = pick_bn(j.rows_p, j.rows_q, BN_MAX);
+    Params<1> prm;
+    memset(&prm, 0, sizeof(prm));
+    Plan pl;
+    rc = build_plan(prm, &j, &bn, 1, 0, nullptr, &pl);
+    if (rc != FP8_OK)
+        return rc;
+    const size_t bytes = workspace_bytes(pl);
+    if (bytes > kNoAllocScratchBytes)
+        return FP8_ERR_SHAPE;                    // needs more scratch than the fixed array holds
+    void* scratch = nullptr;
+    if (bytes) {
+        rc = noalloc_scratch(&scratch);
+        if (rc != FP8_OK)
+            return rc;
+    }
+    bind_workspace(prm, pl, scratch);
+    if (bytes)
+        GB_CUDA_OK(cudaMemsetAsync(prm.ctr, 0, pl.ctr_count * sizeof(unsigned), st));
+    return launch_plan(prm, pl, st);
+}
+
 extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t* a_vals,
                                  const uint8_t* a_meta, const uint8_t* B, int64_t ldb,
                                  const float* a_scale, int a_mode, const float* b_scale, int b_mode,
