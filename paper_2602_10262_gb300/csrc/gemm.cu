@@ -55,9 +55,10 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 //          (cols 0 / 256) so the epilogue of tile i overlaps the MMAs of tile
 //          i + 1.  BNC caps bn for the launch and sizes the ring: BNC = 256,
 //          4 stages of 48 KB (metadata ring at cols 240..255, bn <= 240 for
-//          sparse problems); BNC = 128, 6 stages of 32 KB; BNC = 64, 8 stages
-//          of 24 KB (narrow N, e.g. skinny products whose small M is the MMA
-//          N: more bytes in flight per SM where few tiles exist);
+//          sparse problems); BNC = 128, 6 stages of 32 KB; BNC = 64 / 32 /
+//          16: 8 / 9 / 11 stages of 24 / 20 / 18 KB (narrow N, e.g. skinny
+//          products whose small M is the MMA N: more loads in flight per SM
+//          where few tiles exist);
 //  MT = 2: tile 256 x bn; two MMAs per k-step share the B tile (a third fewer
 //          operand bytes per FLOP); one accumulator spanning all 512 columns
 //          (rows 0-127 in cols 0-255, rows 128-255 in cols 256-511).  Dense
@@ -67,7 +68,8 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 template <int MT, bool SP = false, int BNC = BN_MAX>
 struct Cfg {
     static constexpr bool kSparse2 = MT == 2 && SP;
-    static constexpr int kStages = MT == 2 ? (SP ? 4 : 3) : (BNC == 256 ? 4 : (BNC == 128 ? 6 : 8));
+    static constexpr int kStages =
+        MT == 2 ? (SP ? 4 : 3) : (BNC == 256 ? 4 : (BNC == 128 ? 6 : (BNC == 64 ? 8 : (BNC == 32 ? 9 : 11))));
     static constexpr int kABytes = MT == 1 ? BM * BK : (SP ? 2 * BM * (BK / 2 + BK / 8) : 2 * BM * BK);
     static constexpr int kBBytes = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : BNC * BK;
     static constexpr int kStageBytes = kABytes + kBBytes;
@@ -83,7 +85,7 @@ struct Cfg {
                   "sparse A + metadata fit the A region");
     static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "swizzle atoms stay aligned");
     static_assert(kSmem <= 232448, "shared memory per CTA");
-    static_assert(2 * kStages + 2 * kAcc + 3 <= 28, "barriers fit their 256-byte region");
+    static_assert((2 * kStages + 2 * kAcc + 3) * 8 + 12 <= 256, "barriers and flags fit their 256-byte region");
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
 };
 
@@ -999,6 +1001,10 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
         int max_bn = 0;
         for (int i = 0; i < n; ++i)
             max_bn = std::max(max_bn, bns_in[i]);
+        if (max_bn <= 16)
+            return plan<MAXP, 1, false, 16>(prm, max_ctas, pl);
+        if (max_bn <= 32)
+            return plan<MAXP, 1, false, 32>(prm, max_ctas, pl);
         if (max_bn <= 64)
             return plan<MAXP, 1, false, 64>(prm, max_ctas, pl);
         if (max_bn <= 128)
