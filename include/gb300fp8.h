@@ -59,7 +59,11 @@ const char *fp8_status_string(int status);
  * current device (FP8_OK if no kernel reported an error since the last call).
  * Kernels record FP8_ERR_NONFINITE (quantisation saw NaN/Inf) and
  * FP8_ERR_TIMEOUT (an mbarrier wait exceeded its ~2 s limit; the kernel then
- * stops its pipeline, releases tensor memory and exits). */
+ * stops its pipeline, releases tensor memory and exits).  When the word was
+ * set, the call also synchronises the device and re-zeroes the split-K tile
+ * counters of the library's persistent workspaces (a GEMM that stopped early
+ * may have left one part-way); results of GEMMs launched between the failed
+ * one and this call are unspecified. */
 int fp8_last_device_error(fp8_stream_t stream);
 
 /* Number of SMs of the current device (persistent grids are sized from it). */
@@ -138,12 +142,20 @@ int prune24_decompress(const uint8_t *a_vals, const uint8_t *a_meta, int64_t M, 
  * memory accumulators); the epilogue applies the scales in FP32.
  * C: device [M, N], row stride ldc elements, out_dtype 0 = fp32,
  * 1 = bf16 (round to nearest even).
- * Skinny products whose N-side tiles are too few to occupy the GPU are split
- * along K over several CTAs; their FP32 partial sums go through a workspace
- * taken from the stream-ordered allocator (cudaMallocAsync / cudaFreeAsync
- * on `stream`) and are added in a fixed order, so results are deterministic
- * and do not depend on how the problem is launched (FP8_ERR_OOM if that
- * allocation fails).
+ * Skinny products whose N-side tiles are too few to occupy the GPU (and
+ * whose K is at least 2048) are split along K over several CTAs; their FP32
+ * partial sums go through a workspace and are added in a fixed order, so
+ * results are deterministic and do not depend on how the problem is
+ * launched.  The workspace is a buffer kept per stream (allocated with
+ * cudaMallocAsync on `stream` at the first split launch, grown the same way,
+ * kept for the life of the process; at most 64 streams get one; calls on
+ * further streams allocate and free one per call, ordered on `stream`).  A
+ * call made while `stream` is being captured gives the captured graph a
+ * workspace of its own: allocated at capture time outside the capture, freed
+ * once the graph and every executable graph made from it are destroyed, so
+ * replays allocate nothing.  Replays of one executable graph are ordered by
+ * CUDA; two executable graphs instantiated from the same captured graph must
+ * not be replayed at the same time.  FP8_ERR_OOM if an allocation fails.
  * ------------------------------------------------------------------------- */
 int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
                    const uint8_t *B, int64_t ldb, const float *a_scale, int a_mode,
@@ -154,9 +166,9 @@ int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t ld
  * gemm_fp8_dense without any device allocation.  (The paper has no
  * counterpart: this serves callers of the library.)
  *
- * Same arguments, results and errors as gemm_fp8_dense.  That call takes the
- * scratch of a split-K launch (partial sums of skinny products, see above)
- * from the stream-ordered allocator; this one uses a fixed 4 MiB array that
+ * Same arguments, results and errors as gemm_fp8_dense.  That call may
+ * allocate the scratch of a split-K launch (partial sums of skinny products,
+ * see above) with cudaMallocAsync; this one uses a fixed 4 MiB array that
  * the library keeps in every device's global memory instead, so it never
  * calls cudaMalloc, cudaMallocAsync or any other allocating routine.  It is
  * meant for callers that must not allocate while serving a request: systems
@@ -168,9 +180,12 @@ int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t ld
  * Limits and caveats:
  *   - a problem whose split-K scratch exceeds 4 MiB is rejected with
  *     FP8_ERR_SHAPE and nothing is launched.  The scratch is
- *     tiles x slices x 128 x (N-tile width) floats: skinny products with
- *     M <= 32 always fit; the largest M <= 64 ones (long side near 9600
- *     rows) do not.  Problems that do not split need none and always run;
+ *     256 bytes of counters plus tiles x slices x 128 x (N-tile width)
+ *     floats, with tiles x slices at most the SM count (only products with
+ *     M <= 64 split): skinny products with M <= 32 always fit; those with
+ *     33 <= M <= 64 fit while that total stays within 4 MiB (M = 64 with a
+ *     long side of 8192 rows split in two needs 4 MiB + 256 bytes and is
+ *     rejected).  Problems that do not split need none and always run;
  *   - all calls on a device share the array, which keeps the previous call's
  *     contents; each call zeroes the counters it needs (cudaMemsetAsync, not
  *     an allocation).  Calls whose kernels overlap on the GPU (for example on

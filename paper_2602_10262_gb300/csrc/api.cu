@@ -84,6 +84,7 @@ extern "C" int fp8_last_device_error(fp8_stream_t stream)
     if (v != 0) {
         const int zero = 0;
         GB_CUDA_OK(cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        gb300::reset_split_counters();
     }
     return v;
 }

@@ -27,6 +27,31 @@ int sm_count();
 // True when the current device is an sm_103 part this library was built for.
 bool device_supported();
 
+// Re-zero the split-K tile counters of every persistent workspace on the
+// current device (per-stream caches and grouped graphs).  Called after the
+// device error word was found set: a launch that stopped early may have left
+// a counter part-way.  Synchronises the device.
+void reset_split_counters();
+
+// Programmatic dependent launch.  A grid launched with programmatic stream
+// serialization may start before the previous grid on its stream ends; it
+// must pass grid_dependency_wait (which returns once those grids have
+// completed and their memory is visible; at once for a grid launched
+// without the attribute) before it reads or writes global memory they use.
+__device__ __forceinline__ void grid_dependency_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Lets grids launched after this one with programmatic serialization begin
+// (their setup overlaps this grid's tail) once every CTA of this grid has
+// executed it or exited.  It does not release them past their
+// grid_dependency_wait.
+__device__ __forceinline__ void grid_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 inline bool aligned16(const void* p)
 {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;

@@ -28,7 +28,9 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <map>
+#include <memory>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "common.cuh"
@@ -89,10 +91,10 @@ struct Cfg {
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
 };
 
-struct Problem {
-    CUtensorMap tmP;        // P [rows_p, K] codes, box {128, 128 * MT}
-    CUtensorMap tmQ;        // Q [rows_q, K] codes, box {128, bn}
-    CUtensorMap tmE;        // sparse only: metadata [rows_p, K/8], box {16, 128 * MT}
+// Everything of a problem but its tensor maps.  Each role thread copies this
+// part into registers once per tile, so its inner loops read no kernel
+// parameter memory.
+struct ProblemScalars {
     const float* sp;        // scale of P rows (mode sp_mode)
     const float* sq;        // scale of Q rows
     void* C;
@@ -112,6 +114,12 @@ struct Problem {
     int ctr_off;            // split-K: first tile counter of this problem
     int tile_start;         // first work unit (tile x slice) of this problem
     uint32_t idesc;
+};
+
+struct Problem : ProblemScalars {
+    CUtensorMap tmP;        // P [rows_p, K] codes, box {128, 128 * MT}
+    CUtensorMap tmQ;        // Q [rows_q, K] codes, box {128, bn}
+    CUtensorMap tmE;        // sparse only: metadata [rows_p, K/8], box {16, 128 * MT}
 };
 
 template <int MAXP>
@@ -136,7 +144,7 @@ __device__ __forceinline__ TileCoord tile_coord(const Params<MAXP>& prm, int til
 {
     int p = 0;
 #pragma unroll 1
-    while (p + 1 < prm.num_problems && prm.prob[p + 1].tile_start <= tile)
+    while (p + 1 < MAXP && p + 1 < prm.num_problems && prm.prob[p + 1].tile_start <= tile)
         ++p;
     const Problem& P = prm.prob[p];
     const int unit = tile - P.tile_start;
@@ -158,16 +166,47 @@ __device__ __forceinline__ void abort_pipeline(volatile int* flag, int* err)
 
 // ---------------------------------------------------------------- epilogue
 
+// Column scales of the tile, 32 columns (one window) at a time: lane l
+// holds the scale of column 32 w + l of window w (0 past the last column).
+// Two windows are kept loaded ahead of use, and the first two are loaded
+// before the epilogue waits for the accumulator, so the scale loads do not
+// add their latency to the epilogue.
+struct ScaleWindows {
+    float w0, w1;           // the next two windows to hand out
+    int next;               // tile column of the window after w1
+
+    __device__ __forceinline__ static float load(const ProblemScalars& P, int j, int lane)
+    {
+        j += lane;
+        return j < P.rows_q ? __ldg(P.sq + (P.sq_mode ? j : 0)) : 0.0f;
+    }
+    __device__ __forceinline__ void init(const ProblemScalars& P, int jbase, int lane)
+    {
+        w0 = load(P, jbase, lane);
+        w1 = P.bn > 32 ? load(P, jbase + 32, lane) : 0.0f;
+        next = 64;
+    }
+    // The window at tile columns 32 k .. 32 k + 31 for k = 0, 1, 2, ... in turn.
+    __device__ __forceinline__ float take(const ProblemScalars& P, int jbase, int lane)
+    {
+        const float s = w0;
+        w0 = w1;
+        w1 = next < P.bn ? load(P, jbase + next, lane) : 0.0f;
+        next += 32;
+        return s;
+    }
+};
+
 // Scale 16 accumulator values (columns j0 .. j0+15 of row i) and store them.
-__device__ __forceinline__ void store_vals16(const Problem& P, int i, bool row_ok, float fi, int j0,
-                                             const float (&acc)[16])
+// sw: the scale window holding those columns, at lane offset j_off.
+__device__ __forceinline__ void store_vals16(const ProblemScalars& P, int i, bool row_ok, float fi, int j0,
+                                             const float (&acc)[16], float sw, int j_off)
 {
     float v[16];
     const int rows_q = P.rows_q;
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
-        const int j = j0 + t;
-        const float sj = (j < rows_q) ? __ldg(P.sq + (P.sq_mode ? j : 0)) : 0.0f;
+        const float sj = __shfl_sync(0xFFFFFFFFu, sw, j_off + t);
         v[t] = __fmul_rn(__fmul_rn(acc[t], fi), sj);
     }
     if (!row_ok)
@@ -222,19 +261,19 @@ __device__ __forceinline__ void store_vals16(const Problem& P, int i, bool row_o
     }
 }
 
-__device__ __forceinline__ void store_chunk16(const Problem& P, int i, bool row_ok, float fi,
-                                              int j0, const uint32_t (&r)[16])
+__device__ __forceinline__ void store_chunk16(const ProblemScalars& P, int i, bool row_ok, float fi,
+                                              int j0, const uint32_t (&r)[16], float sw, int j_off)
 {
     float acc[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t)
         acc[t] = __uint_as_float(r[t]);
-    store_vals16(P, i, row_ok, fi, j0, acc);
+    store_vals16(P, i, row_ok, fi, j0, acc, sw, j_off);
 }
 
 // Split-K, part 1: this unit's partial sums (row `row` of the tile, straight
 // from TMEM) go to its slot of the workspace.
-__device__ __forceinline__ void split_write_partial(const Problem& P, float* ws, int rows_per_tile,
+__device__ __forceinline__ void split_write_partial(const ProblemScalars& P, float* ws, int rows_per_tile,
                                                     int tile, int slice, int row, uint32_t taddr)
 {
     float* dst = ws + P.ws_off + (static_cast<long long>(tile) * P.splits + slice) * rows_per_tile * P.bn +
@@ -253,13 +292,17 @@ __device__ __forceinline__ void split_write_partial(const Problem& P, float* ws,
 
 // Split-K, part 2 (the tile's last unit only): add the partials of every
 // slice in slice order and store the scaled result.
-__device__ __forceinline__ void split_reduce_store(const Problem& P, const float* ws, int rows_per_tile,
-                                                   int tile, int row, int i, bool row_ok, float fi, int jbase)
+__device__ __forceinline__ void split_reduce_store(const ProblemScalars& P, const float* ws, int rows_per_tile,
+                                                   int tile, int row, int i, bool row_ok, float fi, int jbase,
+                                                   ScaleWindows& sw, int lane)
 {
     const float* src = ws + P.ws_off + static_cast<long long>(tile) * P.splits * rows_per_tile * P.bn +
                        static_cast<long long>(row) * P.bn;
     const long long slot = static_cast<long long>(rows_per_tile) * P.bn;
+    float s_cur = 0.0f;
     for (int c0 = 0; c0 < P.bn; c0 += 16) {
+        if ((c0 & 31) == 0)
+            s_cur = sw.take(P, jbase, lane);
         float acc[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t)
@@ -274,7 +317,7 @@ __device__ __forceinline__ void split_reduce_store(const Problem& P, const float
                 acc[4 * t + 3] = __fadd_rn(acc[4 * t + 3], v.w);
             }
         }
-        store_vals16(P, i, row_ok, fi, jbase + c0, acc);
+        store_vals16(P, i, row_ok, fi, jbase + c0, acc, s_cur, c0 & 31);
     }
 }
 
@@ -285,22 +328,17 @@ __device__ __forceinline__ void split_reduce_store(const Problem& P, const float
 // buffer (16-byte pieces XOR-swizzled by row: conflict-free on both sides);
 // then 8 lanes per row copy 4 rows x 128 contiguous bytes per instruction.
 template <int ESZ>
-__device__ __forceinline__ void epilogue_rows_coalesced(const Problem& P, uint32_t taddr, int row0,
-                                                        float fi, int jbase, uint8_t* buf, int lane)
+__device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P, uint32_t taddr, int row0,
+                                                        float fi, int jbase, uint8_t* buf, int lane,
+                                                        ScaleWindows& sw)
 {
     constexpr int CW = 128 / ESZ;                     // columns per chunk
     const int rows_q = P.rows_q;
     for (int c0 = 0; c0 < P.bn; c0 += CW) {
         const int cw = min(CW, P.bn - c0);           // multiple of 16
         // column scales of the chunk: lane l holds columns c0 + l and c0 + 32 + l
-        float s_lo = 0.0f, s_hi = 0.0f;
-        {
-            const int j = jbase + c0 + lane;
-            if (j < rows_q)
-                s_lo = __ldg(P.sq + (P.sq_mode ? j : 0));
-            if (CW > 32 && j + 32 < rows_q)
-                s_hi = __ldg(P.sq + (P.sq_mode ? j + 32 : 0));
-        }
+        const float s_lo = sw.take(P, jbase, lane);
+        const float s_hi = (CW > 32 && c0 + 32 < P.bn) ? sw.take(P, jbase, lane) : 0.0f;
         uint32_t packed[32];
 #pragma unroll
         for (int q = 0; q < CW; q += 16) {
@@ -387,6 +425,14 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    grid_launch_dependents();
+    // The first tile's coordinates and tensor maps are fetched before the
+    // setup below, so their parameter loads overlap it.
+    const TileCoord tc_first = tile_coord(prm, blockIdx.x);
+    if (threadIdx.x == 0) {
+        tma_prefetch_desc(&prm.prob[tc_first.p].tmP);
+        tma_prefetch_desc(&prm.prob[tc_first.p].tmQ);
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -412,44 +458,54 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // Everything above reads only the kernel parameters and shared memory;
+    // from here on the previous kernel's outputs (operands, scales, the
+    // split-K workspace) are read and written.
+    grid_dependency_wait();
 
     // Roles are chosen per warp; inside warps 0 and 1 only lane 0 works.
     if (warp == 0) {
         if (lane == 0) {
             // ------------------------------------------------ TMA producer
-            for (int p = 0; p < prm.num_problems; ++p) {
-                tma_prefetch_desc(&prm.prob[p].tmP);
-                tma_prefetch_desc(&prm.prob[p].tmQ);
-                if (prm.prob[p].sparse)
-                    tma_prefetch_desc(&prm.prob[p].tmE);
-            }
             int stage = 0;
             uint32_t phase = 0;
             uint32_t armed = 0;                 // bit s: slot s armed at least once
             bool ok = true;
             for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x) {
-                const TileCoord tc = tile_coord(prm, tile);
-                const Problem& P = prm.prob[tc.p];
+                const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
+                if (tile != static_cast<int>(blockIdx.x) || prm.prob[tc.p].sparse) {
+                    tma_prefetch_desc(&prm.prob[tc.p].tmP);
+                    tma_prefetch_desc(&prm.prob[tc.p].tmQ);
+                    if (prm.prob[tc.p].sparse)
+                        tma_prefetch_desc(&prm.prob[tc.p].tmE);
+                }
+                const ProblemScalars P = prm.prob[tc.p];
+                const CUtensorMap* map_p = &prm.prob[tc.p].tmP;
+                const CUtensorMap* map_q = &prm.prob[tc.p].tmQ;
+                const CUtensorMap* map_e = &prm.prob[tc.p].tmE;
                 const uint32_t a_bytes = P.sparse ? C::kSpABytes + MT * BM * BK / 8 : C::kABytes;
                 const uint32_t bytes = a_bytes + static_cast<uint32_t>(P.bn) * BK;
                 const int row0 = tc.m_blk * BM * MT;
+                const int col0 = tc.n_blk * P.bn;
+                const bool sparse = P.sparse != 0;
                 const int kb0 = tc.slice * P.kb_per_split;
                 const int kb1 = min(P.k_blocks, kb0 + P.kb_per_split);
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
+                    // a slot never armed is free: no wait on its first use
+                    if (((armed >> stage) & 1u) && !mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
                         ok = false;
                         abort_pipeline(abort_flag, prm.err);
                         break;
                     }
                     mbar_arrive_expect_tx(full_bar(stage), bytes);
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
-                    if (P.sparse) {
-                        tma_load_2d(sa, &P.tmP, full_bar(stage), kb * (BK / 2), row0);
-                        tma_load_2d(sa + C::kSpABytes, &P.tmE, full_bar(stage), kb * (BK / 8), row0);
+                    if (sparse) {
+                        tma_load_2d(sa, map_p, full_bar(stage), kb * (BK / 2), row0);
+                        tma_load_2d(sa + C::kSpABytes, map_e, full_bar(stage), kb * (BK / 8), row0);
                     } else {
-                        tma_load_2d(sa, &P.tmP, full_bar(stage), kb * BK, row0);
+                        tma_load_2d(sa, map_p, full_bar(stage), kb * BK, row0);
                     }
-                    tma_load_2d(sa + C::kABytes, &P.tmQ, full_bar(stage), kb * BK, tc.n_blk * P.bn);
+                    tma_load_2d(sa + C::kABytes, map_q, full_bar(stage), kb * BK, col0);
                     armed |= 1u << stage;
                     if (++stage == S) {
                         stage = 0;
@@ -478,11 +534,14 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
             int local = 0;
             bool ok = true;
             for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x, ++local) {
-                const TileCoord tc = tile_coord(prm, tile);
-                const Problem& P = prm.prob[tc.p];
+                const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
+                const ProblemScalars P = prm.prob[tc.p];
+                const bool sparse = P.sparse != 0;
+                const uint32_t idesc = P.idesc;
                 const int acc = local % C::kAcc;
                 const uint32_t acc_phase = (local / C::kAcc) & 1;
-                if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag)) {
+                // an accumulator not used yet is free: no wait on its first use
+                if (local >= C::kAcc && !mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag)) {
                     abort_pipeline(abort_flag, prm.err);
                     break;
                 }
@@ -501,7 +560,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                     tc_fence_after();
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
                     const uint64_t bdesc = sdesc_kmajor_sw128(sa + C::kABytes);
-                    if (P.sparse) {
+                    if (sparse) {
                         // metadata of this k-block -> TMEM slot of this stage
                         // (tcgen05.cp and the MMAs below execute in issue order)
                         const uint32_t sm_meta = sa + C::kSpABytes;
@@ -521,7 +580,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                                 const uint32_t meta = tmem_base + static_cast<uint32_t>(
                                                                       h * BN_MAX + C::kMetaCol0 + 4 * stage);
                                 mma_sp_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 4u * k,
-                                              meta + 2u * k, P.idesc, (first | k) != 0 ? 1u : 0u);
+                                              meta + 2u * k, idesc, (first | k) != 0 ? 1u : 0u);
                             }
                         }
                     } else {
@@ -532,7 +591,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                                 // advance the start address by 32 bytes (K = 32 codes)
                                 const uint64_t adesc = sdesc_kmajor_sw128(sa + h * BM * BK);
                                 mma_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 2u * k,
-                                           P.idesc, (first | k) != 0 ? 1u : 0u);
+                                           idesc, (first | k) != 0 ? 1u : 0u);
                             }
                         }
                     }
@@ -559,10 +618,17 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
         int local = 0;
         uint32_t split_phase = 0;
         for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++local) {
-            const TileCoord tc = tile_coord(prm, tile);
-            const Problem& P = prm.prob[tc.p];
+            const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
+            const ProblemScalars& P = prm.prob[tc.p];
             const int acc = local % C::kAcc;
             const uint32_t acc_phase = (local / C::kAcc) & 1;
+            // the scales do not depend on the accumulator: load them first
+            const int i = tc.m_blk * BM * MT + row;
+            const bool row_ok = i < P.rows_p;
+            const float fi = row_ok ? __fmul_rn(P.alpha, __ldg(P.sp + (P.sp_mode ? i : 0))) : 0.0f;
+            const int jbase = tc.n_blk * P.bn;
+            ScaleWindows sw;
+            sw.init(P, jbase, lane);
             // the whole warp takes the same branch (tcgen05.ld is warp-collective)
             const bool got = mbar_wait(tfull_bar(acc), acc_phase, abort_flag);
             if (!__all_sync(0xFFFFFFFFu, got)) {
@@ -570,12 +636,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int i = tc.m_blk * BM * MT + row;
-            const bool row_ok = i < P.rows_p;
-            const float fi = row_ok ? __fmul_rn(P.alpha, __ldg(P.sp + (P.sp_mode ? i : 0))) : 0.0f;
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>((acc + half) * BN_MAX);
-            const int jbase = tc.n_blk * P.bn;
             if (P.splits > 1) {
                 // every epilogue thread stores its row's partials, then one
                 // thread counts this unit in; the tile's last unit reduces.
@@ -604,7 +666,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                 }
                 if (*split_flag) {
                     __threadfence();
-                    split_reduce_store(P, prm.ws, BM * MT, tc.tile, row, i, row_ok, fi, jbase);
+                    split_reduce_store(P, prm.ws, BM * MT, tc.tile, row, i, row_ok, fi, jbase, sw, lane);
                     if (threadIdx.x == 64)
                         prm.ctr[P.ctr_off + tc.tile] = 0u;         // ready for the next launch
                 }
@@ -614,15 +676,18 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                 uint8_t* buf = epi_smem + (warp - 2) * 32 * 128;
                 const int row0 = i - lane;
                 if (P.out_bf16)
-                    epilogue_rows_coalesced<2>(P, taddr, row0, fi, jbase, buf, lane);
+                    epilogue_rows_coalesced<2>(P, taddr, row0, fi, jbase, buf, lane, sw);
                 else
-                    epilogue_rows_coalesced<4>(P, taddr, row0, fi, jbase, buf, lane);
+                    epilogue_rows_coalesced<4>(P, taddr, row0, fi, jbase, buf, lane, sw);
             } else {
+                float s_cur = 0.0f;
                 for (int c0 = 0; c0 < P.bn; c0 += 16) {
+                    if ((c0 & 31) == 0)
+                        s_cur = sw.take(P, jbase, lane);
                     uint32_t r[16];
                     tmem_ld_32x32b_x16(taddr + c0, r);
                     tmem_ld_wait();
-                    store_chunk16(P, i, row_ok, fi, jbase + c0, r);
+                    store_chunk16(P, i, row_ok, fi, jbase + c0, r, s_cur, c0 & 31);
                 }
             }
             tc_fence_before();
@@ -676,11 +741,24 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, in
     return r == CUDA_SUCCESS;
 }
 
+// True when a problem is split along K (see split_count): its Q side fits
+// one tile of at most 64 columns, its K spans at least 16 k-blocks and its
+// tiles fill at most half the SMs.  (With 128 columns the split epilogue
+// costs more than narrowing the tile and reading P twice.)
+bool splits_k(int64_t rows_p, int64_t rows_q, int64_t K)
+{
+    const int64_t m_blocks = (rows_p + BM - 1) / BM;
+    return rows_q <= 64 && (K + BK - 1) / BK >= 16 && m_blocks > 0 && 2 * m_blocks <= sm_count();
+}
+
 // N of the MMA tile for a problem of rows_p x rows_q: the smallest of
 // {16, 32, 64, 128, 256} covering rows_q, then halved (down to 64) while the
 // problem has fewer 128-row tiles than SMs, so small problems still occupy
-// the GPU.  Depends on the problem only (not on what it is launched with).
-int pick_bn(int64_t rows_p, int64_t rows_q, int bn_max)
+// the GPU.  A problem that splits along K keeps the full width instead: a
+// narrower tile would read the large P operand once per column block, split
+// partial sums cost far less.  Depends on the problem only (not on what it
+// is launched with).
+int pick_bn(int64_t rows_p, int64_t rows_q, int64_t K, int bn_max)
 {
     int bn = 256;
     if (rows_q <= 16) bn = 16;
@@ -688,8 +766,9 @@ int pick_bn(int64_t rows_p, int64_t rows_q, int bn_max)
     else if (rows_q <= 64) bn = 64;
     else if (rows_q <= 128) bn = 128;
     const int64_t m_blocks = (rows_p + BM - 1) / BM;
-    while (bn > 64 && m_blocks * ((rows_q + bn - 1) / bn) < sm_count())
-        bn /= 2;
+    if (!splits_k(rows_p, rows_q, K))
+        while (bn > 64 && m_blocks * ((rows_q + bn - 1) / bn) < sm_count())
+            bn /= 2;
     return bn < bn_max ? bn : bn_max;
 }
 
@@ -752,24 +831,24 @@ int validate(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, con
     return FP8_OK;
 }
 
-// Split-K: k-slices for a skinny problem (N-side extent <= 64, so its long
-// side alone sets the tile count) with too few tiles to occupy the GPU: each
-// SM streams operands at a fraction of HBM bandwidth, so more SMs must share
-// the long operand.  Decided from the problem alone
-// (its tile count at pick_bn(rows_p, rows_q, 256), the SM count and K),
-// never from what it is launched with, so a problem sums its K range the same
-// way alone, grouped or under any tile configuration.  Every slice gets at
-// least two k-blocks and none is empty.
+// Split-K: k-slices for a skinny problem (Q side <= 64 rows, one column
+// block, so its long side alone sets the tile count) with too few tiles to
+// occupy the GPU: each SM streams operands at a fraction of HBM bandwidth,
+// so more SMs must share the long operand.  Decided from the problem alone
+// (its 128-row tile count, the SM count and K), never from what it is
+// launched with, so a problem sums its K range the same way alone, grouped
+// or under any tile configuration.  Every slice gets at least eight k-blocks
+// (K >= 1024): below that the extra pass over the partials costs more than
+// the shorter K loop saves.  No slice is empty.
 int split_count(const Job& j)
 {
     const int sms = sm_count();
-    const int64_t bn = pick_bn(j.rows_p, j.rows_q, BN_MAX);
-    const int64_t tiles = ((j.rows_p + BM - 1) / BM) * ((j.rows_q + bn - 1) / bn);
-    const int k_blocks = static_cast<int>((j.K + BK - 1) / BK);
-    if (j.rows_q > 64 || tiles <= 0 || 2 * tiles > sms)
+    if (!splits_k(j.rows_p, j.rows_q, j.K))
         return 1;
+    const int64_t tiles = (j.rows_p + BM - 1) / BM;            // one column block
+    const int k_blocks = static_cast<int>((j.K + BK - 1) / BK);
     int s = std::min<int64_t>(8, sms / tiles);
-    s = std::min(s, k_blocks / 2);
+    s = std::min(s, k_blocks / 8);
     if (s <= 1)
         return 1;
     const int kbs = (k_blocks + s - 1) / s;
@@ -831,21 +910,35 @@ struct Plan {
     size_t ctr_count = 0;       // split-K tile counters
 };
 
-// Workspace of a split-K launch: partial sums then counters.
+// Workspace of a split-K launch: the tile counters (a region rounded up to
+// 256 bytes), then the partial sums.  The counters come first so that their
+// slots stay put whatever the size of the partials: in a buffer reused by
+// launches of different shapes a counter slot is only ever a counter.
+size_t ctr_region_bytes(size_t ctr_count)
+{
+    return (ctr_count * sizeof(unsigned) + 255) / 256 * 256;
+}
+
 size_t workspace_bytes(const Plan& pl)
 {
     if (pl.ctr_count == 0)
         return 0;
-    return (pl.ws_floats * sizeof(float) + 255) / 256 * 256 + pl.ctr_count * sizeof(unsigned);
+    return ctr_region_bytes(pl.ctr_count) + pl.ws_floats * sizeof(float);
+}
+
+// Point the launch at a workspace whose counter region holds ctr_cap counters.
+template <int MAXP>
+void bind_workspace(Params<MAXP>& prm, void* base, size_t ctr_cap)
+{
+    prm.ctr = static_cast<unsigned*>(base);
+    prm.ws = base ? reinterpret_cast<float*>(static_cast<uint8_t*>(base) + ctr_region_bytes(ctr_cap))
+                  : nullptr;
 }
 
 template <int MAXP>
 void bind_workspace(Params<MAXP>& prm, const Plan& pl, void* base)
 {
-    prm.ws = static_cast<float*>(base);
-    prm.ctr = base ? reinterpret_cast<unsigned*>(static_cast<uint8_t*>(base) +
-                                                 (pl.ws_floats * sizeof(float) + 255) / 256 * 256)
-                   : nullptr;
+    bind_workspace(prm, base, pl.ctr_count);
 }
 
 template <int MAXP, int MT, bool SP, int BNC = BN_MAX>
@@ -897,8 +990,20 @@ int launch_plan(Params<MAXP>& prm, const Plan& pl, cudaStream_t st)
     if (pl.grid == 0)
         return FP8_OK;
     void* args[] = {&prm};
-    GB_CUDA_OK(cudaLaunchKernel(pl.func, dim3(pl.grid), dim3(pl.threads), args,
-                                static_cast<size_t>(pl.smem), st));
+    // programmatic stream serialization: the kernel's setup may overlap the
+    // tail of the previous kernel on `st` (it waits for it before touching
+    // global memory)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pl.grid);
+    cfg.blockDim = dim3(pl.threads);
+    cfg.dynamicSmemBytes = static_cast<size_t>(pl.smem);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GB_CUDA_OK(cudaLaunchKernelExC(&cfg, pl.func, args));
     return FP8_OK;
 }
 
@@ -1014,9 +1119,210 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
     return sparse ? plan<MAXP, 2, true>(prm, max_ctas, pl) : plan<MAXP, 2, false>(prm, max_ctas, pl);
 }
 
-// Plan and launch.  A split-K launch takes its workspace from the stream-
-// ordered allocator (cudaMallocAsync / cudaFreeAsync on `st`) and zeroes the
-// counters first; the partials need no clearing.
+// Split-K workspaces of eager (not captured) launches, one per device and
+// stream.  Launches on one stream run in order, so they can share a buffer:
+// the last unit of every split tile re-zeroes its counter, hence the counters
+// are zero between launches and only a new buffer is cleared.  A launch that
+// needs more grows the buffer (the new one allocated and cleared, the old one
+// freed, all ordered on the stream).  Entries are keyed by the stream's id,
+// which unlike its handle is never given to a later stream, and live as long
+// as the process; past kMaxStreamWorkspaces streams, launches on further
+// streams allocate per call.  The entry's mutex is held from binding to the
+// end of the launch call, so threads sharing a stream never free a buffer
+// that a launch was just bound to.
+struct StreamWorkspace {
+    std::mutex mu;
+    void* buf = nullptr;
+    size_t ctr_cap = 0;         // counters in the counter region
+    size_t floats_cap = 0;      // partial sums after it
+};
+constexpr size_t kMaxStreamWorkspaces = 64;
+std::mutex g_sws_mu;
+std::map<std::pair<int, unsigned long long>, std::unique_ptr<StreamWorkspace>> g_sws;
+
+StreamWorkspace* stream_workspace(int dev, cudaStream_t st)
+{
+    unsigned long long id = 0;
+    if (cudaStreamGetId(st, &id) != cudaSuccess)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(g_sws_mu);
+    const auto key = std::make_pair(dev, id);
+    auto it = g_sws.find(key);
+    if (it != g_sws.end())
+        return it->second.get();
+    if (g_sws.size() >= kMaxStreamWorkspaces)
+        return nullptr;
+    return g_sws.emplace(key, std::make_unique<StreamWorkspace>()).first->second.get();
+}
+
+// Split-K workspaces of captured launches.  Each captured split launch gets
+// a buffer of its own, allocated and cleared outside the capture (on a
+// private non-blocking stream, with this thread in relaxed capture mode) and
+// tied to the captured graph by a CUDA user object: replays then run with no
+// allocation nodes, and the buffer lives until the graph and every
+// executable graph made from it are gone.  CUDA orders the replays of one
+// executable graph; two executables instantiated from the same graph and
+// replayed at the same time would share the buffer.  A user object's
+// destructor may not call CUDA, so it only queues the buffer; the next
+// split launch on that device frees it.
+struct CapturedWorkspace {
+    int dev;
+    void* buf;
+    size_t ctr_bytes;
+};
+std::mutex g_cap_mu;
+std::set<CapturedWorkspace*> g_cap_live;          // counters re-zeroed after a device error
+std::vector<CapturedWorkspace*> g_cap_dead;       // released by their graphs, not yet freed
+
+void CUDART_CB release_captured_workspace(void* p)
+{
+    auto* w = static_cast<CapturedWorkspace*>(p);
+    std::lock_guard<std::mutex> lk(g_cap_mu);
+    g_cap_live.erase(w);
+    g_cap_dead.push_back(w);
+}
+
+cudaStream_t side_stream(int dev)
+{
+    static std::once_flag once[64];
+    static cudaStream_t streams[64];
+    if (dev < 0 || dev >= 64)
+        return nullptr;
+    std::call_once(once[dev], [dev] {
+        if (cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+            streams[dev] = nullptr;
+    });
+    return streams[dev];
+}
+
+// Runs fn with this thread in relaxed capture mode (allocation calls are
+// then allowed while a stream of this or another thread is being captured).
+template <typename F>
+int relaxed_capture_mode(F fn)
+{
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    GB_CUDA_OK(cudaThreadExchangeStreamCaptureMode(&mode));
+    const int rc = fn();
+    cudaThreadExchangeStreamCaptureMode(&mode);
+    return rc;
+}
+
+void free_released_workspaces(int dev)
+{
+    std::vector<CapturedWorkspace*> mine;
+    {
+        std::lock_guard<std::mutex> lk(g_cap_mu);
+        if (g_cap_dead.empty())
+            return;
+        auto keep = std::partition(g_cap_dead.begin(), g_cap_dead.end(),
+                                   [dev](CapturedWorkspace* w) { return w->dev != dev; });
+        mine.assign(keep, g_cap_dead.end());
+        g_cap_dead.erase(keep, g_cap_dead.end());
+    }
+    cudaStream_t side = side_stream(dev);
+    relaxed_capture_mode([&] {
+        for (CapturedWorkspace* w : mine) {
+            if (side)
+                cudaFreeAsync(w->buf, side);
+            delete w;
+        }
+        return FP8_OK;
+    });
+}
+
+int captured_workspace(int dev, cudaGraph_t graph, const Plan& pl, void** out)
+{
+    cudaStream_t side = side_stream(dev);
+    if (!side)
+        return FP8_ERR_CUDA;
+    const size_t ctr_bytes = ctr_region_bytes(pl.ctr_count);
+    return relaxed_capture_mode([&] {
+        void* buf = nullptr;
+        if (cudaMallocAsync(&buf, workspace_bytes(pl), side) != cudaSuccess)
+            return FP8_ERR_OOM;
+        if (cudaMemsetAsync(buf, 0, ctr_bytes, side) != cudaSuccess ||
+            cudaStreamSynchronize(side) != cudaSuccess) {
+            cudaFreeAsync(buf, side);
+            return FP8_ERR_CUDA;
+        }
+        auto* w = new CapturedWorkspace{dev, buf, ctr_bytes};
+        cudaUserObject_t obj = nullptr;
+        if (cudaUserObjectCreate(&obj, w, release_captured_workspace, 1,
+                                 cudaUserObjectNoDestructorSync) != cudaSuccess) {
+            cudaFreeAsync(buf, side);
+            delete w;
+            return FP8_ERR_CUDA;
+        }
+        {
+            std::lock_guard<std::mutex> lk(g_cap_mu);
+            g_cap_live.insert(w);
+        }
+        if (cudaGraphRetainUserObject(graph, obj, 1, cudaGraphUserObjectMove) != cudaSuccess) {
+            cudaUserObjectRelease(obj, 1);            // the destructor queues the buffer
+            return FP8_ERR_CUDA;
+        }
+        *out = buf;
+        return FP8_OK;
+    });
+}
+
+// Launch a split-K plan: on the graph's own workspace under capture, else on
+// the stream's persistent one, else (past the stream limit) on a workspace
+// from the stream-ordered allocator for this call only (cudaMallocAsync,
+// counters cleared, cudaFreeAsync after the kernel, all on `st`).
+template <int MAXP>
+int launch_split(Params<MAXP>& prm, const Plan& pl, cudaStream_t st)
+{
+    int dev = 0;
+    GB_CUDA_OK(cudaGetDevice(&dev));
+    free_released_workspaces(dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    GB_CUDA_OK(cudaStreamGetCaptureInfo(st, &cap, nullptr, &graph));
+    if (cap == cudaStreamCaptureStatusActive) {
+        void* buf = nullptr;
+        const int rc = captured_workspace(dev, graph, pl, &buf);
+        if (rc != FP8_OK)
+            return rc;
+        bind_workspace(prm, pl, buf);
+        return launch_plan(prm, pl, st);
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return FP8_ERR_CUDA;                      // a capture that was invalidated
+    if (StreamWorkspace* w = stream_workspace(dev, st)) {
+        std::lock_guard<std::mutex> lk(w->mu);
+        if (pl.ctr_count > w->ctr_cap || pl.ws_floats > w->floats_cap) {
+            const size_t ctr_cap = std::max(pl.ctr_count, w->ctr_cap);
+            const size_t floats_cap = std::max(pl.ws_floats, w->floats_cap);
+            void* nb = nullptr;
+            if (cudaMallocAsync(&nb, ctr_region_bytes(ctr_cap) + floats_cap * sizeof(float), st) !=
+                cudaSuccess)
+                return FP8_ERR_OOM;
+            if (cudaMemsetAsync(nb, 0, ctr_region_bytes(ctr_cap), st) != cudaSuccess ||
+                (w->buf && cudaFreeAsync(w->buf, st) != cudaSuccess)) {
+                cudaFreeAsync(nb, st);
+                return FP8_ERR_CUDA;
+            }
+            w->buf = nb;
+            w->ctr_cap = ctr_cap;
+            w->floats_cap = floats_cap;
+        }
+        bind_workspace(prm, w->buf, w->ctr_cap);
+        return launch_plan(prm, pl, st);
+    }
+    void* buf = nullptr;
+    if (cudaMallocAsync(&buf, workspace_bytes(pl), st) != cudaSuccess)
+        return FP8_ERR_OOM;
+    bind_workspace(prm, pl, buf);
+    int rc = cudaMemsetAsync(prm.ctr, 0, pl.ctr_count * sizeof(unsigned), st) == cudaSuccess
+                 ? launch_plan(prm, pl, st)
+                 : FP8_ERR_CUDA;
+    if (cudaFreeAsync(buf, st) != cudaSuccess && rc == FP8_OK)
+        rc = FP8_ERR_CUDA;
+    return rc;
+}
+
+// Plan and launch (split-K plans through launch_split).
 template <int MAXP>
 int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_ctas,
              cudaStream_t st, const TileChoice* expl = nullptr)
@@ -1025,21 +1331,11 @@ int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_
     int rc = build_plan(prm, jobs, bns, n, max_ctas, expl, &pl);
     if (rc != FP8_OK)
         return rc;
-    const size_t bytes = workspace_bytes(pl);
-    if (bytes == 0) {
+    if (workspace_bytes(pl) == 0) {
         bind_workspace(prm, pl, nullptr);
         return launch_plan(prm, pl, st);
     }
-    void* buf = nullptr;
-    if (cudaMallocAsync(&buf, bytes, st) != cudaSuccess)
-        return FP8_ERR_OOM;
-    bind_workspace(prm, pl, buf);
-    rc = cudaMemsetAsync(prm.ctr, 0, pl.ctr_count * sizeof(unsigned), st) == cudaSuccess
-             ? launch_plan(prm, pl, st)
-             : FP8_ERR_CUDA;
-    if (cudaFreeAsync(buf, st) != cudaSuccess && rc == FP8_OK)
-        rc = FP8_ERR_CUDA;
-    return rc;
+    return launch_split(prm, pl, st);
 }
 
 // Map a user-level GEMM (A [M,K], B [N,K], C [M,N] or C^T) onto (P, Q)
@@ -1090,7 +1386,7 @@ extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A,
         return write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
                      ldc, out_dtype, 0);
-    const int bn = pick_bn(j.rows_p, j.rows_q, BN_MAX);
+    const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     return run_jobs(prm, &j, &bn, 1, 0, st);
@@ -1144,7 +1440,7 @@ extern "C" int gemm_fp8_dense_noalloc(int64_t M, int64_t N, int64_t K, const uin
         return write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
                      ldc, out_dtype, 0);
-    const int bn = pick_bn(j.rows_p, j.rows_q, BN_MAX);
+    const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     Plan pl;
@@ -1185,7 +1481,7 @@ extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t*
                               : write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, a_vals, K / 2, a_meta, B, ldb, a_scale, a_mode, b_scale, b_mode,
                      alpha, C, ldc, out_dtype, out_transposed);
-    const int bn = pick_bn(j.rows_p, j.rows_q, SPARSE_BN_MAX);
+    const int bn = pick_bn(j.rows_p, j.rows_q, j.K, SPARSE_BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     return run_jobs(prm, &j, &bn, 1, 0, st);
@@ -1246,7 +1542,7 @@ int grouped_jobs(const fp8_gemm_problem* problems, int num_problems, cudaStream_
         jobs[n] = make_job(g.M, g.N, g.K, g.A, sp ? g.K / 2 : g.lda, g.A_meta, g.B, g.ldb,
                            g.a_scale, g.a_mode, g.b_scale, g.b_mode, g.alpha, g.C, g.ldc,
                            g.out_dtype, g.out_transposed);
-        bns[n] = pick_bn(jobs[n].rows_p, jobs[n].rows_q, bn_max);
+        bns[n] = pick_bn(jobs[n].rows_p, jobs[n].rows_q, jobs[n].K, bn_max);
         ++n;
     }
     *n_out = n;
@@ -1425,6 +1721,7 @@ struct fp8_grouped_graph {
     gb300::Plan plan;
     std::vector<int64_t> sig;
     int max_ctas = 0;
+    int dev = 0;
     void* ws = nullptr;         // split-K workspace owned by the graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1432,6 +1729,11 @@ struct fp8_grouped_graph {
 };
 
 namespace {
+
+// Graphs that own a split-K workspace (their counters are re-zeroed after a
+// device error).
+std::mutex g_graphs_mu;
+std::set<fp8_grouped_graph*> g_graphs;
 
 int graph_params(fp8_grouped_graph* g, const fp8_gemm_problem* problems, int num_problems,
                  std::vector<int64_t>* sig)
@@ -1474,6 +1776,10 @@ extern "C" int gemm_fp8_grouped_graph_create(const fp8_gemm_problem* problems, i
         return FP8_ERR_INVALID;
     auto* g = new fp8_grouped_graph;
     g->max_ctas = max_ctas;
+    if (cudaGetDevice(&g->dev) != cudaSuccess) {
+        delete g;
+        return FP8_ERR_CUDA;
+    }
     int rc = graph_params(g, problems, num_problems, &g->sig);
     const size_t bytes = rc == FP8_OK ? gb300::workspace_bytes(g->plan) : 0;
     if (bytes) {
@@ -1502,6 +1808,10 @@ extern "C" int gemm_fp8_grouped_graph_create(const fp8_gemm_problem* problems, i
             cudaFree(g->ws);
         delete g;
         return rc;
+    }
+    if (g->ws) {
+        std::lock_guard<std::mutex> lk(g_graphs_mu);
+        g_graphs.insert(g);
     }
     *out = g;
     return FP8_OK;
@@ -1538,12 +1848,47 @@ extern "C" int gemm_fp8_grouped_graph_destroy(fp8_grouped_graph* g)
 {
     if (!g)
         return FP8_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(g_graphs_mu);
+        g_graphs.erase(g);
+    }
     cudaGraphExecDestroy(g->exec);
     cudaGraphDestroy(g->graph);
     if (g->ws)
         cudaFree(g->ws);
     delete g;
     return FP8_OK;
+}
+
+void gb300::reset_split_counters()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return;
+    cudaDeviceSynchronize();
+    {
+        std::lock_guard<std::mutex> lk(g_sws_mu);
+        for (auto& kv : g_sws) {
+            if (kv.first.first != dev)
+                continue;
+            std::lock_guard<std::mutex> lk2(kv.second->mu);
+            if (kv.second->buf)
+                cudaMemset(kv.second->buf, 0, ctr_region_bytes(kv.second->ctr_cap));
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_graphs_mu);
+        for (fp8_grouped_graph* g : g_graphs)
+            if (g->dev == dev && g->ws)
+                cudaMemset(g->ws, 0, ctr_region_bytes(g->plan.ctr_count));
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_cap_mu);
+        for (CapturedWorkspace* w : g_cap_live)
+            if (w->dev == dev)
+                cudaMemset(w->buf, 0, w->ctr_bytes);
+    }
+    cudaDeviceSynchronize();
 }
 
 extern "C" int fp8_gemm_set_tile_config(int mt, int group_m)

@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(kThreads) prune24_vec_kernel(const uint8_t* __
                                                                uint8_t* __restrict__ vals,
                                                                uint8_t* __restrict__ meta)
 {
+    grid_launch_dependents();
     const int pieces = static_cast<int>(K / 16);
     const int64_t ldv = K / 2, ldm = K / 8;
     const int p_first = blockIdx.x * (kThreads * kPieces) + threadIdx.x;
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kThreads) prune24_kernel(const uint8_t* __rest
                                                            uint8_t* __restrict__ vals,
                                                            uint8_t* __restrict__ meta)
 {
+    grid_launch_dependents();
     const int64_t ldv = K / 2, ldm = (K + 7) / 8;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
     const int64_t tid = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(kThreads) decompress24_kernel(const uint8_t* _
                                                                 int64_t M, int64_t K,
                                                                 uint8_t* __restrict__ out)
 {
+    grid_launch_dependents();
     const int64_t ldv = K / 2, ldm = (K + 7) / 8, groups = K / 4;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < M * groups;

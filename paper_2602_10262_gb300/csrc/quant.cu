@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(kThreads) quant_row_kernel(const float* __rest
                                                              int64_t ldq, float* __restrict__ d,
                                                              int vec, int* err)
 {
+    grid_launch_dependents();
     __shared__ uint32_t red[kThreads / 32];
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
         quantize_row(x + r * ldx, cols, q + r * ldq, d + r, vec, err, red);
@@ -131,6 +132,7 @@ struct RowJobs {
 __global__ void __launch_bounds__(kThreads) quant_rows_grouped_kernel(const __grid_constant__ RowJobs jobs,
                                                                       int* err)
 {
+    grid_launch_dependents();
     __shared__ uint32_t red[kThreads / 32];
     const int64_t total = jobs.row_start[jobs.n];
     for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(kThreads) quant_encode_kernel(const float* __r
 
 __global__ void quant_finalize_kernel(uint32_t* slot, int* err)
 {
+    grid_launch_dependents();
     const uint32_t m = *slot;
     if (m >= kInfBits)
         report_device_error(err, FP8_ERR_NONFINITE);

@@ -192,7 +192,7 @@ def test_tile_configs_bitwise_equal_and_correct(gb, orc, tile_cfg, M, N, K, gm):
 @pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (1, 8192, 2048), (1024, 1024, 1024),
                                    (100, 300, 2000)])
 def test_split_k_repeatable_and_correct(gb, orc, M, N, K):
-    """Few 128-row tiles: K is split across CTAs (partials in a stream-ordered
+    """Few 128-row tiles: K is split across CTAs (partials in the stream's
     workspace, the last unit of each tile adds them in slice order).  Calls
     repeat bit for bit (the tile counters reset themselves) and match the
     oracle."""
@@ -203,6 +203,58 @@ def test_split_k_repeatable_and_correct(gb, orc, M, N, K):
     ref = orc.gemm(A, B, dA, 1, dB, 1)
     S = orc.gemm(parity.abs_codes(A), parity.abs_codes(B), dA, 1, dB, 1)
     parity.check_bf16(C1, ref, S, K)
+
+
+def test_split_k_workspace_reuse_streams_and_capture(gb, orc):
+    """Split launches share their stream's persistent workspace.  A sequence
+    that grows and shrinks it, the same calls on a second stream, and a
+    captured graph (which owns a workspace of its own, freed after the graph
+    is destroyed) all give the bitwise-same results as the first calls."""
+    shapes = [(8, 4096, 2048), (16, 8192, 8192), (8, 4096, 2048), (1, 2048, 4096)]
+    data = []
+    for i, (M, N, K) in enumerate(shapes):
+        A = _codes(workloads.random_codes((M, K), seed=300 + i))
+        B = _codes(workloads.random_codes((N, K), seed=400 + i))
+        data.append((A, B, _ones(M), _ones(N)))
+
+    def run(outs=None, stream=None):
+        outs = outs or [None] * len(data)
+        return [gb.gemm_fp8_dense(A, B, sa, 1, sb, 1, 1.0, gb.OUT_F32, C=o, stream=stream)
+                for (A, B, sa, sb), o in zip(data, outs)]
+
+    first = run()
+    torch.cuda.synchronize()
+    for f in first:
+        assert not torch.isnan(f).any()
+    for o, f in zip(run(), first):
+        assert torch.equal(o, f)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        on_side = run(stream=side)
+    side.synchronize()
+    for o, f in zip(on_side, first):
+        assert torch.equal(o, f)
+    outs = [torch.empty_like(f) for f in first]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run(outs)
+    for _ in range(2):
+        for o in outs:
+            o.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for o, f in zip(outs, first):
+            assert torch.equal(o, f)
+    del g                                  # releases the graph's workspace
+    torch.cuda.synchronize()
+    for o, f in zip(run(), first):         # the next split launch frees it
+        assert torch.equal(o, f)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    A, B = data[0][0].cpu().numpy(), data[0][1].cpu().numpy()
+    one = np.ones(1, np.float32)
+    parity.check_fp32(first[0].cpu().numpy(), orc.gemm(A, B, one, 0, one, 0))
 
 
 def test_split_k_integers_exact(gb, orc):
