@@ -260,8 +260,8 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * mt: 128-row MMA halves per CTA tile: 1 (128 x N tiles, double-buffered
  * accumulators), 2 (256 x N tiles: two MMAs share each B tile, a third fewer
  * operand bytes per FLOP), 0 = chosen per launch (2 when every problem fills
- * 256-row tiles with N tiles >= 128 wide and there are at least as many tiles
- * as SMs; a launch mixing dense and sparse problems always uses 1).
+ * 256-row tiles with N tiles >= 128 wide and those tiles number at least
+ * half the SMs; a launch mixing dense and sparse problems always uses 1).
  * group_m: M-blocks per raster band (0 = 16).  Results do not depend on
  * either.  Affects launches enqueued after the call, from any thread. */
 int fp8_gemm_set_tile_config(int mt, int group_m);

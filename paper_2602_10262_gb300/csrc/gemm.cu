@@ -272,21 +272,21 @@ __device__ __forceinline__ void store_chunk16(const ProblemScalars& P, int i, bo
 }
 
 // Split-K, part 1: this unit's partial sums (row `row` of the tile, straight
-// from TMEM) go to its slot of the workspace.
+// from TMEM) go to its slot of the workspace.  A slot holds the tile column
+// by column (element (row, col) at col * rows_per_tile + row), so the 32
+// lanes of a warp, which own 32 consecutive rows, store 128 contiguous bytes
+// per column.
 __device__ __forceinline__ void split_write_partial(const ProblemScalars& P, float* ws, int rows_per_tile,
                                                     int tile, int slice, int row, uint32_t taddr)
 {
-    float* dst = ws + P.ws_off + (static_cast<long long>(tile) * P.splits + slice) * rows_per_tile * P.bn +
-                 static_cast<long long>(row) * P.bn;
+    float* dst = ws + P.ws_off + (static_cast<long long>(tile) * P.splits + slice) * rows_per_tile * P.bn + row;
     for (int c0 = 0; c0 < P.bn; c0 += 16) {
         uint32_t r[16];
         tmem_ld_32x32b_x16(taddr + c0, r);
         tmem_ld_wait();
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-            __stcg(reinterpret_cast<float4*>(dst + c0) + t,
-                   make_float4(__uint_as_float(r[4 * t]), __uint_as_float(r[4 * t + 1]),
-                               __uint_as_float(r[4 * t + 2]), __uint_as_float(r[4 * t + 3])));
+        for (int t = 0; t < 16; ++t)
+            __stcg(dst + static_cast<long long>(c0 + t) * rows_per_tile, __uint_as_float(r[t]));
     }
 }
 
@@ -296,8 +296,7 @@ __device__ __forceinline__ void split_reduce_store(const ProblemScalars& P, cons
                                                    int tile, int row, int i, bool row_ok, float fi, int jbase,
                                                    ScaleWindows& sw, int lane)
 {
-    const float* src = ws + P.ws_off + static_cast<long long>(tile) * P.splits * rows_per_tile * P.bn +
-                       static_cast<long long>(row) * P.bn;
+    const float* src = ws + P.ws_off + static_cast<long long>(tile) * P.splits * rows_per_tile * P.bn + row;
     const long long slot = static_cast<long long>(rows_per_tile) * P.bn;
     float s_cur = 0.0f;
     for (int c0 = 0; c0 < P.bn; c0 += 16) {
@@ -308,14 +307,10 @@ __device__ __forceinline__ void split_reduce_store(const ProblemScalars& P, cons
         for (int t = 0; t < 16; ++t)
             acc[t] = 0.0f;
         for (int sl = 0; sl < P.splits; ++sl) {
+            const float* col = src + sl * slot + static_cast<long long>(c0) * rows_per_tile;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float4 v = __ldcg(reinterpret_cast<const float4*>(src + sl * slot + c0) + t);
-                acc[4 * t] = __fadd_rn(acc[4 * t], v.x);
-                acc[4 * t + 1] = __fadd_rn(acc[4 * t + 1], v.y);
-                acc[4 * t + 2] = __fadd_rn(acc[4 * t + 2], v.z);
-                acc[4 * t + 3] = __fadd_rn(acc[4 * t + 3], v.w);
-            }
+            for (int t = 0; t < 16; ++t)
+                acc[t] = __fadd_rn(acc[t], __ldcg(col + static_cast<long long>(t) * rows_per_tile));
         }
         store_vals16(P, i, row_ok, fi, jbase + c0, acc, s_cur, c0 & 31);
     }
@@ -753,11 +748,12 @@ bool splits_k(int64_t rows_p, int64_t rows_q, int64_t K)
 
 // N of the MMA tile for a problem of rows_p x rows_q: the smallest of
 // {16, 32, 64, 128, 256} covering rows_q, then halved (down to 64) while the
-// problem has fewer 128-row tiles than SMs, so small problems still occupy
-// the GPU.  A problem that splits along K keeps the full width instead: a
-// narrower tile would read the large P operand once per column block, split
-// partial sums cost far less.  Depends on the problem only (not on what it
-// is launched with).
+// problem has fewer 128-row tiles than half the SMs, so small problems still
+// occupy the GPU.  (Halving further, to a full wave, costs more than it
+// gains: every extra column block reads the P operand again, and the tiles
+// run at a lower ratio of MMA work to loaded bytes.)  A problem that splits
+// along K keeps the full width.  Depends on the problem only (not on what
+// it is launched with).
 int pick_bn(int64_t rows_p, int64_t rows_q, int64_t K, int bn_max)
 {
     int bn = 256;
@@ -767,7 +763,7 @@ int pick_bn(int64_t rows_p, int64_t rows_q, int64_t K, int bn_max)
     else if (rows_q <= 128) bn = 128;
     const int64_t m_blocks = (rows_p + BM - 1) / BM;
     if (!splits_k(rows_p, rows_q, K))
-        while (bn > 64 && m_blocks * ((rows_q + bn - 1) / bn) < sm_count())
+        while (bn > 64 && 2 * m_blocks * ((rows_q + bn - 1) / bn) < sm_count())
             bn /= 2;
     return bn < bn_max ? bn : bn_max;
 }
@@ -1075,7 +1071,9 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
                     ok2 = false;
                 tiles2 += ((jobs[i].rows_p + 2 * BM - 1) / (2 * BM)) * ((jobs[i].rows_q + bns[i] - 1) / bns[i]);
             }
-            c.mt = ok2 && tiles2 >= sm_count() ? 2 : 1;
+            // 256-row tiles load a third fewer bytes per MMA; take them
+            // while they still give at least half the SMs a tile
+            c.mt = ok2 && 2 * tiles2 >= sm_count() ? 2 : 1;
         }
     }
     if (mixed_kinds(jobs, n))
