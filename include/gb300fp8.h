@@ -143,7 +143,7 @@ int prune24_decompress(const uint8_t *a_vals, const uint8_t *a_meta, int64_t M, 
  * C: device [M, N], row stride ldc elements, out_dtype 0 = fp32,
  * 1 = bf16 (round to nearest even).
  * Skinny products whose N-side tiles are too few to occupy the GPU (and
- * whose K is at least 2048) are split along K over several CTAs; their FP32
+ * whose K is at least 4096) are split along K over several CTAs; their FP32
  * partial sums go through a workspace and are added in a fixed order, so
  * results are deterministic and do not depend on how the problem is
  * launched.  The workspace is a buffer kept per stream (allocated with
@@ -184,8 +184,8 @@ int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t ld
  *     floats, with tiles x slices at most the SM count (only products with
  *     M <= 64 split): skinny products with M <= 32 always fit; those with
  *     33 <= M <= 64 fit while that total stays within 4 MiB (M = 64 with a
- *     long side of 8192 rows split in two needs 4 MiB + 256 bytes and is
- *     rejected).  Problems that do not split need none and always run;
+ *     long side of 4864 rows and K = 8192, split in four, needs 4.98 MB and
+ *     is rejected).  Problems that do not split need none and always run;
  *   - all calls on a device share the array, which keeps the previous call's
  *     contents; each call zeroes the counters it needs (cudaMemsetAsync, not
  *     an allocation).  Calls whose kernels overlap on the GPU (for example on

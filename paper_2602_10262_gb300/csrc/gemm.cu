@@ -42,7 +42,6 @@ namespace {
 constexpr int BM = 128;                   // rows of one MMA (M = 128, cta_group::1)
 constexpr int BK = 128;                   // codes per k-block (one 128-byte swizzle row)
 constexpr int BN_MAX = 256;
-constexpr int B_BYTES = BN_MAX * BK;      // 32 KB: B tile of a stage
 constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M_DEFAULT = 16;       // raster: M-blocks per band
 // 2:4-sparse tiles: per stage the kept A codes (rows x 64 bytes, 64-byte
@@ -67,13 +66,28 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 //          launches (SP = false): 3 stages of 64 KB.  Sparse launches
 //          (SP = true): 4 stages of 48 KB (20 KB kept codes + metadata, 28 KB
 //          B with bn <= 224), metadata rings at cols 224..239 of each half.
-template <int MT, bool SP = false, int BNC = BN_MAX>
+// KC = k-blocks (128-wide K chunks) per stage.  A CTA's TMA loads complete
+// at about one stage barrier per ~0.36 us whatever the bytes behind it, so
+// a stage must carry enough bytes for the tile's MMA rate (or, for skinny
+// products, for its share of HBM bandwidth).  Dense launches of 128-row
+// tiles with bn <= 128 use KC = 2: stage = KC x (A chunk + B chunk), chunk c
+// of each operand at its own 1024-aligned offset (A chunks 16 KB apart, B
+// chunks bn x 128 bytes apart); BNC = 128 / 64 / 32 / 16 then run 3 / 4 / 5
+// / 5 stages of 64 / 48 / 40 / 36 KB.  When K % 128 == 0 one 3-D TMA box per
+// operand (x: byte in a 128-byte chunk, y: row, z: chunk) brings all KC
+// chunks of a stage, else one 2-D box per chunk.  Launches with sparse
+// problems, BNC = 256 and MT = 2 keep KC = 1.
+template <int MT, bool SP = false, int BNC = BN_MAX, int KC = 1>
 struct Cfg {
     static constexpr bool kSparse2 = MT == 2 && SP;
     static constexpr int kStages =
-        MT == 2 ? (SP ? 4 : 3) : (BNC == 256 ? 4 : (BNC == 128 ? 6 : (BNC == 64 ? 8 : (BNC == 32 ? 9 : 11))));
-    static constexpr int kABytes = MT == 1 ? BM * BK : (SP ? 2 * BM * (BK / 2 + BK / 8) : 2 * BM * BK);
-    static constexpr int kBBytes = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : BNC * BK;
+        KC == 2 ? (BNC == 128 ? 3 : (BNC == 64 ? 4 : 5))
+                : MT == 2 ? (SP ? 4 : 3)
+                          : (BNC == 256 ? 4 : (BNC == 128 ? 6 : (BNC == 64 ? 8 : (BNC == 32 ? 9 : 11))));
+    static constexpr int kAChunk = MT == 1 ? BM * BK : (SP ? 2 * BM * (BK / 2 + BK / 8) : 2 * BM * BK);
+    static constexpr int kBChunk = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : BNC * BK;
+    static constexpr int kABytes = KC * kAChunk;
+    static constexpr int kBBytes = KC * kBChunk;
     static constexpr int kStageBytes = kABytes + kBBytes;
     static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : (BNC == 256 ? SPARSE_BN_MAX : BNC);
     static constexpr int kAcc = MT == 2 ? 1 : 2;                  // accumulator buffers
@@ -89,6 +103,8 @@ struct Cfg {
     static_assert(kSmem <= 232448, "shared memory per CTA");
     static_assert((2 * kStages + 2 * kAcc + 3) * 8 + 12 <= 256, "barriers and flags fit their 256-byte region");
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
+    static_assert(KC == 1 || (KC == 2 && MT == 1 && !SP && BNC <= 128), "two-chunk stages: dense 128-row tiles");
+    static_assert(kBChunk % 1024 == 0, "B chunks stay swizzle-atom aligned");
 };
 
 // Everything of a problem but its tensor maps.  Each role thread copies this
@@ -107,6 +123,7 @@ struct ProblemScalars {
     int vec_store;          // 16-byte stores allowed in the non-transposed path
     int bn;
     int sparse;             // P holds kept codes [rows_p, K/2] + metadata in tmE
+    int tma3d;              // tmP / tmQ are 3-D chunk views (one box per operand per stage)
     int m_blocks, n_blocks, k_blocks;
     int splits;             // k-slices per tile (split-K); 1 = none
     int kb_per_split;       // k-blocks per slice
@@ -391,11 +408,11 @@ __device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P,
 
 // ---------------------------------------------------------------- kernel
 
-template <int MAXP, int MT, bool SP, int BNC>
-__global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
+template <int MAXP, int MT, bool SP, int BNC, int KC>
+__global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
     gemm_fp8_kernel(const __grid_constant__ Params<MAXP> prm)
 {
-    using C = Cfg<MT, SP, BNC>;
+    using C = Cfg<MT, SP, BNC, KC>;
     constexpr int S = C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -478,29 +495,45 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                 const CUtensorMap* map_p = &prm.prob[tc.p].tmP;
                 const CUtensorMap* map_q = &prm.prob[tc.p].tmQ;
                 const CUtensorMap* map_e = &prm.prob[tc.p].tmE;
-                const uint32_t a_bytes = P.sparse ? C::kSpABytes + MT * BM * BK / 8 : C::kABytes;
-                const uint32_t bytes = a_bytes + static_cast<uint32_t>(P.bn) * BK;
+                const bool sparse = KC == 1 && P.sparse != 0;
+                const uint32_t a_bytes = sparse ? C::kSpABytes + MT * BM * BK / 8 : C::kAChunk;
+                const uint32_t b_chunk = static_cast<uint32_t>(P.bn) * BK;      // B chunks bn x 128 B apart
+                const uint32_t chunk_bytes = a_bytes + b_chunk;
                 const int row0 = tc.m_blk * BM * MT;
                 const int col0 = tc.n_blk * P.bn;
-                const bool sparse = P.sparse != 0;
                 const int kb0 = tc.slice * P.kb_per_split;
                 const int kb1 = min(P.k_blocks, kb0 + P.kb_per_split);
-                for (int kb = kb0; kb < kb1; ++kb) {
+                for (int kb = kb0; kb < kb1; kb += KC) {
+                    const int nck = min(KC, kb1 - kb);          // k-blocks in this stage
                     // a slot never armed is free: no wait on its first use
                     if (((armed >> stage) & 1u) && !mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
                         ok = false;
                         abort_pipeline(abort_flag, prm.err);
                         break;
                     }
-                    mbar_arrive_expect_tx(full_bar(stage), bytes);
+                    // a 3-D box always lands all KC chunks (those past K as zeros)
+                    mbar_arrive_expect_tx(full_bar(stage),
+                                          chunk_bytes * static_cast<uint32_t>(KC > 1 && P.tma3d ? KC : nck));
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
                     if (sparse) {
                         tma_load_2d(sa, map_p, full_bar(stage), kb * (BK / 2), row0);
                         tma_load_2d(sa + C::kSpABytes, map_e, full_bar(stage), kb * (BK / 8), row0);
+                    } else if (KC > 1 && P.tma3d) {
+                        tma_load_3d(sa, map_p, full_bar(stage), 0, row0, kb);
+                        tma_load_3d(sa + C::kABytes, map_q, full_bar(stage), 0, col0, kb);
                     } else {
-                        tma_load_2d(sa, map_p, full_bar(stage), kb * BK, row0);
+#pragma unroll
+                        for (int c = 0; c < KC; ++c)
+                            if (c < nck)
+                                tma_load_2d(sa + c * C::kAChunk, map_p, full_bar(stage), (kb + c) * BK, row0);
                     }
-                    tma_load_2d(sa + C::kABytes, map_q, full_bar(stage), kb * BK, col0);
+                    if (!(KC > 1 && P.tma3d)) {
+#pragma unroll
+                        for (int c = 0; c < KC; ++c)
+                            if (c < nck)
+                                tma_load_2d(sa + C::kABytes + c * b_chunk, map_q, full_bar(stage), (kb + c) * BK,
+                                            col0);
+                    }
                     armed |= 1u << stage;
                     if (++stage == S) {
                         stage = 0;
@@ -531,8 +564,9 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
             for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x, ++local) {
                 const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
                 const ProblemScalars P = prm.prob[tc.p];
-                const bool sparse = P.sparse != 0;
+                const bool sparse = KC == 1 && P.sparse != 0;
                 const uint32_t idesc = P.idesc;
+                const uint32_t b_chunk = static_cast<uint32_t>(P.bn) * BK;      // B chunks bn x 128 B apart
                 const int acc = local % C::kAcc;
                 const uint32_t acc_phase = (local / C::kAcc) & 1;
                 // an accumulator not used yet is free: no wait on its first use
@@ -545,7 +579,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                 const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN_MAX);
                 const int kb0 = tc.slice * P.kb_per_split;
                 const int kb1 = min(P.k_blocks, kb0 + P.kb_per_split);
-                for (int kb = kb0; kb < kb1; ++kb) {
+                for (int kb = kb0; kb < kb1; kb += KC) {
+                    const int nck = min(KC, kb1 - kb);          // k-blocks in this stage
                     const uint32_t first = kb == kb0 ? 0u : 1u;     // 0: overwrite the accumulator
                     if (!mbar_wait(full_bar(stage), phase, abort_flag)) {
                         ok = false;
@@ -580,13 +615,19 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC>::kThreads, 1)
                         }
                     } else {
 #pragma unroll
-                        for (int k = 0; k < BK / 32; ++k) {
+                        for (int c = 0; c < KC; ++c) {
+                            if (c >= nck)
+                                break;
+                            const uint64_t bdesc_c = sdesc_kmajor_sw128(sa + C::kABytes + c * b_chunk);
 #pragma unroll
-                            for (int h = 0; h < MT; ++h) {
-                                // advance the start address by 32 bytes (K = 32 codes)
-                                const uint64_t adesc = sdesc_kmajor_sw128(sa + h * BM * BK);
-                                mma_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 2u * k,
-                                           idesc, (first | k) != 0 ? 1u : 0u);
+                            for (int k = 0; k < BK / 32; ++k) {
+#pragma unroll
+                                for (int h = 0; h < MT; ++h) {
+                                    // advance the start address by 32 bytes (K = 32 codes)
+                                    const uint64_t adesc = sdesc_kmajor_sw128(sa + c * C::kAChunk + h * BM * BK);
+                                    mma_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc_c + 2u * k, idesc,
+                                               (first | c | k) != 0 ? 1u : 0u);
+                                }
                             }
                         }
                     }
@@ -736,14 +777,39 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, in
     return r == CUDA_SUCCESS;
 }
 
-// True when a problem is split along K (see split_count): its Q side fits
-// one tile of at most 64 columns, its K spans at least 16 k-blocks and its
-// tiles fill at most half the SMs.  (With 128 columns the split epilogue
-// costs more than narrowing the tile and reading P twice.)
+// 3-D view of a byte matrix [rows, cols] (cols % 128 == 0, row stride ld
+// bytes) as x = byte within a 128-byte K chunk, y = row, z = chunk; box
+// {128, box_rows, chunks}: one copy lands `chunks` swizzled K-major tiles of
+// box_rows x 128 bytes back to back in shared memory.
+bool make_map3(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+               int chunks)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return false;
+    cuuint64_t dims[3] = {128, static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols / 128)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld), 128};
+    cuuint32_t box[3] = {128, static_cast<cuuint32_t>(box_rows), static_cast<cuuint32_t>(chunks)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// True when a problem is split along K (see split_count): K spans at least
+// 32 k-blocks, and its Q side fits one tile of at most 32 columns with the
+// tiles filling at most half the SMs, or of at most 64 columns with the
+// tiles filling at most a quarter.  Measured on L2-cold skinny products, the
+// split's extra pass over the partial sums (about 1.5 us, more for wider
+// tiles) costs more than the shorter K loop saves outside that range.
 bool splits_k(int64_t rows_p, int64_t rows_q, int64_t K)
 {
     const int64_t m_blocks = (rows_p + BM - 1) / BM;
-    return rows_q <= 64 && (K + BK - 1) / BK >= 16 && m_blocks > 0 && 2 * m_blocks <= sm_count();
+    const int sms = sm_count();
+    if ((K + BK - 1) / BK < 32 || m_blocks <= 0)
+        return false;
+    return (rows_q <= 32 && 2 * m_blocks <= sms) || (rows_q <= 64 && 4 * m_blocks <= sms);
 }
 
 // N of the MMA tile for a problem of rows_p x rows_q: the smallest of
@@ -836,6 +902,14 @@ int validate(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, con
 // or under any tile configuration.  Every slice gets at least eight k-blocks
 // (K >= 1024): below that the extra pass over the partials costs more than
 // the shorter K loop saves.  No slice is empty.
+// k-blocks per slice when K is cut into s slices: a multiple of 4, so
+// slices start on stage boundaries whatever the k-blocks per stage of the
+// launch.
+int slice_kblocks(int k_blocks, int s)
+{
+    return ((k_blocks + s - 1) / s + 3) / 4 * 4;
+}
+
 int split_count(const Job& j)
 {
     const int sms = sm_count();
@@ -847,24 +921,29 @@ int split_count(const Job& j)
     s = std::min(s, k_blocks / 8);
     if (s <= 1)
         return 1;
-    const int kbs = (k_blocks + s - 1) / s;
+    const int kbs = slice_kblocks(k_blocks, s);
     return (k_blocks + kbs - 1) / kbs;
 }
 
 // Fill one problem entry for a launch with MT row-halves per tile.
-int fill_problem(Problem& pr, const Job& j, int bn, int mt)
+int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
 {
     memset(&pr, 0, sizeof(pr));
     pr.sparse = j.E != nullptr;
     const int box_p = BM * mt;
-    if (pr.sparse) {
+    pr.tma3d = kc > 1 && !pr.sparse && j.K % BK == 0 &&
+               make_map3(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, box_p, kc) &&
+               make_map3(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, bn, kc);
+    if (pr.tma3d) {
+        // both maps made
+    } else if (pr.sparse) {
         if (!make_map(&pr.tmP, j.P, j.rows_p, j.K / 2, j.K / 2, BK / 2, box_p, CU_TENSOR_MAP_SWIZZLE_64B) ||
             !make_map(&pr.tmE, j.E, j.rows_p, j.K / 8, j.K / 8, BK / 8, box_p, CU_TENSOR_MAP_SWIZZLE_NONE))
             return FP8_ERR_CUDA;
     } else if (!make_map(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BK, box_p, CU_TENSOR_MAP_SWIZZLE_128B)) {
         return FP8_ERR_CUDA;
     }
-    if (!make_map(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, CU_TENSOR_MAP_SWIZZLE_128B))
+    if (!pr.tma3d && !make_map(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, CU_TENSOR_MAP_SWIZZLE_128B))
         return FP8_ERR_CUDA;
     pr.sp = j.sp;
     pr.sq = j.sq;
@@ -885,7 +964,8 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt)
     pr.n_blocks = static_cast<int>((j.rows_q + bn - 1) / bn);
     pr.k_blocks = static_cast<int>((j.K + BK - 1) / BK);
     pr.splits = split_count(j);
-    pr.kb_per_split = (pr.k_blocks + pr.splits - 1) / pr.splits;
+    pr.kb_per_split = pr.splits > 1 ? slice_kblocks(pr.k_blocks, pr.splits) : pr.k_blocks;
+    pr.splits = (pr.k_blocks + pr.kb_per_split - 1) / pr.kb_per_split;     // no empty slice
     pr.idesc = idesc_e4m3_f32(BM, bn, pr.sparse != 0, 0);
     return FP8_OK;
 }
@@ -937,10 +1017,10 @@ void bind_workspace(Params<MAXP>& prm, const Plan& pl, void* base)
     bind_workspace(prm, base, pl.ctr_count);
 }
 
-template <int MAXP, int MT, bool SP, int BNC = BN_MAX>
+template <int MAXP, int MT, bool SP, int BNC = BN_MAX, int KC = 1>
 int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
 {
-    using C = Cfg<MT, SP, BNC>;
+    using C = Cfg<MT, SP, BNC, KC>;
     static std::once_flag attr_once[64];
     int dev = 0;
     GB_CUDA_OK(cudaGetDevice(&dev));
@@ -948,7 +1028,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
         return FP8_ERR_UNSUPPORTED;
     cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once[dev], [&] {
-        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP, BNC>,
+        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     });
     GB_CUDA_OK(attr_err);
@@ -973,7 +1053,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
-    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC>);
+    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC>);
     out->grid = grid;
     out->threads = C::kThreads;
     out->smem = C::kSmem;
@@ -1090,20 +1170,33 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
 {
     const TileChoice c = choose(jobs, bns_in, n, max_ctas, expl);
     const bool sparse = n > 0 && jobs[0].E != nullptr;     // all alike when mt == 2
+    int max_bn = 0;
+    bool any_sparse = false;
+    for (int i = 0; i < n; ++i) {
+        max_bn = std::max(max_bn, bns_in[i]);
+        any_sparse = any_sparse || jobs[i].E != nullptr;
+    }
+    const int kc = (c.mt == 1 && !any_sparse && max_bn <= 128) ? 2 : 1;
     for (int i = 0; i < n; ++i) {
         int bn = bns_in[i];
         if (c.mt == 2 && sparse)
             bn = std::min(bn, SPARSE_BN_MAX_MT2);
-        int rc = fill_problem(prm.prob[i], jobs[i], bn, c.mt);
+        int rc = fill_problem(prm.prob[i], jobs[i], bn, c.mt, kc);
         if (rc != FP8_OK)
             return rc;
     }
     prm.num_problems = n;
     prm.group_m = c.group_m;
     if (c.mt == 1) {
-        int max_bn = 0;
-        for (int i = 0; i < n; ++i)
-            max_bn = std::max(max_bn, bns_in[i]);
+        if (kc == 2) {
+            if (max_bn <= 16)
+                return plan<MAXP, 1, false, 16, 2>(prm, max_ctas, pl);
+            if (max_bn <= 32)
+                return plan<MAXP, 1, false, 32, 2>(prm, max_ctas, pl);
+            if (max_bn <= 64)
+                return plan<MAXP, 1, false, 64, 2>(prm, max_ctas, pl);
+            return plan<MAXP, 1, false, 128, 2>(prm, max_ctas, pl);
+        }
         if (max_bn <= 16)
             return plan<MAXP, 1, false, 16>(prm, max_ctas, pl);
         if (max_bn <= 32)

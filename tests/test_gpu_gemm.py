@@ -189,8 +189,8 @@ def test_tile_configs_bitwise_equal_and_correct(gb, orc, tile_cfg, M, N, K, gm):
     parity.check_fp32(outs[1], orc.gemm(A, B, dA, 1, dB, 1))
 
 
-@pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (1, 8192, 2048), (1024, 1024, 1024),
-                                   (100, 300, 2000)])
+@pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (1, 8192, 4096), (40, 2048, 8192),
+                                   (1024, 1024, 1024), (100, 300, 2000)])
 def test_split_k_repeatable_and_correct(gb, orc, M, N, K):
     """Few 128-row tiles: K is split across CTAs (partials in the stream's
     workspace, the last unit of each tile adds them in slice order).  Calls
@@ -210,7 +210,7 @@ def test_split_k_workspace_reuse_streams_and_capture(gb, orc):
     that grows and shrinks it, the same calls on a second stream, and a
     captured graph (which owns a workspace of its own, freed after the graph
     is destroyed) all give the bitwise-same results as the first calls."""
-    shapes = [(8, 4096, 2048), (16, 8192, 8192), (8, 4096, 2048), (1, 2048, 4096)]
+    shapes = [(8, 4096, 4096), (16, 8192, 8192), (8, 4096, 4096), (1, 2048, 4096)]
     data = []
     for i, (M, N, K) in enumerate(shapes):
         A = _codes(workloads.random_codes((M, K), seed=300 + i))
