@@ -75,16 +75,25 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 // chunks bn x 128 bytes apart); BNC = 128 / 64 / 32 / 16 then run 3 / 4 / 5
 // / 5 stages of 64 / 48 / 40 / 36 KB.  When K % 128 == 0 one 3-D TMA box per
 // operand (x: byte in a 128-byte chunk, y: row, z: chunk) brings all KC
-// chunks of a stage, else one 2-D box per chunk.  Launches with sparse
-// problems, BNC = 256 and MT = 2 keep KC = 1.
+// chunks of a stage, else one 2-D box per chunk.  Launches whose problems
+// are all 2:4-sparse (SP = true, KC = 2) hold per stage the kept codes of
+// both k-blocks (8 KB each, 64-byte swizzle), then both metadata blocks
+// (2 KB each), then the B chunks: 4 / 5 / 7 / 8 stages for BNC = 128 / 64 /
+// 32 / 16, each k-block's metadata in its own 4 TMEM columns.  Launches
+// mixing dense and sparse problems, BNC = 256 and MT = 2 keep KC = 1.
 template <int MT, bool SP = false, int BNC = BN_MAX, int KC = 1>
 struct Cfg {
     static constexpr bool kSparse2 = MT == 2 && SP;
     static constexpr int kStages =
-        KC == 2 ? (BNC == 128 ? 3 : (BNC == 64 ? 4 : 5))
+        KC == 2 ? (SP ? (BNC == 128 ? 4 : (BNC == 64 ? 5 : (BNC == 32 ? 7 : 8)))
+                      : (BNC == 128 ? 3 : (BNC == 64 ? 4 : 5)))
                 : MT == 2 ? (SP ? 4 : 3)
                           : (BNC == 256 ? 4 : (BNC == 128 ? 6 : (BNC == 64 ? 8 : (BNC == 32 ? 9 : 11))));
-    static constexpr int kAChunk = MT == 1 ? BM * BK : (SP ? 2 * BM * (BK / 2 + BK / 8) : 2 * BM * BK);
+    static constexpr int kSpChunk = MT * BM * BK / 2;            // kept codes of one k-block
+    static constexpr int kMetaChunk = MT * BM * BK / 8;          // metadata of one k-block
+    // A bytes of one k-block: dense codes, or (SP launches) kept codes +
+    // metadata; 128-row dense-capable tiles also hold a sparse k-block there
+    static constexpr int kAChunk = SP ? kSpChunk + kMetaChunk : MT * BM * BK;
     static constexpr int kBChunk = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : BNC * BK;
     static constexpr int kABytes = KC * kAChunk;
     static constexpr int kBBytes = KC * kBChunk;
@@ -92,18 +101,17 @@ struct Cfg {
     static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : (BNC == 256 ? SPARSE_BN_MAX : BNC);
     static constexpr int kAcc = MT == 2 ? 1 : 2;                  // accumulator buffers
     static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
-    static constexpr int kSpABytes = MT * BM * BK / 2;           // kept codes of a stage
     static constexpr int kEpiWarps = 4 * MT;
     static constexpr int kEpiBytes = kEpiWarps * 32 * 128;       // 32 rows x 128 B per warp
     static constexpr int kSmem = 1024 + kStages * kStageBytes + 256 + kEpiBytes;
-    static_assert(kMetaCol0 + 4 * kStages <= BN_MAX, "metadata ring must fit beside the accumulator");
-    static_assert(kSpABytes + MT * BM * BK / 8 <= kABytes || (MT == 2 && !SP),
+    static_assert(kMetaCol0 + 4 * kStages * KC <= BN_MAX, "metadata ring must fit beside the accumulator");
+    static_assert(KC * (kSpChunk + kMetaChunk) <= kABytes || (MT == 2 && !SP),
                   "sparse A + metadata fit the A region");
     static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "swizzle atoms stay aligned");
     static_assert(kSmem <= 232448, "shared memory per CTA");
     static_assert((2 * kStages + 2 * kAcc + 3) * 8 + 12 <= 256, "barriers and flags fit their 256-byte region");
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
-    static_assert(KC == 1 || (KC == 2 && MT == 1 && !SP && BNC <= 128), "two-chunk stages: dense 128-row tiles");
+    static_assert(KC == 1 || (KC == 2 && MT == 1 && BNC <= 128), "two-chunk stages: 128-row tiles");
     static_assert(kBChunk % 1024 == 0, "B chunks stay swizzle-atom aligned");
 };
 
@@ -495,8 +503,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                 const CUtensorMap* map_p = &prm.prob[tc.p].tmP;
                 const CUtensorMap* map_q = &prm.prob[tc.p].tmQ;
                 const CUtensorMap* map_e = &prm.prob[tc.p].tmE;
-                const bool sparse = KC == 1 && P.sparse != 0;
-                const uint32_t a_bytes = sparse ? C::kSpABytes + MT * BM * BK / 8 : C::kAChunk;
+                const bool sparse = P.sparse != 0;
+                const uint32_t a_bytes = sparse ? C::kSpChunk + C::kMetaChunk : C::kAChunk;
                 const uint32_t b_chunk = static_cast<uint32_t>(P.bn) * BK;      // B chunks bn x 128 B apart
                 const uint32_t chunk_bytes = a_bytes + b_chunk;
                 const int row0 = tc.m_blk * BM * MT;
@@ -515,19 +523,24 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                     mbar_arrive_expect_tx(full_bar(stage),
                                           chunk_bytes * static_cast<uint32_t>(KC > 1 && P.tma3d ? KC : nck));
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
-                    if (sparse) {
+                    if (sparse && KC > 1) {
+                        // kept codes then metadata of all KC k-blocks (3-D chunk boxes)
+                        tma_load_3d(sa, map_p, full_bar(stage), 0, row0, kb);
+                        tma_load_3d(sa + KC * C::kSpChunk, map_e, full_bar(stage), 0, row0, kb);
+                    } else if (sparse) {
                         tma_load_2d(sa, map_p, full_bar(stage), kb * (BK / 2), row0);
-                        tma_load_2d(sa + C::kSpABytes, map_e, full_bar(stage), kb * (BK / 8), row0);
+                        tma_load_2d(sa + C::kSpChunk, map_e, full_bar(stage), kb * (BK / 8), row0);
                     } else if (KC > 1 && P.tma3d) {
                         tma_load_3d(sa, map_p, full_bar(stage), 0, row0, kb);
-                        tma_load_3d(sa + C::kABytes, map_q, full_bar(stage), 0, col0, kb);
                     } else {
 #pragma unroll
                         for (int c = 0; c < KC; ++c)
                             if (c < nck)
                                 tma_load_2d(sa + c * C::kAChunk, map_p, full_bar(stage), (kb + c) * BK, row0);
                     }
-                    if (!(KC > 1 && P.tma3d)) {
+                    if (KC > 1 && P.tma3d) {
+                        tma_load_3d(sa + C::kABytes, map_q, full_bar(stage), 0, col0, kb);
+                    } else {
 #pragma unroll
                         for (int c = 0; c < KC; ++c)
                             if (c < nck)
@@ -564,7 +577,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x, ++local) {
                 const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
                 const ProblemScalars P = prm.prob[tc.p];
-                const bool sparse = KC == 1 && P.sparse != 0;
+                const bool sparse = P.sparse != 0;
                 const uint32_t idesc = P.idesc;
                 const uint32_t b_chunk = static_cast<uint32_t>(P.bn) * BK;      // B chunks bn x 128 B apart
                 const int acc = local % C::kAcc;
@@ -591,26 +604,30 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
                     const uint64_t bdesc = sdesc_kmajor_sw128(sa + C::kABytes);
                     if (sparse) {
-                        // metadata of this k-block -> TMEM slot of this stage
-                        // (tcgen05.cp and the MMAs below execute in issue order)
-                        const uint32_t sm_meta = sa + C::kSpABytes;
 #pragma unroll
-                        for (int h = 0; h < MT; ++h) {
-                            const uint32_t meta = tmem_base + static_cast<uint32_t>(
-                                                                  h * BN_MAX + C::kMetaCol0 + 4 * stage);
-                            tmem_cp_128x128b(meta, sdesc_rows16_noswizzle(sm_meta + h * BM * 16));
-                        }
+                        for (int c = 0; c < KC; ++c) {
+                            if (c >= nck)
+                                break;
+                            // metadata of k-block c -> its TMEM columns (tcgen05.cp
+                            // and the MMAs below execute in issue order)
+                            const uint32_t sm_meta = sa + KC * C::kSpChunk + c * C::kMetaChunk;
+                            const uint32_t mcol = static_cast<uint32_t>(C::kMetaCol0 + 4 * (stage * KC + c));
 #pragma unroll
-                        for (int k = 0; k < BK / 64; ++k) {
+                            for (int h = 0; h < MT; ++h)
+                                tmem_cp_128x128b(tmem_base + h * BN_MAX + mcol,
+                                                 sdesc_rows16_noswizzle(sm_meta + h * BM * 16));
+                            const uint64_t bdesc_c = sdesc_kmajor_sw128(sa + C::kABytes + c * b_chunk);
 #pragma unroll
-                            for (int h = 0; h < MT; ++h) {
-                                // logical K = 64 per MMA: 32 kept A bytes, 64 B
-                                // bytes, 64 metadata bits (two TMEM columns)
-                                const uint64_t adesc = sdesc_kmajor_sw64(sa + h * BM * 64);
-                                const uint32_t meta = tmem_base + static_cast<uint32_t>(
-                                                                      h * BN_MAX + C::kMetaCol0 + 4 * stage);
-                                mma_sp_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc + 4u * k,
-                                              meta + 2u * k, idesc, (first | k) != 0 ? 1u : 0u);
+                            for (int k = 0; k < BK / 64; ++k) {
+#pragma unroll
+                                for (int h = 0; h < MT; ++h) {
+                                    // logical K = 64 per MMA: 32 kept A bytes, 64 B
+                                    // bytes, 64 metadata bits (two TMEM columns)
+                                    const uint64_t adesc = sdesc_kmajor_sw64(sa + c * C::kSpChunk + h * BM * 64);
+                                    mma_sp_f8f6f4(d_tmem + h * BN_MAX, adesc + 2u * k, bdesc_c + 4u * k,
+                                                  tmem_base + h * BN_MAX + mcol + 2u * k, idesc,
+                                                  (first | c | k) != 0 ? 1u : 0u);
+                                }
                             }
                         }
                     } else {
@@ -777,22 +794,24 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, in
     return r == CUDA_SUCCESS;
 }
 
-// 3-D view of a byte matrix [rows, cols] (cols % 128 == 0, row stride ld
-// bytes) as x = byte within a 128-byte K chunk, y = row, z = chunk; box
-// {128, box_rows, chunks}: one copy lands `chunks` swizzled K-major tiles of
-// box_rows x 128 bytes back to back in shared memory.
-bool make_map3(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-               int chunks)
+// 3-D view of a byte matrix [rows, cols] (cols % chunk == 0, row stride ld
+// bytes) as x = byte within a chunk of K, y = row, z = chunk; box {chunk,
+// box_rows, chunks}: one copy lands `chunks` tiles of box_rows x chunk bytes
+// back to back in shared memory, each swizzled as a 2-D box would be.
+bool make_map3(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int chunk,
+               int box_rows, int chunks, CUtensorMapSwizzle swizzle)
 {
     auto fn = encode_fn();
     if (!fn)
         return false;
-    cuuint64_t dims[3] = {128, static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols / 128)};
-    cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld), 128};
-    cuuint32_t box[3] = {128, static_cast<cuuint32_t>(box_rows), static_cast<cuuint32_t>(chunks)};
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(chunk), static_cast<cuuint64_t>(rows),
+                          static_cast<cuuint64_t>(cols / chunk)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(chunk)};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(chunk), static_cast<cuuint32_t>(box_rows),
+                         static_cast<cuuint32_t>(chunks)};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -931,11 +950,21 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
     memset(&pr, 0, sizeof(pr));
     pr.sparse = j.E != nullptr;
     const int box_p = BM * mt;
-    pr.tma3d = kc > 1 && !pr.sparse && j.K % BK == 0 &&
-               make_map3(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, box_p, kc) &&
-               make_map3(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, bn, kc);
+    if (kc > 1 && pr.sparse) {
+        // sparse K is a multiple of 128: kept codes in 64-byte chunks,
+        // metadata in 16-byte chunks, B in 128-byte chunks
+        if (!make_map3(&pr.tmP, j.P, j.rows_p, j.K / 2, j.K / 2, BK / 2, box_p, kc, CU_TENSOR_MAP_SWIZZLE_64B) ||
+            !make_map3(&pr.tmE, j.E, j.rows_p, j.K / 8, j.K / 8, BK / 8, box_p, kc, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+            !make_map3(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, kc, CU_TENSOR_MAP_SWIZZLE_128B))
+            return FP8_ERR_CUDA;
+        pr.tma3d = 1;
+    } else {
+        pr.tma3d = kc > 1 && j.K % BK == 0 &&
+                   make_map3(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BK, box_p, kc, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                   make_map3(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, kc, CU_TENSOR_MAP_SWIZZLE_128B);
+    }
     if (pr.tma3d) {
-        // both maps made
+        // maps made above
     } else if (pr.sparse) {
         if (!make_map(&pr.tmP, j.P, j.rows_p, j.K / 2, j.K / 2, BK / 2, box_p, CU_TENSOR_MAP_SWIZZLE_64B) ||
             !make_map(&pr.tmE, j.E, j.rows_p, j.K / 8, j.K / 8, BK / 8, box_p, CU_TENSOR_MAP_SWIZZLE_NONE))
@@ -1171,12 +1200,15 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
     const TileChoice c = choose(jobs, bns_in, n, max_ctas, expl);
     const bool sparse = n > 0 && jobs[0].E != nullptr;     // all alike when mt == 2
     int max_bn = 0;
-    bool any_sparse = false;
+    bool any_sparse = false, all_sparse = n > 0;
     for (int i = 0; i < n; ++i) {
         max_bn = std::max(max_bn, bns_in[i]);
         any_sparse = any_sparse || jobs[i].E != nullptr;
+        all_sparse = all_sparse && jobs[i].E != nullptr;
     }
-    const int kc = (c.mt == 1 && !any_sparse && max_bn <= 128) ? 2 : 1;
+    // two k-blocks per stage for 128-row tiles up to 128 wide, unless the
+    // launch mixes dense and sparse problems
+    const int kc = (c.mt == 1 && max_bn <= 128 && (!any_sparse || all_sparse)) ? 2 : 1;
     for (int i = 0; i < n; ++i) {
         int bn = bns_in[i];
         if (c.mt == 2 && sparse)
@@ -1188,6 +1220,15 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
     prm.num_problems = n;
     prm.group_m = c.group_m;
     if (c.mt == 1) {
+        if (kc == 2 && all_sparse) {
+            if (max_bn <= 16)
+                return plan<MAXP, 1, true, 16, 2>(prm, max_ctas, pl);
+            if (max_bn <= 32)
+                return plan<MAXP, 1, true, 32, 2>(prm, max_ctas, pl);
+            if (max_bn <= 64)
+                return plan<MAXP, 1, true, 64, 2>(prm, max_ctas, pl);
+            return plan<MAXP, 1, true, 128, 2>(prm, max_ctas, pl);
+        }
         if (kc == 2) {
             if (max_bn <= 16)
                 return plan<MAXP, 1, false, 16, 2>(prm, max_ctas, pl);
