@@ -231,8 +231,10 @@ def config(size, ws):
 
 class ServingBench:
     """Poisson stream of FP8 GEMM requests from two tenants against resident
-    weights, served by the library's request server in continuous-batching
-    mode and in per-call mode (one quantise + one GEMM launch per request).
+    weights, served by the library's request server in three modes: per call
+    (one quantise + one GEMM launch per request), continuous batching, and
+    continuous batching with co-scheduling (the bulk tenant's GEMMs capped
+    at SMs - 24 CTAs so the latency tenant always finds free SMs).
 
     Tenant 0 (latency): M log-uniform in [1, 64]; tenant 1 (throughput): M
     log-uniform in [64, 4096]; (N, K) uniform over {4096, 8192, 14336}^2;
@@ -277,22 +279,26 @@ class ServingBench:
         self.arena_pos += (n + 127) // 128 * 128
         return o.data_ptr()
 
-    def _server(self, batching):
+    MODES = {"per_call": (False, False), "batched": (True, False), "batched_coscheduled": (True, True)}
+
+    def _server(self, mode):
         from paper_2602_10262_gb300.server import Server
         sms = self.gb.fp8_device_sm_count()
+        batching, cosched = self.MODES[mode]
         srv = Server(num_tenants=2, latency_tenant=0, batching=batching,
-                     bulk_max_ctas=max(sms - 24, 1) if batching else 0, pool_bytes=4 << 30)
+                     bulk_max_ctas=max(sms - 24, 1) if cosched else 0, pool_bytes=4 << 30)
         handles = {}
         for (N, K), (Wd, dW, vals, meta) in self.weights.items():
             handles[(N, K, False)] = srv.register_weight(N, K, Wd, dW, 1)
             handles[(N, K, True)] = srv.register_weight(N, K, vals, dW, 1, W_meta=meta)
         return srv, handles
 
-    def run(self, reqs, batching, rate=None):
+    def run(self, reqs, mode, rate=None):
         """Submit `reqs` (all at once when rate is None, else Poisson at
-        `rate` requests/s); returns per-request (latency_us, tenant, flops)
-        and the makespan in microseconds."""
-        srv, handles = self._server(batching)
+        `rate` requests/s) to a server in `mode`; returns per-request
+        latencies, the makespan in microseconds, the server's stats and the
+        results."""
+        srv, handles = self._server(mode)
         ld = self.X.stride(0)
         try:
             times = None
@@ -325,7 +331,7 @@ class ServingBench:
 
     def isolated(self, reqs):
         """Latency of each request run alone (per-call server, one at a time)."""
-        srv, handles = self._server(False)
+        srv, handles = self._server("per_call")
         ld = self.X.stride(0)
         out = []
         try:
@@ -343,13 +349,13 @@ def serving_report(gb, dev, n_cap=1500, n_load=1500, load=0.8):
     sb = ServingBench(dev, gb)
     cap_reqs = sb.trace(n_cap, workloads.SEED_REQUESTS + 1)
     cap = {}
-    for mode, batching in (("batched", True), ("per_call", False)):
-        sb.run(cap_reqs[:64], batching)                      # warm-up
-        _, span, stats, _ = sb.run(cap_reqs, batching)
+    for mode in ServingBench.MODES:
+        sb.run(cap_reqs[:64], mode)                          # warm-up
+        _, span, stats, _ = sb.run(cap_reqs, mode)
         cap[mode] = {"tflops": sb.flops(cap_reqs) / (span * 1e-6) / 1e12,
                      "req_per_s": n_cap / (span * 1e-6),
                      "kernel_launches": stats["kernel_launches"], "batches": stats["batches"]}
-    rate = load * min(cap["batched"]["req_per_s"], cap["per_call"]["req_per_s"])
+    rate = load * min(c["req_per_s"] for c in cap.values())
     reqs = sb.trace(n_load, workloads.SEED_REQUESTS)
     iso = sb.isolated(reqs)
     tenant = np.array([r["tenant"] for r in reqs])
@@ -357,8 +363,8 @@ def serving_report(gb, dev, n_cap=1500, n_load=1500, load=0.8):
                        "(N,K) in {4096,8192,14336}^2, 50% 2:4-sparse weights",
            "offered_load": f"{load} x per-call capacity = {rate:.0f} req/s",
            "capacity": cap}
-    for mode, batching in (("batched", True), ("per_call", False)):
-        lat, span, stats, res = sb.run(reqs, batching, rate)
+    for mode in ServingBench.MODES:
+        lat, span, stats, res = sb.run(reqs, mode, rate)
         slow = iso / lat
         x = [float(np.mean(slow[tenant == t])) for t in (0, 1)]
         mean_lat = [float(np.mean(lat[tenant == t])) for t in (0, 1)]

@@ -341,7 +341,7 @@ typedef struct {
     int latency_tenant;       /* tenant given the high-priority stream (-1: none) */
     int batching;             /* 1: continuous batching; 0: one launch per request */
     int max_batch;            /* requests per batch, 1..FP8_GROUPED_MAX_PROBLEMS (0: max) */
-    int max_inflight;         /* in-flight batches per tenant (0: 2) */
+    int max_inflight;         /* in-flight batches per tenant (0: 4) */
     int bulk_max_ctas;        /* CTA cap for non-latency tenants' GEMMs (0: all SMs) */
     size_t pool_bytes;        /* workspace pool; 0: free HBM minus reserve_bytes */
     size_t reserve_bytes;     /* HBM left untouched when sizing the pool (0: 1 GiB) */

@@ -548,7 +548,7 @@ int normalise(const fp8_server_config* in, fp8_server_config* out)
     if (c.max_batch > FP8_QUANT_GROUPED_MAX)
         c.max_batch = FP8_QUANT_GROUPED_MAX;
     if (c.max_inflight <= 0)
-        c.max_inflight = 2;
+        c.max_inflight = 4;
     if (c.bulk_max_ctas < 0)
         c.bulk_max_ctas = 0;
     *out = c;
