@@ -446,9 +446,17 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     grid_launch_dependents();
-    // The first tile's coordinates and tensor maps are fetched before the
-    // setup below, so their parameter loads overlap it.
+    // Loop-invariant parameters, the first tile's coordinates and problem
+    // scalars are read into registers before the setup below, so their
+    // parameter loads overlap it (indexed parameter reads are memory loads,
+    // and the asm statements below would otherwise make the compiler repeat
+    // them on the critical path).
+    const int total_tiles = prm.total_tiles;
+    int* const err = prm.err;
+    float* const ws = prm.ws;
+    unsigned* const ctr = prm.ctr;
     const TileCoord tc_first = tile_coord(prm, blockIdx.x);
+    const ProblemScalars P_first = prm.prob[tc_first.p];
     if (threadIdx.x == 0) {
         tma_prefetch_desc(&prm.prob[tc_first.p].tmP);
         tma_prefetch_desc(&prm.prob[tc_first.p].tmQ);
@@ -491,15 +499,16 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             uint32_t phase = 0;
             uint32_t armed = 0;                 // bit s: slot s armed at least once
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x) {
+            for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
                 const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
-                if (tile != static_cast<int>(blockIdx.x) || prm.prob[tc.p].sparse) {
+                const bool first = tile == static_cast<int>(blockIdx.x);
+                const ProblemScalars P = first ? P_first : prm.prob[tc.p];
+                if (!first || P.sparse) {
                     tma_prefetch_desc(&prm.prob[tc.p].tmP);
                     tma_prefetch_desc(&prm.prob[tc.p].tmQ);
-                    if (prm.prob[tc.p].sparse)
+                    if (P.sparse)
                         tma_prefetch_desc(&prm.prob[tc.p].tmE);
                 }
-                const ProblemScalars P = prm.prob[tc.p];
                 const CUtensorMap* map_p = &prm.prob[tc.p].tmP;
                 const CUtensorMap* map_q = &prm.prob[tc.p].tmQ;
                 const CUtensorMap* map_e = &prm.prob[tc.p].tmE;
@@ -516,7 +525,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                     // a slot never armed is free: no wait on its first use
                     if (((armed >> stage) & 1u) && !mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
                         ok = false;
-                        abort_pipeline(abort_flag, prm.err);
+                        abort_pipeline(abort_flag, err);
                         break;
                     }
                     // a 3-D box always lands all KC chunks (those past K as zeros)
@@ -574,9 +583,9 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             uint32_t phase = 0;
             int local = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < prm.total_tiles; tile += gridDim.x, ++local) {
+            for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x, ++local) {
                 const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
-                const ProblemScalars P = prm.prob[tc.p];
+                const ProblemScalars P = tile == static_cast<int>(blockIdx.x) ? P_first : prm.prob[tc.p];
                 const bool sparse = P.sparse != 0;
                 const uint32_t idesc = P.idesc;
                 const uint32_t b_chunk = static_cast<uint32_t>(P.bn) * BK;      // B chunks bn x 128 B apart
@@ -584,7 +593,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                 const uint32_t acc_phase = (local / C::kAcc) & 1;
                 // an accumulator not used yet is free: no wait on its first use
                 if (local >= C::kAcc && !mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag)) {
-                    abort_pipeline(abort_flag, prm.err);
+                    abort_pipeline(abort_flag, err);
                     break;
                 }
                 tc_fence_after();
@@ -597,7 +606,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                     const uint32_t first = kb == kb0 ? 0u : 1u;     // 0: overwrite the accumulator
                     if (!mbar_wait(full_bar(stage), phase, abort_flag)) {
                         ok = false;
-                        abort_pipeline(abort_flag, prm.err);
+                        abort_pipeline(abort_flag, err);
                         break;
                     }
                     tc_fence_after();
@@ -670,9 +679,9 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
         const int row = half * BM + quarter * 32 + lane;
         int local = 0;
         uint32_t split_phase = 0;
-        for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++local) {
+        for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++local) {
             const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
-            const ProblemScalars& P = prm.prob[tc.p];
+            const ProblemScalars P = tile == static_cast<int>(blockIdx.x) ? P_first : prm.prob[tc.p];
             const int acc = local % C::kAcc;
             const uint32_t acc_phase = (local / C::kAcc) & 1;
             // the scales do not depend on the accumulator: load them first
@@ -685,7 +694,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             // the whole warp takes the same branch (tcgen05.ld is warp-collective)
             const bool got = mbar_wait(tfull_bar(acc), acc_phase, abort_flag);
             if (!__all_sync(0xFFFFFFFFu, got)) {
-                abort_pipeline(abort_flag, prm.err);
+                abort_pipeline(abort_flag, err);
                 break;
             }
             tc_fence_after();
@@ -696,32 +705,32 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                 // thread counts this unit in; the tile's last unit reduces.
                 // (The verdict slot is rewritten only after every thread has
                 // arrived for the next split tile, i.e. after it was read.)
-                split_write_partial(P, prm.ws, BM * MT, tc.tile, tc.slice, row, taddr);
+                split_write_partial(P, ws, BM * MT, tc.tile, tc.slice, row, taddr);
                 tc_fence_before();
                 mbar_arrive(tempty_bar(acc));          // TMEM is free; the reduction reads global memory
                 __threadfence();
                 mbar_arrive(split_written_bar);
                 if (threadIdx.x == 64) {
                     if (mbar_wait(split_written_bar, split_phase, abort_flag)) {
-                        const unsigned prev = atomicAdd(prm.ctr + P.ctr_off + tc.tile, 1u);
+                        const unsigned prev = atomicAdd(ctr + P.ctr_off + tc.tile, 1u);
                         *split_flag = (prev == static_cast<unsigned>(P.splits - 1)) ? 1 : 0;
                     } else {
                         *split_flag = 0;
-                        abort_pipeline(abort_flag, prm.err);
+                        abort_pipeline(abort_flag, err);
                     }
                     mbar_arrive(split_verdict_bar);
                 }
                 const bool got_verdict = mbar_wait(split_verdict_bar, split_phase, abort_flag);
                 split_phase ^= 1u;
                 if (!__all_sync(0xFFFFFFFFu, got_verdict)) {
-                    abort_pipeline(abort_flag, prm.err);
+                    abort_pipeline(abort_flag, err);
                     break;
                 }
                 if (*split_flag) {
                     __threadfence();
-                    split_reduce_store(P, prm.ws, BM * MT, tc.tile, row, i, row_ok, fi, jbase, sw, lane);
+                    split_reduce_store(P, ws, BM * MT, tc.tile, row, i, row_ok, fi, jbase, sw, lane);
                     if (threadIdx.x == 64)
-                        prm.ctr[P.ctr_off + tc.tile] = 0u;         // ready for the next launch
+                        ctr[P.ctr_off + tc.tile] = 0u;         // ready for the next launch
                 }
                 continue;
             }
