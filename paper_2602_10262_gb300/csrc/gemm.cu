@@ -31,6 +31,7 @@
 #include <memory>
 #include <mutex>
 #include <set>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -156,6 +157,7 @@ struct Params {
     int* err;
     float* ws;              // split-K partial sums (nullptr when no problem splits)
     unsigned* ctr;          // split-K arrival counters, zero between launches
+    int cluster_split;      // > 0: one problem whose split tiles run as clusters of this many CTAs
 };
 
 struct TileCoord {
@@ -341,6 +343,55 @@ __device__ __forceinline__ void split_reduce_store(const ProblemScalars& P, cons
     }
 }
 
+// Split-K within a cluster (one unit per CTA, the slices of a tile as the
+// CTAs of one cluster, rank = slice).  Slice r > 0 writes its partial sums
+// into the idle TMA ring of the cluster's rank-0 CTA, column by column
+// (element (row, col) of slice r at ((r - 1) * bn + col) * rows_per_tile +
+// row floats from the ring's start).
+__device__ __forceinline__ void cluster_send_partial(const ProblemScalars& P, uint32_t leader_ring,
+                                                     int rows_per_tile, int slice, int row, uint32_t taddr)
+{
+    const uint32_t base = leader_ring + 4u * static_cast<uint32_t>((slice - 1) * P.bn * rows_per_tile + row);
+    for (int c0 = 0; c0 < P.bn; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld_32x32b_x16(taddr + c0, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            st_cluster_f32(base + 4u * static_cast<uint32_t>((c0 + t) * rows_per_tile), __uint_as_float(r[t]));
+    }
+}
+
+// The rank-0 CTA: its own partial from TMEM, then the other slices' from its
+// ring, added in slice order (the same sums as the global split path), then
+// scaled and stored.
+__device__ __forceinline__ void cluster_reduce_store(const ProblemScalars& P, const uint8_t* ring,
+                                                     int rows_per_tile, int row, uint32_t taddr, int i,
+                                                     bool row_ok, float fi, int jbase, ScaleWindows& sw,
+                                                     int lane)
+{
+    const float* recv = reinterpret_cast<const float*>(ring) + row;
+    float s_cur = 0.0f;
+    for (int c0 = 0; c0 < P.bn; c0 += 16) {
+        if ((c0 & 31) == 0)
+            s_cur = sw.take(P, jbase, lane);
+        uint32_t r[16];
+        tmem_ld_32x32b_x16(taddr + c0, r);
+        tmem_ld_wait();
+        float acc[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            acc[t] = __fadd_rn(0.0f, __uint_as_float(r[t]));
+        for (int sl = 1; sl < P.splits; ++sl) {
+            const float* col = recv + ((sl - 1) * P.bn + c0) * rows_per_tile;
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                acc[t] = __fadd_rn(acc[t], col[t * rows_per_tile]);
+        }
+        store_vals16(P, i, row_ok, fi, jbase + c0, acc, s_cur, c0 & 31);
+    }
+}
+
 // Coalesced epilogue for a row-major output (trans_out == 0, 16-byte stores
 // allowed).  The warp owns 32 tile rows (TMEM lanes); per chunk of 128 bytes
 // of output columns (64 bf16 or 32 fp32) each thread scales its row's
@@ -452,6 +503,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
     // and the asm statements below would otherwise make the compiler repeat
     // them on the critical path).
     const int total_tiles = prm.total_tiles;
+    const int cluster_split = prm.cluster_split;
     int* const err = prm.err;
     float* const ws = prm.ws;
     unsigned* const ctr = prm.ctr;
@@ -472,7 +524,9 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             mbar_init(tempty_bar(b), 128 * MT);
         }
         mbar_init(drain_bar, 1);
-        mbar_init(split_written_bar, 128 * MT);
+        // cluster split-K: "written" counts the other slices' epilogue
+        // threads, "verdict" is the rank-0 CTA's "ring free" signal
+        mbar_init(split_written_bar, cluster_split ? (cluster_split - 1) * 128 * MT : 128 * MT);
         mbar_init(split_verdict_bar, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -700,6 +754,36 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             tc_fence_after();
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>((acc + half) * BN_MAX);
+            if (P.splits > 1 && cluster_split) {
+                const int rank = static_cast<int>(cluster_ctarank());
+                if (rank != tc.slice) {                 // launch shape broken: never expected
+                    abort_pipeline(abort_flag, err);
+                    break;
+                }
+                if (rank == 0) {
+                    // every MMA of this unit has completed: the ring is free
+                    if (threadIdx.x == 64)
+                        for (int r = 1; r < P.splits; ++r)
+                            mbar_arrive_remote(cluster_map(split_verdict_bar, static_cast<uint32_t>(r)));
+                    const bool got = mbar_wait_cluster(split_written_bar, 0u, abort_flag);
+                    if (!__all_sync(0xFFFFFFFFu, got)) {
+                        abort_pipeline(abort_flag, err);
+                        break;
+                    }
+                    cluster_reduce_store(P, smem, BM * MT, row, taddr, i, row_ok, fi, jbase, sw, lane);
+                } else {
+                    const bool got = mbar_wait_cluster(split_verdict_bar, 0u, abort_flag);
+                    if (!__all_sync(0xFFFFFFFFu, got)) {
+                        abort_pipeline(abort_flag, err);
+                        break;
+                    }
+                    cluster_send_partial(P, cluster_map(smem_base, 0u), BM * MT, rank, row, taddr);
+                    mbar_arrive_remote(cluster_map(split_written_bar, 0u));
+                }
+                tc_fence_before();
+                mbar_arrive(tempty_bar(acc));
+                continue;
+            }
             if (P.splits > 1) {
                 // every epilogue thread stores its row's partials, then one
                 // thread counts this unit in; the tile's last unit reduces.
@@ -762,6 +846,10 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
     __syncwarp();
     tc_fence_before();
     __syncthreads();
+    // cluster split-K: no CTA leaves while a peer may still write to its
+    // shared memory (every wait above is bounded, so all threads get here)
+    if (cluster_split)
+        cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, TMEM_COLS);
@@ -1020,6 +1108,8 @@ int write_zeros(void* C, int64_t ldc, int64_t rows, int64_t cols, int out_bf16, 
 struct Plan {
     const void* func = nullptr;
     int grid = 0, threads = 0, smem = 0;
+    int cluster = 0;            // > 1: launched as clusters of this many CTAs (split-K in the cluster)
+    size_t ring_bytes = 0;      // bytes of the kernel's TMA ring
     size_t ws_floats = 0;       // split-K partials
     size_t ctr_count = 0;       // split-K tile counters
 };
@@ -1092,6 +1182,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
     out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC>);
+    out->ring_bytes = static_cast<size_t>(C::kStages) * C::kStageBytes;
     out->grid = grid;
     out->threads = C::kThreads;
     out->smem = C::kSmem;
@@ -1107,18 +1198,62 @@ int launch_plan(Params<MAXP>& prm, const Plan& pl, cudaStream_t st)
     // programmatic stream serialization: the kernel's setup may overlap the
     // tail of the previous kernel on `st` (it waits for it before touching
     // global memory)
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = static_cast<unsigned>(pl.cluster);
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.grid);
     cfg.blockDim = dim3(pl.threads);
     cfg.dynamicSmemBytes = static_cast<size_t>(pl.smem);
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pl.cluster > 1 ? 2 : 1;
     GB_CUDA_OK(cudaLaunchKernelExC(&cfg, pl.func, args));
     return FP8_OK;
+}
+
+// True when `clusters` clusters of `size` CTAs of the plan's kernel can all
+// be resident at once (each CTA needs an SM to itself; clusters must fit in
+// one GPC).  Cached per kernel variant and size.
+bool clusters_fit(const Plan& pl, int size, int clusters)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return false;
+    const auto key = std::make_tuple(dev, pl.func, size);
+    int active = -1;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end())
+            active = it->second;
+    }
+    if (active < 0) {
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = static_cast<unsigned>(size);
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(size * clusters));
+        cfg.blockDim = dim3(pl.threads);
+        cfg.dynamicSmemBytes = static_cast<size_t>(pl.smem);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&active, pl.func, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            active = 0;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = active;
+    }
+    return active >= clusters;
 }
 
 // ---------------------------------------------------------------- tile choice
@@ -1203,8 +1338,8 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
 
 // Fill the table for `n` jobs and plan the kernel variant that fits them.
 template <int MAXP>
-int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int max_ctas,
-               const TileChoice* expl, Plan* pl)
+int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int max_ctas,
+                     const TileChoice* expl, Plan* pl)
 {
     const TileChoice c = choose(jobs, bns_in, n, max_ctas, expl);
     const bool sparse = n > 0 && jobs[0].E != nullptr;     // all alike when mt == 2
@@ -1258,6 +1393,34 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
         return plan<MAXP, 1, false, 256>(prm, max_ctas, pl);
     }
     return sparse ? plan<MAXP, 2, true>(prm, max_ctas, pl) : plan<MAXP, 2, false>(prm, max_ctas, pl);
+}
+
+// Plan a launch.  With allow_cluster, a single problem that splits along K
+// runs its tiles' slices as thread-block clusters (the slices add up through
+// distributed shared memory, no workspace) when one unit per CTA covers the
+// problem, the other slices' partial sums fit in a CTA's TMA ring, and all
+// clusters can be resident at once; otherwise the global split path.
+template <int MAXP>
+int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int max_ctas,
+               const TileChoice* expl, Plan* pl, bool allow_cluster = false)
+{
+    const int rc = build_plan_tiles(prm, jobs, bns_in, n, max_ctas, expl, pl);
+    prm.cluster_split = 0;
+    pl->cluster = 0;
+    if (rc != FP8_OK || !allow_cluster || n != 1 || max_ctas != 0)
+        return rc;
+    const ProblemScalars& P = prm.prob[0];
+    const int s = P.splits;
+    const size_t rows_per_tile = static_cast<size_t>(pl->threads - 64);        // BM * MT
+    if (s < 2 || s > 8 || pl->grid != prm.total_tiles || prm.total_tiles % s != 0 ||
+        static_cast<size_t>(s - 1) * P.bn * rows_per_tile * sizeof(float) > pl->ring_bytes ||
+        !clusters_fit(*pl, s, prm.total_tiles / s))
+        return rc;
+    prm.cluster_split = s;
+    pl->cluster = s;
+    pl->ws_floats = 0;
+    pl->ctr_count = 0;
+    return rc;
 }
 
 // Split-K workspaces of eager (not captured) launches, one per device and
@@ -1466,10 +1629,10 @@ int launch_split(Params<MAXP>& prm, const Plan& pl, cudaStream_t st)
 // Plan and launch (split-K plans through launch_split).
 template <int MAXP>
 int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_ctas,
-             cudaStream_t st, const TileChoice* expl = nullptr)
+             cudaStream_t st, const TileChoice* expl = nullptr, bool allow_cluster = false)
 {
     Plan pl;
-    int rc = build_plan(prm, jobs, bns, n, max_ctas, expl, &pl);
+    int rc = build_plan(prm, jobs, bns, n, max_ctas, expl, &pl, allow_cluster);
     if (rc != FP8_OK)
         return rc;
     if (workspace_bytes(pl) == 0) {
@@ -1530,7 +1693,7 @@ extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A,
     const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
-    return run_jobs(prm, &j, &bn, 1, 0, st);
+    return run_jobs(prm, &j, &bn, 1, 0, st, nullptr, true);
 }
 
 // ---------------------------------------------------------------- no-allocation variant
@@ -1625,7 +1788,7 @@ extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t*
     const int bn = pick_bn(j.rows_p, j.rows_q, j.K, SPARSE_BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
-    return run_jobs(prm, &j, &bn, 1, 0, st);
+    return run_jobs(prm, &j, &bn, 1, 0, st, nullptr, true);
 }
 
 extern "C" int gemm_fp8_grouped(const fp8_gemm_problem* problems, int num_problems,

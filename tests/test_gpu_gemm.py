@@ -257,6 +257,34 @@ def test_split_k_workspace_reuse_streams_and_capture(gb, orc):
     parity.check_fp32(first[0].cpu().numpy(), orc.gemm(A, B, one, 0, one, 0))
 
 
+@pytest.mark.parametrize("M,N,K", [(16, 8192, 8192), (16, 4096, 4096), (1, 2048, 4096), (32, 1024, 8192),
+                                   (40, 2048, 8192)])
+def test_split_k_cluster_equals_global_bitwise(gb, orc, M, N, K):
+    """A single call splits its tiles' K range across the CTAs of a cluster
+    (partials added through distributed shared memory) when that fits; the
+    same problem inside a grouped launch takes the global-memory split path.
+    Both add the slices in the same order: bitwise equal, and within the
+    tolerance of the oracle."""
+    A = _codes(workloads.random_codes((M, K), seed=M + 21))
+    B = _codes(workloads.random_codes((N, K), seed=N + 22))
+    sa = torch.from_numpy(np.abs(workloads.randn_f32((M,), seed=5)) + 0.5).cuda()
+    sb = torch.from_numpy(np.abs(workloads.randn_f32((N,), seed=6)) + 0.5).cuda()
+    single = gb.gemm_fp8_dense(A, B, sa, 1, sb, 1, 1.0, gb.OUT_F32)
+    C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    X = _codes(workloads.random_codes((64, 256), seed=3))
+    Y = _codes(workloads.random_codes((64, 256), seed=4))
+    one = _ones(64)
+    Cx = torch.empty((64, 64), dtype=torch.float32, device="cuda")
+    gb.gemm_fp8_grouped([gb.make_problem(A, B, sa, 1, sb, 1, C, 1.0, gb.OUT_F32),
+                         gb.make_problem(X, Y, one, 1, one, 1, Cx, 1.0, gb.OUT_F32)])
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    assert torch.equal(single, C)
+    Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+    ref = orc.gemm(Ah, Bh, sa.cpu().numpy(), 1, sb.cpu().numpy(), 1)
+    parity.check_fp32(single.cpu().numpy(), ref)
+
+
 def test_split_k_integers_exact(gb, orc):
     A = workloads.small_int_codes((8, 6144), seed=91)
     B = workloads.small_int_codes((2048, 6144), seed=92)
