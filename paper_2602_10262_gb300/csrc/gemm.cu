@@ -914,18 +914,17 @@ bool make_map3(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, i
 }
 
 // True when a problem is split along K (see split_count): K spans at least
-// 32 k-blocks, and its Q side fits one tile of at most 32 columns with the
-// tiles filling at most half the SMs, or of at most 64 columns with the
-// tiles filling at most a quarter.  Measured on L2-cold skinny products, the
-// split's extra pass over the partial sums (about 1.5 us, more for wider
-// tiles) costs more than the shorter K loop saves outside that range.
+// 32 k-blocks and its Q side fits one tile of at most 64 columns whose tiles
+// fill at most half the SMs.  Measured on L2-cold skinny products (single
+// calls, slices added within a cluster): below K = 4096, or with more tiles,
+// the extra pass over the partial sums costs more than the shorter K loop
+// saves.
 bool splits_k(int64_t rows_p, int64_t rows_q, int64_t K)
 {
     const int64_t m_blocks = (rows_p + BM - 1) / BM;
-    const int sms = sm_count();
     if ((K + BK - 1) / BK < 32 || m_blocks <= 0)
         return false;
-    return (rows_q <= 32 && 2 * m_blocks <= sms) || (rows_q <= 64 && 4 * m_blocks <= sms);
+    return rows_q <= 64 && 2 * m_blocks <= sm_count();
 }
 
 // N of the MMA tile for a problem of rows_p x rows_q: the smallest of
