@@ -913,40 +913,44 @@ bool make_map3(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, i
     return r == CUDA_SUCCESS;
 }
 
-// True when a problem is split along K (see split_count): K spans at least
-// 32 k-blocks and its Q side fits one tile of at most 64 columns whose tiles
-// fill at most half the SMs.  Measured on L2-cold skinny products (single
-// calls, slices added within a cluster): below K = 4096, or with more tiles,
-// the extra pass over the partial sums costs more than the shorter K loop
-// saves.
-bool splits_k(int64_t rows_p, int64_t rows_q, int64_t K)
-{
-    const int64_t m_blocks = (rows_p + BM - 1) / BM;
-    if ((K + BK - 1) / BK < 32 || m_blocks <= 0)
-        return false;
-    return rows_q <= 64 && 2 * m_blocks <= sm_count();
-}
-
 // N of the MMA tile for a problem of rows_p x rows_q: the smallest of
 // {16, 32, 64, 128, 256} covering rows_q, then halved (down to 64) while the
 // problem has fewer 128-row tiles than half the SMs, so small problems still
 // occupy the GPU.  (Halving further, to a full wave, costs more than it
 // gains: every extra column block reads the P operand again, and the tiles
-// run at a lower ratio of MMA work to loaded bytes.)  A problem that splits
-// along K keeps the full width.  Depends on the problem only (not on what
-// it is launched with).
+// run at a lower ratio of MMA work to loaded bytes.)  Depends on the problem
+// only (not on what it is launched with).
 int pick_bn(int64_t rows_p, int64_t rows_q, int64_t K, int bn_max)
 {
+    (void)K;
     int bn = 256;
     if (rows_q <= 16) bn = 16;
     else if (rows_q <= 32) bn = 32;
     else if (rows_q <= 64) bn = 64;
     else if (rows_q <= 128) bn = 128;
     const int64_t m_blocks = (rows_p + BM - 1) / BM;
-    if (!splits_k(rows_p, rows_q, K))
-        while (bn > 64 && 2 * m_blocks * ((rows_q + bn - 1) / bn) < sm_count())
-            bn /= 2;
+    while (bn > 64 && 2 * m_blocks * ((rows_q + bn - 1) / bn) < sm_count())
+        bn /= 2;
     return bn < bn_max ? bn : bn_max;
+}
+
+// Tiles of a problem at its pick_bn width.
+int64_t problem_tiles(int64_t rows_p, int64_t rows_q, int64_t K)
+{
+    const int64_t bn = pick_bn(rows_p, rows_q, K, BN_MAX);
+    return ((rows_p + BM - 1) / BM) * ((rows_q + bn - 1) / bn);
+}
+
+// True when a problem is split along K (see split_count): K spans at least
+// 32 k-blocks, its Q side is at most 128 rows and its tiles fill at most
+// half the SMs.  Measured on L2-cold skinny products (single calls, slices
+// added within a cluster): below K = 4096, or with more tiles, the extra
+// pass over the partial sums costs more than the shorter K loop saves.
+bool splits_k(int64_t rows_p, int64_t rows_q, int64_t K)
+{
+    if ((K + BK - 1) / BK < 32 || rows_q > 128 || rows_p <= 0 || rows_q <= 0)
+        return false;
+    return 2 * problem_tiles(rows_p, rows_q, K) <= sm_count();
 }
 
 // One GEMM in the kernel's (P, Q) roles.
@@ -1008,11 +1012,10 @@ int validate(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, con
     return FP8_OK;
 }
 
-// Split-K: k-slices for a skinny problem (Q side <= 64 rows, one column
-// block, so its long side alone sets the tile count) with too few tiles to
-// occupy the GPU: each SM streams operands at a fraction of HBM bandwidth,
-// so more SMs must share the long operand.  Decided from the problem alone
-// (its 128-row tile count, the SM count and K), never from what it is
+// Split-K: k-slices for a skinny problem (Q side <= 128 rows) with too few
+// tiles to occupy the GPU: each SM streams operands at a fraction of HBM
+// bandwidth, so more SMs must share the long operand.  Decided from the
+// problem alone (its tile count, the SM count and K), never from what it is
 // launched with, so a problem sums its K range the same way alone, grouped
 // or under any tile configuration.  Every slice gets at least eight k-blocks
 // (K >= 1024): below that the extra pass over the partials costs more than
@@ -1030,7 +1033,7 @@ int split_count(const Job& j)
     const int sms = sm_count();
     if (!splits_k(j.rows_p, j.rows_q, j.K))
         return 1;
-    const int64_t tiles = (j.rows_p + BM - 1) / BM;            // one column block
+    const int64_t tiles = problem_tiles(j.rows_p, j.rows_q, j.K);
     const int k_blocks = static_cast<int>((j.K + BK - 1) / BK);
     int s = std::min<int64_t>(8, sms / tiles);
     s = std::min(s, k_blocks / 8);
