@@ -133,6 +133,7 @@ struct ProblemScalars {
     int bn;
     int sparse;             // P holds kept codes [rows_p, K/2] + metadata in tmE
     int tma3d;              // tmP / tmQ are 3-D chunk views (one box per operand per stage)
+    int tma_store;          // tmC is a map of C: full output chunks leave through TMA stores
     int m_blocks, n_blocks, k_blocks;
     int splits;             // k-slices per tile (split-K); 1 = none
     int kb_per_split;       // k-blocks per slice
@@ -146,6 +147,7 @@ struct Problem : ProblemScalars {
     CUtensorMap tmP;        // P [rows_p, K] codes, box {128, 128 * MT}
     CUtensorMap tmQ;        // Q [rows_q, K] codes, box {128, bn}
     CUtensorMap tmE;        // sparse only: metadata [rows_p, K/8], box {16, 128 * MT}
+    CUtensorMap tmC;        // C [rows_p, rows_q] (row stride ldc), box {128 bytes, 32 rows}, 128-byte swizzle
 };
 
 template <int MAXP>
@@ -398,10 +400,18 @@ __device__ __forceinline__ void cluster_reduce_store(const ProblemScalars& P, co
 // accumulators, packs them and writes the 128 bytes into the warp's staging
 // buffer (16-byte pieces XOR-swizzled by row: conflict-free on both sides);
 // then 8 lanes per row copy 4 rows x 128 contiguous bytes per instruction.
-template <int ESZ>
+// The staging buffer of a warp is 32 rows x 128 bytes, 1024-aligned, with
+// 16-byte piece k of row r at (k ^ (r & 7)) * 16: the layout of a TMA box
+// {128 bytes, 32 rows} with 128-byte swizzle.  Full-width chunks leave
+// through one TMA store issued by lane 0 (which clips rows and columns
+// outside C); lane 0 waits until that store has read the buffer before the
+// buffer is written again.  A partial last chunk (bn not a multiple of the
+// chunk width) is copied out by the lanes, masked, so no store reaches the
+// next tile's columns.
+template <int ESZ, int LB>       // LB: 16-column TMEM loads in flight per wait (1 or 2)
 __device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P, uint32_t taddr, int row0,
                                                         float fi, int jbase, uint8_t* buf, int lane,
-                                                        ScaleWindows& sw)
+                                                        ScaleWindows& sw, const CUtensorMap* tmC)
 {
     constexpr int CW = 128 / ESZ;                     // columns per chunk
     const int rows_q = P.rows_q;
@@ -411,36 +421,72 @@ __device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P,
         const float s_lo = sw.take(P, jbase, lane);
         const float s_hi = (CW > 32 && c0 + 32 < P.bn) ? sw.take(P, jbase, lane) : 0.0f;
         uint32_t packed[32];
+        // scale + convert 16 columns starting at column c of the chunk
+        auto convert16 = [&](const uint32_t (&r)[16], int q) {
 #pragma unroll
-        for (int q = 0; q < CW; q += 16) {
-            if (q < cw) {
-                uint32_t r[16];
-                tmem_ld_32x32b_x16(taddr + c0 + q, r);
+            for (int t = 0; t < 16; t += 2) {
+                const int c = q + t;                          // compile-time column in chunk
+                const float s0 = __shfl_sync(0xFFFFFFFFu, c < 32 ? s_lo : s_hi, c & 31);
+                const float s1 = __shfl_sync(0xFFFFFFFFu, c + 1 < 32 ? s_lo : s_hi, (c + 1) & 31);
+                const float v0 = __fmul_rn(__fmul_rn(__uint_as_float(r[t]), fi), s0);
+                const float v1 = __fmul_rn(__fmul_rn(__uint_as_float(r[t + 1]), fi), s1);
+                if (ESZ == 2) {
+                    __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                    packed[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+                } else {
+                    packed[c] = __float_as_uint(v0);
+                    packed[c + 1] = __float_as_uint(v1);
+                }
+            }
+        };
+        if constexpr (LB == 2) {
+#pragma unroll
+            for (int q = 0; q < CW; q += 32) {
+                uint32_t ra[16], rb[16];
+                if (q < cw)
+                    tmem_ld_32x32b_x16(taddr + c0 + q, ra);
+                if (q + 16 < cw)
+                    tmem_ld_32x32b_x16(taddr + c0 + q + 16, rb);
                 tmem_ld_wait();
+                if (q < cw)
+                    convert16(ra, q);
+                if (q + 16 < cw)
+                    convert16(rb, q + 16);
+            }
+        } else {
 #pragma unroll
-                for (int t = 0; t < 16; t += 2) {
-                    const int c = q + t;                      // compile-time column in chunk
-                    const float s0 = __shfl_sync(0xFFFFFFFFu, c < 32 ? s_lo : s_hi, c & 31);
-                    const float s1 = __shfl_sync(0xFFFFFFFFu, c + 1 < 32 ? s_lo : s_hi, (c + 1) & 31);
-                    const float v0 = __fmul_rn(__fmul_rn(__uint_as_float(r[t]), fi), s0);
-                    const float v1 = __fmul_rn(__fmul_rn(__uint_as_float(r[t + 1]), fi), s1);
-                    if (ESZ == 2) {
-                        __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                        packed[c / 2] = *reinterpret_cast<uint32_t*>(&h);
-                    } else {
-                        packed[c] = __float_as_uint(v0);
-                        packed[c + 1] = __float_as_uint(v1);
-                    }
+            for (int q = 0; q < CW; q += 16) {
+                if (q < cw) {
+                    uint32_t r[16];
+                    tmem_ld_32x32b_x16(taddr + c0 + q, r);
+                    tmem_ld_wait();
+                    convert16(r, q);
                 }
             }
         }
         const int nck = cw * ESZ / 16;                   // 16-byte pieces per row
+        const bool via_tma = tmC != nullptr && cw == CW;
+        if (tmC != nullptr) {
+            // the previous chunk's store must have read the buffer
+            if (lane == 0)
+                bulk_wait_read_all();
+            __syncwarp();
+        }
         uint8_t* my_row = buf + lane * 128;
 #pragma unroll
         for (int k = 0; k < 8; ++k)
             if (k < nck)
                 *reinterpret_cast<uint4*>(my_row + ((k ^ (lane & 7)) << 4)) =
                     make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+        if (via_tma) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                tma_store_2d(tmC, smem_u32(buf), jbase + c0, row0);
+                bulk_commit();
+            }
+            continue;
+        }
         __syncwarp();
         const int k = lane & 7;
 #pragma unroll
@@ -476,12 +522,13 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * C::kStageBytes);
+    // ring | epilogue staging (1024-aligned, per warp 32 x 128 bytes) | barriers
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * C::kStageBytes + C::kEpiBytes);
     // bar[0..S) full, bar[S..2S) empty, then kAcc tmem_full, kAcc tmem_empty,
     // then drain, split-K "partials written", split-K "verdict ready"
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2 * S + 2 * C::kAcc + 3);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    uint8_t* epi_smem = smem + S * C::kStageBytes + 256;      // epilogue staging, per warp
+    uint8_t* epi_smem = smem + S * C::kStageBytes;            // epilogue staging, per warp
     volatile int* split_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
     const uint32_t smem_base = smem_u32(smem);
@@ -821,10 +868,12 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             if (!P.trans_out && P.vec_store) {
                 uint8_t* buf = epi_smem + (warp - 2) * 32 * 128;
                 const int row0 = i - lane;
+                const CUtensorMap* tmC = P.tma_store ? &prm.prob[tc.p].tmC : nullptr;
+                // (256-row tiles have the smaller register budget: one load per wait)
                 if (P.out_bf16)
-                    epilogue_rows_coalesced<2>(P, taddr, row0, fi, jbase, buf, lane, sw);
+                    epilogue_rows_coalesced<2, MT == 1 ? 2 : 1>(P, taddr, row0, fi, jbase, buf, lane, sw, tmC);
                 else
-                    epilogue_rows_coalesced<4>(P, taddr, row0, fi, jbase, buf, lane, sw);
+                    epilogue_rows_coalesced<4, MT == 1 ? 2 : 1>(P, taddr, row0, fi, jbase, buf, lane, sw, tmC);
             } else {
                 float s_cur = 0.0f;
                 for (int c0 = 0; c0 < P.bn; c0 += 16) {
@@ -839,6 +888,9 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             tc_fence_before();
             mbar_arrive(tempty_bar(acc));
         }
+        // TMA stores issued by this warp are complete before the CTA ends
+        if (lane == 0)
+            bulk_wait_all();
     }
 
     // In warps 0 and 1 only lane 0 ran a role loop: reconverge every warp
@@ -888,6 +940,24 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, in
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Map of an output matrix C [rows, cols] (row stride ld elements of esz
+// bytes): box {128 bytes of a row, 32 rows}, 128-byte swizzle, the layout
+// of the epilogue's per-warp staging buffer.
+bool make_out_map(CUtensorMap* map, void* base, int64_t rows, int64_t cols, int64_t ld, int esz)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return false;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * esz)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
+                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -1087,6 +1157,7 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
     pr.trans_out = j.trans_out;
     const int esz = j.out_bf16 ? 2 : 4;
     pr.vec_store = aligned16(j.C) && ((j.ldc * esz) % 16 == 0);
+    pr.tma_store = pr.vec_store && !pr.trans_out && make_out_map(&pr.tmC, j.C, j.rows_p, j.rows_q, j.ldc, esz);
     pr.bn = bn;
     pr.m_blocks = static_cast<int>((j.rows_p + box_p - 1) / box_p);
     pr.n_blocks = static_cast<int>((j.rows_q + bn - 1) / bn);
