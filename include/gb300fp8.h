@@ -144,12 +144,15 @@ int prune24_decompress(const uint8_t *a_vals, const uint8_t *a_meta, int64_t M, 
  * 1 = bf16 (round to nearest even).
  * Skinny products whose N-side tiles are too few to occupy the GPU (and
  * whose K is at least 4096) are split along K over several CTAs; their FP32
- * partial sums go through a workspace and are added in a fixed order, so
- * results are deterministic and do not depend on how the problem is
- * launched.  The workspace is a buffer kept per stream (allocated with
- * cudaMallocAsync on `stream` at the first split launch, grown the same way,
- * kept for the life of the process; at most 64 streams get one; calls on
- * further streams allocate and free one per call, ordered on `stream`).  A
+ * partial sums are added in a fixed order, so results are deterministic and
+ * do not depend on how the problem is launched.  When the slices of a tile
+ * fit one thread-block cluster (and all clusters can be resident at once)
+ * they add up through distributed shared memory and need no workspace.
+ * Otherwise the partials go through a workspace: a buffer kept per stream
+ * (allocated with cudaMallocAsync on `stream` at the first split launch,
+ * grown the same way, kept for the life of the process; at most 64 streams
+ * get one; calls on further streams allocate and free one per call, ordered
+ * on `stream`).  A
  * call made while `stream` is being captured gives the captured graph a
  * workspace of its own: allocated at capture time outside the capture, freed
  * once the graph and every executable graph made from it are destroyed, so
