@@ -291,3 +291,39 @@ def test_split_k_integers_exact(gb, orc):
     one = np.ones(1, np.float32)
     C = _gemm(gb, A, B, one, 0, one, 0, 1.0, gb.OUT_F32)
     assert np.array_equal(C.astype(np.float64), orc.gemm(A, B, one, 0, one, 0))
+
+
+@pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (512, 1024, 2048)])
+def test_dependent_chain_back_to_back_equals_synchronised(gb, M, N, K):
+    """GEMMs launch with programmatic dependent launch (their setup may
+    overlap the previous kernel) and wait for it before reading operands.
+    A chain whose every step reads the previous step's output - quantise,
+    GEMM, quantise that result, GEMM - enqueued back to back must give
+    bitwise what the same steps give with a device sync after each."""
+    dev = torch.device("cuda")
+    x = torch.from_numpy(workloads.randn_f32((M, K), seed=M + 31)).to(dev)
+    w1 = torch.from_numpy(workloads.randn_f32((N, K), seed=N + 32)).to(dev)
+    w2 = torch.from_numpy(workloads.randn_f32((K, N), seed=K + 33)).to(dev)
+    W1, d1 = gb.fp8_quantize_e4m3(w1, 1)
+    W2, d2 = gb.fp8_quantize_e4m3(w2, 1)
+    torch.cuda.synchronize()
+
+    def chain(sync):
+        q, dq = gb.fp8_quantize_e4m3(x, 1)
+        if sync:
+            torch.cuda.synchronize()
+        h = gb.gemm_fp8_dense(q, W1, dq, 1, d1, 1, 1.0, gb.OUT_F32)
+        if sync:
+            torch.cuda.synchronize()
+        qh, dh = gb.fp8_quantize_e4m3(h, 1)
+        if sync:
+            torch.cuda.synchronize()
+        y = gb.gemm_fp8_dense(qh, W2, dh, 1, d2, 1, 1.0, gb.OUT_F32)
+        torch.cuda.synchronize()
+        return h, y
+
+    h_ref, y_ref = chain(True)
+    for _ in range(3):
+        h, y = chain(False)
+        assert torch.equal(h, h_ref) and torch.equal(y, y_ref)
+    assert gb.fp8_last_device_error() == 0
