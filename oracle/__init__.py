@@ -1,4 +1,4 @@
-"""CPU oracle for the FP8 E4M3 dense / 2:4-sparse GEMM path.
+"""CPU oracle for the FP8 (E4M3 / E5M2) dense / 2:4-sparse GEMM path.
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
 of the benchmark use it; the product library never imports, links or runs it.
@@ -7,8 +7,10 @@ It shares no code with the CUDA path.
 The arithmetic lives in ``oracle.c`` (plain C, FP64 accumulation, OpenMP over
 output rows); this module compiles it with gcc on first use and wraps it with
 numpy arrays.  Each wrapper names the definition it follows (arXiv 2602.10262:
-section 2 "FP8 Matrix Cores" for the E4M3 format and FP8 x FP8 -> wide
-accumulation, section 2 "Structured Sparsity" and section 6 for 2:4 sparsity).
+section 2 "FP8 Matrix Cores" for the E4M3 and E5M2 formats and FP8 x FP8 ->
+wide accumulation, Table 3 for mixed-format operand pairs, section 2
+"Structured Sparsity" and section 6 for 2:4 sparsity).  Format numbers:
+``E4M3 = 0``, ``E5M2 = 1``.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (exhaustive decode, brute-force encode, closed-form
@@ -76,26 +78,32 @@ class Oracle:
         P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         lib.orc_e4m3_decode.restype = ctypes.c_double
         lib.orc_e4m3_decode.argtypes = [ctypes.c_uint8]
-        for name in ("orc_e4m3_encode", "orc_e4m3_encode_bruteforce", "orc_e4m3_encode_search"):
+        lib.orc_e5m2_decode.restype = ctypes.c_double
+        lib.orc_e5m2_decode.argtypes = [ctypes.c_uint8]
+        for name in ("orc_e4m3_encode", "orc_e4m3_encode_bruteforce", "orc_e4m3_encode_search",
+                     "orc_e5m2_encode", "orc_e5m2_encode_bruteforce", "orc_e5m2_encode_search"):
             getattr(lib, name).restype = ctypes.c_uint8
             getattr(lib, name).argtypes = [ctypes.c_float]
-        lib.orc_e4m3_decode_array.argtypes = [P, i64, P]
-        lib.orc_e4m3_encode_array.argtypes = [P, i64, P]
-        lib.orc_check_encoder_range.restype = i64
-        lib.orc_check_encoder_range.argtypes = [ctypes.c_uint64, ctypes.c_uint64,
-                                                ctypes.POINTER(ctypes.c_uint32)]
-        lib.orc_encode_pattern_range.argtypes = [ctypes.c_uint64, ctypes.c_uint64, P]
-        lib.orc_quantize.restype = i32
-        lib.orc_quantize.argtypes = [P, i64, i64, i64, i32, P, i64, P]
+        for f in ("e4m3", "e5m2"):
+            getattr(lib, f"orc_{f}_decode_array").argtypes = [P, i64, P]
+            getattr(lib, f"orc_{f}_encode_array").argtypes = [P, i64, P]
+        for name in ("orc_check_encoder_range", "orc_check_e5m2_encoder_range"):
+            getattr(lib, name).restype = i64
+            getattr(lib, name).argtypes = [ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_uint32)]
+        for name in ("orc_encode_pattern_range", "orc_e5m2_encode_pattern_range"):
+            getattr(lib, name).argtypes = [ctypes.c_uint64, ctypes.c_uint64, P]
+        lib.orc_quantize_fmt.restype = i32
+        lib.orc_quantize_fmt.argtypes = [P, i64, i64, i64, i32, i32, P, i64, P]
         lib.orc_prune24.restype = i32
         lib.orc_prune24.argtypes = [P, i64, i64, i64, P, P]
         lib.orc_decompress24.argtypes = [P, P, i64, i64, P]
         lib.orc_gemm.argtypes = [i64, i64, i64, P, i64, P, i64, P, i32, P, i32,
-                                 ctypes.c_double, P]
+                                 ctypes.c_double, i32, i32, P]
         lib.orc_gemm_sampled.argtypes = [i64, P, i64, P, i64, P, i32, P, i32,
-                                         ctypes.c_double, i64, P, P, P]
+                                         ctypes.c_double, i32, i32, i64, P, P, P]
         lib.orc_gemm_sparse24.argtypes = [i64, i64, i64, P, P, P, i64, P, i32, P, i32,
-                                          ctypes.c_double, P]
+                                          ctypes.c_double, i32, i32, P]
         lib.orc_max_threads.restype = i32
         lib.orc_set_threads.argtypes = [i32]
         self.lib = lib
@@ -137,10 +145,48 @@ class Oracle:
         self.lib.orc_encode_pattern_range(lo, hi, _ptr(out))
         return out
 
+    # --- E5M2 codec (OCP E5M2; paper section 2 "bf8") --------------------------
+
+    def e5m2_decode(self, codes) -> np.ndarray:
+        """Decode E5M2 codes to float64 by the OCP bit layout (inf and NaN
+        codes decode to inf and NaN)."""
+        c = _c(codes, np.uint8)
+        out = np.empty(c.shape, np.float64)
+        self.lib.orc_e5m2_decode_array(_ptr(c), c.size, _ptr(out))
+        return out
+
+    def e5m2_encode(self, x) -> np.ndarray:
+        """fp32 -> E5M2 code, round to nearest even, saturating to +-57344."""
+        a = _c(x, np.float32)
+        out = np.empty(a.shape, np.uint8)
+        self.lib.orc_e5m2_encode_array(_ptr(a), a.size, _ptr(out))
+        return out
+
+    def e5m2_encode_bruteforce(self, x: float) -> int:
+        return int(self.lib.orc_e5m2_encode_bruteforce(ctypes.c_float(x)))
+
+    def e5m2_encode_search(self, x: float) -> int:
+        return int(self.lib.orc_e5m2_encode_search(ctypes.c_float(x)))
+
+    def check_e5m2_encoder_range(self, lo: int, hi: int):
+        first = ctypes.c_uint32(0)
+        bad = self.lib.orc_check_e5m2_encoder_range(lo, hi, ctypes.byref(first))
+        return int(bad), int(first.value)
+
+    def e5m2_encode_pattern_range(self, lo: int, hi: int) -> np.ndarray:
+        out = np.empty(hi - lo, np.uint8)
+        self.lib.orc_e5m2_encode_pattern_range(lo, hi, _ptr(out))
+        return out
+
+    def decode(self, codes, fmt: int) -> np.ndarray:
+        """Decode codes of format fmt (0: E4M3, 1: E5M2)."""
+        return self.e5m2_decode(codes) if fmt == 1 else self.e4m3_decode(codes)
+
     # --- quantisation ---------------------------------------------------------
 
-    def quantize(self, x, mode: int):
-        """Scale selection + encode.  mode 0 = per tensor, 1 = per row.
+    def quantize(self, x, mode: int, fmt: int = 0):
+        """Scale selection + encode.  mode 0 = per tensor, 1 = per row; fmt 0 =
+        E4M3 (amax -> 448), 1 = E5M2 (amax -> 57344).
         Returns (codes uint8 [R, C], dequant scales float32 [1] or [R])."""
         a = _c(x, np.float32)
         if a.ndim != 2:
@@ -148,7 +194,10 @@ class Oracle:
         R, C = a.shape
         q = np.empty((R, C), np.uint8)
         d = np.empty(1 if mode == 0 else R, np.float32)
-        rc = self.lib.orc_quantize(_ptr(a), R, C, C, int(mode), _ptr(q), C, _ptr(d))
+        if fmt not in (0, 1):
+            raise OracleError("fmt must be 0 (E4M3) or 1 (E5M2)")
+        rc = self.lib.orc_quantize_fmt(_ptr(a), R, C, C, int(mode), int(fmt), _ptr(q), C,
+                                       _ptr(d))
         if rc == -4:
             raise OracleError("non-finite input")
         return q, d
@@ -176,9 +225,9 @@ class Oracle:
 
     # --- GEMM ---------------------------------------------------------------
 
-    def gemm(self, A, B, dA, a_mode, dB, b_mode, alpha=1.0) -> np.ndarray:
-        """C = alpha * dA[m] * dB[n] * sum_k dec(A[m,k]) dec(B[n,k]) in FP64.
-        A: codes [M, K]; B: codes [N, K]."""
+    def gemm(self, A, B, dA, a_mode, dB, b_mode, alpha=1.0, a_fmt=0, b_fmt=0) -> np.ndarray:
+        """C = alpha * dA[m] * dB[n] * sum_k decA(A[m,k]) decB(B[n,k]) in FP64.
+        A: codes [M, K] of format a_fmt; B: codes [N, K] of format b_fmt."""
         A = _c(A, np.uint8)
         B = _c(B, np.uint8)
         M, K = A.shape
@@ -188,10 +237,11 @@ class Oracle:
         sa, sb = _scales(dA, M, a_mode), _scales(dB, N, b_mode)
         C = np.empty((M, N), np.float64)
         self.lib.orc_gemm(M, N, K, _ptr(A), K, _ptr(B), K, _ptr(sa), int(a_mode),
-                          _ptr(sb), int(b_mode), float(alpha), _ptr(C))
+                          _ptr(sb), int(b_mode), float(alpha), int(a_fmt), int(b_fmt), _ptr(C))
         return C
 
-    def gemm_sampled(self, A, B, dA, a_mode, dB, b_mode, alpha, ms, ns) -> np.ndarray:
+    def gemm_sampled(self, A, B, dA, a_mode, dB, b_mode, alpha, ms, ns, a_fmt=0,
+                     b_fmt=0) -> np.ndarray:
         """The GEMM definition at the (ms[i], ns[i]) entries only."""
         A = _c(A, np.uint8)
         B = _c(B, np.uint8)
@@ -204,11 +254,13 @@ class Oracle:
         sa, sb = _scales(dA, M, a_mode), _scales(dB, N, b_mode)
         out = np.empty(ms.size, np.float64)
         self.lib.orc_gemm_sampled(K, _ptr(A), K, _ptr(B), K, _ptr(sa), int(a_mode),
-                                  _ptr(sb), int(b_mode), float(alpha), ms.size,
+                                  _ptr(sb), int(b_mode), float(alpha), int(a_fmt), int(b_fmt),
+                                  ms.size,
                                   _ptr(ms), _ptr(ns), _ptr(out))
         return out
 
-    def gemm_sparse24(self, vals, meta, B, K, dA, a_mode, dB, b_mode, alpha=1.0):
+    def gemm_sparse24(self, vals, meta, B, K, dA, a_mode, dB, b_mode, alpha=1.0, a_fmt=0,
+                      b_fmt=0):
         """Sparse GEMM = dense GEMM of the decompressed pruned A."""
         v = _c(vals, np.uint8)
         m = _c(meta, np.uint8)
@@ -217,7 +269,8 @@ class Oracle:
         sa, sb = _scales(dA, M, a_mode), _scales(dB, N, b_mode)
         C = np.empty((M, N), np.float64)
         self.lib.orc_gemm_sparse24(M, N, K, _ptr(v), _ptr(m), _ptr(B), K, _ptr(sa),
-                                   int(a_mode), _ptr(sb), int(b_mode), float(alpha), _ptr(C))
+                                   int(a_mode), _ptr(sb), int(b_mode), float(alpha), int(a_fmt),
+                                   int(b_fmt), _ptr(C))
         return C
 
     def max_threads(self) -> int:

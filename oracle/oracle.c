@@ -1,5 +1,5 @@
 /*
- * CPU oracle for the FP8 (E4M3) GEMM path: plain, slow, obviously correct.
+ * CPU oracle for the FP8 (E4M3 / E5M2) GEMM path: plain, slow, obviously correct.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
  * loads this file; only the tests, the smoke check and the CPU-baseline leg of
@@ -14,13 +14,17 @@
  *     paper gives no bit layout; the OCP E4M3 definition is used: 1 sign bit,
  *     4 exponent bits (bias 7), 3 mantissa bits, no infinities, S.1111.111 is
  *     NaN, largest finite 448.
+ *   - E5M2 decode / encode: the other OCP variant the paper lists ("bf8",
+ *     section 2; mixed E4M3 x E5M2 operands in Table 3): 1 sign bit, 5
+ *     exponent bits (bias 15), 2 mantissa bits, infinities and NaNs as in
+ *     IEEE-754, largest finite 57344.
  *   - Quantisation: per-tensor or per-row amax scaling so that amax maps to
- *     448, one fp32 multiply, round-to-nearest-even with saturation to the
- *     finite range.
+ *     the format's largest finite value (448 or 57344), one fp32 multiply,
+ *     round-to-nearest-even with saturation to the finite range.
  *   - 2:4 structured sparsity (section 2 "Structured Sparsity" and section 6):
  *     in every group of four consecutive elements along K two are zero; the
  *     pruning keeps the two largest magnitudes.
- *   - GEMM: C = alpha * dA[m] * dB[n] * sum_k dec(A[m,k]) * dec(B[n,k]),
+ *   - GEMM: C = alpha * dA[m] * dB[n] * sum_k decA(A[m,k]) * decB(B[n,k]),
  *     FP8 x FP8 products accumulated (here in FP64), as the FP8 matrix-core
  *     operation of section 4 (FP8 x FP8 operands, wide accumulation).
  *
@@ -228,21 +232,204 @@ void orc_encode_pattern_range(uint64_t lo, uint64_t hi, uint8_t *out)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Quantisation (scale selection + E4M3 encode).                            */
+/* E5M2 decode / encode (OCP FP8, E5M2 variant; paper section 2 lists both  */
+/* FP8 variants, E5M2 ("bf8") beside E4M3 ("fp8"), as MFMA operand types).  */
+/* ------------------------------------------------------------------------ */
+
+/* Value of code c.  s = bit 7, e = bits 6..2, m = bits 1..0 (bias 15, the
+ * IEEE-754 binary16 layout with the low eight mantissa bits dropped).
+ *   e == 31, m == 0          -> (-1)^s * inf
+ *   e == 31, m != 0          -> NaN (codes 0x7D..0x7F, 0xFD..0xFF)
+ *   e == 0                   -> (-1)^s * m * 2^-16            (subnormal)
+ *   otherwise                -> (-1)^s * (1 + m/4) * 2^(e-15)
+ * Largest finite magnitude: (1 + 3/4) * 2^15 = 57344 (code 0x7B).         */
+double orc_e5m2_decode(uint8_t c)
+{
+    int s = (c >> 7) & 1;
+    int e = (c >> 2) & 31;
+    int m = c & 3;
+    double v;
+    if (e == 31)
+        v = (m == 0) ? INFINITY : NAN;
+    else if (e == 0)
+        v = ldexp((double)m, -16);
+    else
+        v = ldexp(1.0 + (double)m / 4.0, e - 15);
+    if (isnan(v))
+        return v;
+    return s ? -v : v;
+}
+
+/* Arithmetic encoder, round to nearest, ties to even, saturating.  Readings
+ * where the paper is silent (the same as for E4M3):
+ *   - finite overflow and +-inf saturate to +-57344 ("satfinite"), so no
+ *     quantised operand is ever infinite;
+ *   - NaN -> 0x7F with the input's sign bit;
+ *   - ties go to the even code; the code sequence is continuous across the
+ *     subnormal/normal and binade edges, so "even mantissa" = "even code";
+ *   - the sign is kept for results that round to zero.                     */
+uint8_t orc_e5m2_encode(float xf)
+{
+    uint8_t sign = signbit(xf) ? 0x80 : 0x00;
+    double a = fabs((double)xf);
+    if (isnan(xf))
+        return (uint8_t)(sign | 0x7F);
+    if (a >= 57344.0)                     /* includes +-inf */
+        return (uint8_t)(sign | 0x7B);
+    if (a < ldexp(1.0, -14)) {
+        /* subnormal range: quantum 2^-16, code = number of quanta (0..4);
+         * 4 quanta is 2^-14, whose code 0x04 is the first normal code.      */
+        double q = rne_int(a / ldexp(1.0, -16));
+        return (uint8_t)(sign | (uint8_t)q);
+    }
+    int e;
+    frexp(a, &e);                         /* a = f * 2^e, f in [0.5, 1)      */
+    e -= 1;                               /* a in [2^e, 2^(e+1))             */
+    double q = rne_int(a / ldexp(1.0, e - 2));   /* in [4, 8]                */
+    if (q == 8.0) {                       /* carried into the next binade    */
+        q = 4.0;
+        e += 1;
+    }
+    if (e + 15 > 30)
+        return (uint8_t)(sign | 0x7B);    /* cannot happen below 57344       */
+    return (uint8_t)(sign | (uint8_t)(((e + 15) << 2) | (int)(q - 4.0)));
+}
+
+void orc_e5m2_decode_array(const uint8_t *c, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = orc_e5m2_decode(c[i]);
+}
+
+void orc_e5m2_encode_array(const float *x, int64_t n, uint8_t *q)
+{
+    for (int64_t i = 0; i < n; ++i)
+        q[i] = orc_e5m2_encode(x[i]);
+}
+
+/* Brute force from "nearest finite value, ties to the even code": a scan of
+ * the finite codes of the input's sign.  Where two codes are nearly equally
+ * near, x lies between them within a factor of two of the larger, so both
+ * differences are exact in double (fp32 x: 24 significant bits; codes:
+ * multiples of 2^-16 with 3 significant bits); farther codes may round but
+ * rounding is monotone and cannot move them ahead.  Beyond 2^17 every finite
+ * code lies below x and the largest is the nearest.                       */
+uint8_t orc_e5m2_encode_bruteforce(float xf)
+{
+    uint8_t sign = signbit(xf) ? 0x80 : 0x00;
+    if (isnan(xf))
+        return (uint8_t)(sign | 0x7F);
+    if (isinf(xf) || fabs((double)xf) > 131072.0)
+        return (uint8_t)(sign | 0x7B);
+    double x = (double)xf;
+    int best = -1;
+    double bestd = INFINITY;
+    for (int c = 0; c <= 0x7B; ++c) {
+        uint8_t code = (uint8_t)(sign | c);
+        double d = fabs(x - orc_e5m2_decode(code));
+        if (d < bestd || (d == bestd && (code & 1) == 0 && (best & 1) == 1)) {
+            bestd = d;
+            best = code;
+        }
+    }
+    return (uint8_t)best;
+}
+
+/* The same definition located by bisection over the monotone positive finite
+ * codes 0x00..0x7B; used for the exhaustive fp32 sweep.                   */
+uint8_t orc_e5m2_encode_search(float xf)
+{
+    uint8_t sign = signbit(xf) ? 0x80 : 0x00;
+    if (isnan(xf))
+        return (uint8_t)(sign | 0x7F);
+    double a = fabs((double)xf);
+    if (isinf(xf) || a >= 57344.0)
+        return (uint8_t)(sign | 0x7B);
+    int lo = 0, hi = 0x7B;                /* largest c with dec(c) <= a */
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (orc_e5m2_decode((uint8_t)mid) <= a)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    int c = lo;
+    if (c == 0x7B)
+        return (uint8_t)(sign | c);
+    double dl = a - orc_e5m2_decode((uint8_t)c);
+    double du = orc_e5m2_decode((uint8_t)(c + 1)) - a;
+    int pick;
+    if (dl < du)
+        pick = c;
+    else if (du < dl)
+        pick = c + 1;
+    else
+        pick = (c % 2 == 0) ? c : c + 1;
+    return (uint8_t)(sign | pick);
+}
+
+/* Format-generic front ends.  fmt 0: E4M3, fmt 1: E5M2.                   */
+double orc_fp8_decode(int fmt, uint8_t c)
+{
+    return fmt == 1 ? orc_e5m2_decode(c) : orc_e4m3_decode(c);
+}
+
+uint8_t orc_fp8_encode(int fmt, float x)
+{
+    return fmt == 1 ? orc_e5m2_encode(x) : orc_e4m3_encode(x);
+}
+
+/* Exhaustive arithmetic-vs-search comparison for E5M2 over fp32 patterns
+ * [lo, hi); returns mismatches, *first_bad the first (or 0xFFFFFFFF).     */
+int64_t orc_check_e5m2_encoder_range(uint64_t lo, uint64_t hi, uint32_t *first_bad)
+{
+    int64_t bad = 0;
+    uint32_t first = 0xFFFFFFFFu;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t i = (int64_t)lo; i < (int64_t)hi; ++i) {
+        uint32_t u = (uint32_t)i;
+        float x;
+        memcpy(&x, &u, 4);
+        if (orc_e5m2_encode(x) != orc_e5m2_encode_search(x)) {
+            bad += 1;
+#pragma omp critical
+            if (u < first)
+                first = u;
+        }
+    }
+    *first_bad = first;
+    return bad;
+}
+
+/* E5M2 codes of every fp32 bit pattern in [lo, hi).                       */
+void orc_e5m2_encode_pattern_range(uint64_t lo, uint64_t hi, uint8_t *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = (int64_t)lo; i < (int64_t)hi; ++i) {
+        uint32_t u = (uint32_t)i;
+        float x;
+        memcpy(&x, &u, 4);
+        out[i - (int64_t)lo] = orc_e5m2_encode(x);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quantisation (scale selection + E4M3 / E5M2 encode).                     */
 /* ------------------------------------------------------------------------ */
 
 /* x: fp32 [rows, cols] with row stride ld (elements).  mode 0: one scale for
- * the tensor; mode 1: one scale per row.  For each scaling group:
+ * the tensor; mode 1: one scale per row.  fmt 0: E4M3, whose largest finite
+ * value T is 448; fmt 1: E5M2, T = 57344.  For each scaling group:
  *   amax = max |x|                                   (exact)
- *   s    = fl32(448 / amax),  d = fl32(amax / 448)   (one IEEE fp32 division
+ *   s    = fl32(T / amax),  d = fl32(amax / T)       (one IEEE fp32 division
  *                                                     each; amax == 0 gives
  *                                                     s = d = 1)
  *   q    = enc(fl32(x * s))                          (one fp32 multiply)
  * d (the dequantisation factor) is written to d[0] (mode 0) or d[r].
  * q has row stride ldq bytes.  Returns 0, or -4 if any input is not finite
  * (outputs are then unspecified).                                        */
-int orc_quantize(const float *x, int64_t rows, int64_t cols, int64_t ld,
-                 int mode, uint8_t *q, int64_t ldq, float *d)
+int orc_quantize_fmt(const float *x, int64_t rows, int64_t cols, int64_t ld,
+                     int mode, int fmt, uint8_t *q, int64_t ldq, float *d)
 {
     int64_t groups = (mode == 0) ? 1 : rows;
     for (int64_t g = 0; g < groups; ++g) {
@@ -264,6 +451,8 @@ int orc_quantize(const float *x, int64_t rows, int64_t cols, int64_t ld,
             dq = 1.0f;
         } else {
             volatile float num = 448.0f;   /* keep both divisions in fp32 */
+            if (fmt == 1)
+                num = 57344.0f;
             s = num / amax;
             dq = amax / num;
         }
@@ -271,10 +460,17 @@ int orc_quantize(const float *x, int64_t rows, int64_t cols, int64_t ld,
         for (int64_t r = r0; r < r1; ++r)
             for (int64_t c = 0; c < cols; ++c) {
                 volatile float y = x[r * ld + c] * s;
-                q[r * ldq + c] = orc_e4m3_encode(y);
+                q[r * ldq + c] = orc_fp8_encode(fmt, y);
             }
     }
     return 0;
+}
+
+/* E4M3 quantisation: orc_quantize_fmt with fmt 0. */
+int orc_quantize(const float *x, int64_t rows, int64_t cols, int64_t ld,
+                 int mode, uint8_t *q, int64_t ldq, float *d)
+{
+    return orc_quantize_fmt(x, rows, cols, ld, mode, 0, q, ldq, d);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -284,7 +480,8 @@ int orc_quantize(const float *x, int64_t rows, int64_t cols, int64_t ld,
 
 /* a: codes [M, K], row stride lda.  K % 4 == 0.
  * For row m and group g (elements 4g..4g+3):
- *   key(c) = c & 0x7F (monotone in |value| over the finite codes);
+ *   key(c) = c & 0x7F (monotone in |value| over the finite codes of either
+ *            FP8 variant, so the same pruning serves E4M3 and E5M2);
  *   the kept pair is the first two positions when the four are ordered by
  *   key descending, then index ascending (ties keep the lower index);
  *   vals[m, 2g], vals[m, 2g+1] = the kept codes in increasing index order;
@@ -338,30 +535,35 @@ void orc_decompress24(const uint8_t *vals, const uint8_t *meta, int64_t M,
 }
 
 /* ------------------------------------------------------------------------ */
-/* GEMM: C[m,n] = alpha * dA[m] * dB[n] * sum_k dec(A[m,k]) * dec(B[n,k])    */
+/* GEMM: C[m,n] = alpha * dA[m] * dB[n] * sum_k decA(A[m,k]) * decB(B[n,k])  */
 /* A: codes [M, K] (row stride lda), B: codes [N, K] (row stride ldb), both */
-/* K-contiguous.  a_mode/b_mode 0: one scale dA[0] / dB[0]; 1: per row of   */
-/* the stored matrix (dA[m], dB[n]).  FP64 everywhere; C is [M, N] doubles. */
+/* K-contiguous; a_fmt / b_fmt pick each operand's FP8 variant (0: E4M3,    */
+/* 1: E5M2; paper section 2 and Table 3: the FP8 matrix cores take either   */
+/* variant for each operand).  a_mode/b_mode 0: one scale dA[0] / dB[0];    */
+/* 1: per row of the stored matrix (dA[m], dB[n]).  FP64 everywhere; C is   */
+/* [M, N] doubles.                                                          */
 /* ------------------------------------------------------------------------ */
 
-static double dot_codes(const uint8_t *a, const uint8_t *b, int64_t K)
+static double dot_codes(const uint8_t *a, int fa, const uint8_t *b, int fb, int64_t K)
 {
     double s = 0.0;
     for (int64_t k = 0; k < K; ++k)
-        s += orc_e4m3_decode(a[k]) * orc_e4m3_decode(b[k]);
+        s += orc_fp8_decode(fa, a[k]) * orc_fp8_decode(fb, b[k]);
     return s;
 }
 
 void orc_gemm(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
               const uint8_t *B, int64_t ldb, const float *dA, int a_mode,
-              const float *dB, int b_mode, double alpha, double *C)
+              const float *dB, int b_mode, double alpha, int a_fmt, int b_fmt,
+              double *C)
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t m = 0; m < M; ++m)
         for (int64_t n = 0; n < N; ++n) {
             double sa = (double)dA[a_mode ? m : 0];
             double sb = (double)dB[b_mode ? n : 0];
-            C[m * N + n] = alpha * sa * sb * dot_codes(A + m * lda, B + n * ldb, K);
+            C[m * N + n] = alpha * sa * sb *
+                           dot_codes(A + m * lda, a_fmt, B + n * ldb, b_fmt, K);
         }
 }
 
@@ -371,30 +573,30 @@ void orc_gemm(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
 void orc_gemm_sampled(int64_t K, const uint8_t *A, int64_t lda,
                       const uint8_t *B, int64_t ldb, const float *dA,
                       int a_mode, const float *dB, int b_mode, double alpha,
-                      int64_t n_samples, const int64_t *ms, const int64_t *ns,
-                      double *out)
+                      int a_fmt, int b_fmt, int64_t n_samples, const int64_t *ms,
+                      const int64_t *ns, double *out)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n_samples; ++i) {
         int64_t m = ms[i], n = ns[i];
         double sa = (double)dA[a_mode ? m : 0];
         double sb = (double)dB[b_mode ? n : 0];
-        out[i] = alpha * sa * sb * dot_codes(A + m * lda, B + n * ldb, K);
+        out[i] = alpha * sa * sb * dot_codes(A + m * lda, a_fmt, B + n * ldb, b_fmt, K);
     }
 }
 
 /* Sparse GEMM: the dense definition applied to the decompressed pruned A
  * (paper section 6 compares sparse GEMM against dense GEMM on the same
  * operands; the sparse product equals the dense product of the zero-filled
- * matrix).                                                                */
+ * matrix).  Code 0x00 is +0 in both FP8 variants.                         */
 void orc_gemm_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t *vals,
                        const uint8_t *meta, const uint8_t *B, int64_t ldb,
                        const float *dA, int a_mode, const float *dB,
-                       int b_mode, double alpha, double *C)
+                       int b_mode, double alpha, int a_fmt, int b_fmt, double *C)
 {
     uint8_t *a = (uint8_t *)malloc((size_t)(M * K));
     orc_decompress24(vals, meta, M, K, a);
-    orc_gemm(M, N, K, a, K, B, ldb, dA, a_mode, dB, b_mode, alpha, C);
+    orc_gemm(M, N, K, a, K, B, ldb, dA, a_mode, dB, b_mode, alpha, a_fmt, b_fmt, C);
     free(a);
 }
 

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_codec as tc
+from tests import test_oracle_e5m2 as t5
 from tests import test_oracle_gemm as tg
 from tests import test_oracle_prune as tp
 from tests import test_oracle_quant as tq
@@ -38,8 +39,9 @@ MUTANTS = {
                              "uint8_t nib = (uint8_t)(i1 | (i0 << 2));"),
     "prune_nibble_high_first": ("meta[m * ldm + g / 2] |= (uint8_t)(nib << (4 * (g % 2)));",
                                 "meta[m * ldm + g / 2] |= (uint8_t)(nib << (4 * (1 - g % 2)));"),
-    "gemm_sign": ("s += orc_e4m3_decode(a[k]) * orc_e4m3_decode(b[k]);",
-                  "s -= orc_e4m3_decode(a[k]) * orc_e4m3_decode(b[k]);"),
+    "gemm_sign": ("s += orc_fp8_decode(fa, a[k]) * orc_fp8_decode(fb, b[k]);",
+                  "s -= orc_fp8_decode(fa, a[k]) * orc_fp8_decode(fb, b[k]);"),
+    "gemm_b_format_from_a": ("orc_fp8_decode(fb, b[k])", "orc_fp8_decode(fa, b[k])"),
     "gemm_short_k": ("for (int64_t k = 0; k < K; ++k)\n        s +=",
                      "for (int64_t k = 1; k < K; ++k)\n        s +="),
     "gemm_alpha_dropped": ("C[m * N + n] = alpha * sa * sb *", "C[m * N + n] = sa * sb *"),
@@ -49,8 +51,27 @@ MUTANTS = {
                          "            double sa = (double)dA[a_mode ? m : 0];\n"
                          "            double sb = (double)dB[b_mode ? m % 1 : 0];\n"
                          "            C[m * N + n]"),
-    "gemm_b_row_stride": ("dot_codes(A + m * lda, B + n * ldb, K);\n        }\n}",
-                          "dot_codes(A + m * lda, B + n, K);\n        }\n}"),
+    "gemm_b_row_stride": ("dot_codes(A + m * lda, a_fmt, B + n * ldb, b_fmt, K);\n        }\n}",
+                          "dot_codes(A + m * lda, a_fmt, B + n, b_fmt, K);\n        }\n}"),
+    "e5m2_decode_bias_16": ("ldexp(1.0 + (double)m / 4.0, e - 15)", "ldexp(1.0 + (double)m / 4.0, e - 16)"),
+    "e5m2_decode_subnormal_scale": ("v = ldexp((double)m, -16);", "v = ldexp((double)m, -15);"),
+    "e5m2_decode_inf_as_nan": ("v = (m == 0) ? INFINITY : NAN;", "v = NAN;"),
+    "e5m2_encode_saturates_to_inf": ("    if (a >= 57344.0)                     /* includes +-inf */\n"
+                                     "        return (uint8_t)(sign | 0x7B);",
+                                     "    if (a >= 57344.0)                     /* includes +-inf */\n"
+                                     "        return (uint8_t)(sign | 0x7C);"),
+    "e5m2_encode_binade_off_by_one": ("double q = rne_int(a / ldexp(1.0, e - 2));   /* in [4, 8]",
+                                      "double q = rne_int(a / ldexp(1.0, e - 3));   /* in [4, 8]"),
+    "e5m2_encode_subnormal_edge": ("if (a < ldexp(1.0, -14)) {", "if (a < ldexp(1.0, -15)) {"),
+    "e5m2_encode_carry_dropped": ("    if (q == 8.0) {                       /* carried into the next binade    */\n"
+                                  "        q = 4.0;\n        e += 1;\n    }",
+                                  "    if (q == 8.0) {                       /* carried into the next binade    */\n"
+                                  "        q = 7.0;\n    }"),
+    "fp8_decode_dispatch": ("return fmt == 1 ? orc_e5m2_decode(c) : orc_e4m3_decode(c);",
+                            "return fmt == 0 ? orc_e5m2_decode(c) : orc_e4m3_decode(c);"),
+    "fp8_encode_dispatch": ("return fmt == 1 ? orc_e5m2_encode(x) : orc_e4m3_encode(x);",
+                            "return orc_e4m3_encode(x);"),
+    "quant_e5m2_target": ("                num = 57344.0f;", "                num = 65536.0f;"),
     "decompress_swapped": ("out[m * K + 4 * g + i0] = vals[m * ldv + 2 * g];",
                            "out[m * K + 4 * g + i1] = vals[m * ldv + 2 * g];"),
 }
@@ -78,6 +99,18 @@ def _pins(orc):
         lambda: tg.test_small_integers_exact(orc),
         lambda: tg.test_identity(orc),
         lambda: tg.test_sparse_equals_dense_on_pruned(orc),
+        lambda: t5.test_decode_all_256_codes_vs_torch(orc),
+        lambda: t5.test_decode_landmarks(orc),
+        lambda: t5.test_encode_landmarks_roundtrip(orc),
+        lambda: t5.test_encode_vs_torch_in_range(orc),
+        lambda: t5.test_encode_every_binary16_by_integer_rounding(orc),
+        lambda: t5.test_encode_saturates(orc),
+        lambda: t5.test_quantize_closed_form(orc),
+        lambda: t5.test_quantize_matches_torch_restatement(orc, 1, (64, 256)),
+        lambda: t5.test_gemm_formats_vs_numpy(orc, 0, 1, 17, 9, 64, 1, 1),
+        lambda: t5.test_gemm_formats_vs_numpy(orc, 1, 0, 3, 5, 7, 0, 0),
+        lambda: t5.test_gemm_small_integers_exact_every_pairing(orc),
+        lambda: t5.test_gemm_format_is_per_operand(orc),
     ]
 
 

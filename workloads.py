@@ -31,20 +31,28 @@ def randint_f32(shape, seed: int, lo: int, hi: int) -> np.ndarray:
     return torch.randint(lo, hi + 1, tuple(shape), generator=g).to(torch.float32).numpy()
 
 
-def small_int_codes(shape, seed: int, maxabs: int = 4) -> np.ndarray:
-    """E4M3 codes of integers uniform in [-maxabs, maxabs].
+def small_int_codes(shape, seed: int, maxabs: int = 4, fmt: int = 0) -> np.ndarray:
+    """FP8 codes (fmt 0: E4M3, 1: E5M2) of integers uniform in [-maxabs, maxabs].
 
-    The codes come from PyTorch's own float8_e4m3fn cast (exact for small
-    integers), so neither the oracle nor the CUDA path produces them.  With
-    such inputs every partial sum of a GEMM is an integer far below 2^24, so
-    an FP32-accumulated product is exact."""
+    The codes come from PyTorch's own float8_e4m3fn / float8_e5m2 cast (exact
+    for integers up to 8 in both), so neither the oracle nor the CUDA path
+    produces them.  With such inputs every partial sum of a GEMM is an integer
+    far below 2^24, so an FP32-accumulated product is exact."""
+    if fmt == 1 and maxabs > 8:
+        raise ValueError("E5M2 holds the integers up to 8 exactly")
     v = torch.from_numpy(randint_f32(shape, seed, -maxabs, maxabs))
-    return v.to(torch.float8_e4m3fn).view(torch.uint8).numpy().copy()
+    dt = torch.float8_e5m2 if fmt == 1 else torch.float8_e4m3fn
+    return v.to(dt).view(torch.uint8).numpy().copy()
 
 
-def random_codes(shape, seed: int) -> np.ndarray:
-    """Uniform random finite E4M3 codes (every byte except 0x7F and 0xFF)."""
+def random_codes(shape, seed: int, fmt: int = 0) -> np.ndarray:
+    """Uniform random finite FP8 codes.  fmt 0 (E4M3): every byte except 0x7F
+    and 0xFF; fmt 1 (E5M2): every byte except 0x7C..0x7F and 0xFC..0xFF."""
     g = torch.Generator().manual_seed(int(seed))
+    if fmt == 1:
+        c = torch.randint(0, 248, tuple(shape), generator=g, dtype=torch.int32)
+        c = torch.where(c >= 124, c + 4, c)       # skip 0x7C..0x7F
+        return c.to(torch.uint8).numpy().copy()
     c = torch.randint(0, 254, tuple(shape), generator=g, dtype=torch.int32)
     c = torch.where(c >= 0x7F, c + 1, c)          # skip 0x7F
     return c.to(torch.uint8).numpy().copy()
