@@ -441,13 +441,55 @@ def _time_ms(fn, target_s=0.15, warmup=3, reps=10, capture=True):
     return ms
 
 
-def _operands(gb, M, N, K, dev, seed):
+def _operands(gb, M, N, K, dev, seed, a_fmt=0, b_fmt=0):
     g = torch.Generator(device=dev).manual_seed(seed)
     x = torch.randn((M, K), generator=g, device=dev)
     w = torch.randn((N, K), generator=g, device=dev)
-    A, dA = gb.fp8_quantize_e4m3(x, 1)
-    B, dB = gb.fp8_quantize_e4m3(w, 1)
+    quant = {0: gb.fp8_quantize_e4m3, 1: gb.fp8_quantize_e5m2}
+    A, dA = quant[a_fmt](x, 1)
+    B, dB = quant[b_fmt](w, 1)
     return x, w, A, dA, B, dB
+
+
+FORMAT_NAMES = {0: "e4m3", 1: "e5m2"}
+
+
+def format_sweep(gb, dev):
+    """The four operand-format pairings (E4M3 / E5M2 for each operand, paper
+    Table 3) on the same dense shapes, plus the quantisation rate of each
+    format.  Operands rotate through copies as in the shape sweep."""
+    rows = []
+    for (M, N, K) in [(8192, 8192, 8192), (16384, 16384, 16384),
+                      (16, workloads.SKINNY_NK, workloads.SKINNY_NK)]:
+        for af in (0, 1):
+            for bf in (0, 1):
+                x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 5 * M + N, af, bf)
+                del x, w
+                n8 = _l2_copies(dev, M * K + N * K + 2 * M * N)
+                sets = [(A, B, torch.empty((M, N), dtype=torch.bfloat16, device=dev))] + \
+                       [(A.clone(), B.clone(), torch.empty((M, N), dtype=torch.bfloat16, device=dev))
+                        for _ in range(n8 - 1)]
+                ms = _time_ms([lambda a=a, b=b, c=c: gb.gemm_fp8_dense_fmt(
+                    a, b, dA, 1, dB, 1, 1.0, gb.OUT_BF16, af, bf, C=c) for a, b, c in sets])
+                del sets, A, B
+                torch.cuda.empty_cache()
+                rows.append({"M": M, "N": N, "K": K, "a_format": FORMAT_NAMES[af],
+                             "b_format": FORMAT_NAMES[bf], "ms": ms,
+                             "tflops": 2.0 * M * N * K / ms / 1e9, "operand_copies": n8})
+    quant = []
+    R = C = 8192
+    x = torch.randn((R, C), device=dev)
+    for fmt, fn in ((0, gb.fp8_quantize_e4m3), (1, gb.fp8_quantize_e5m2)):
+        for mode in (0, 1):
+            q = torch.empty((R, C), dtype=torch.uint8, device=dev)
+            d = torch.empty((R if mode else 1,), dtype=torch.float32, device=dev)
+            n = _l2_copies(dev, R * C * 5)
+            xs = [x] + [x.clone() for _ in range(n - 1)]
+            ms = _time_ms([lambda xx=xx: fn(xx, mode, q, d) for xx in xs])
+            quant.append({"format": FORMAT_NAMES[fmt], "scale_mode": mode, "rows": R, "cols": C,
+                          "us": ms * 1e3, "gbs": R * C * 5 / ms / 1e6, "input_copies": n})
+            del xs
+    return {"dense": rows, "quantize": quant}
 
 
 def sweep(gb, dev):
@@ -551,6 +593,7 @@ def sweep(gb, dev):
         "speedup_vs_bf16_per_call": ms_bf16 / ms_graph}
     del keep
     torch.cuda.empty_cache()
+    out["formats"] = format_sweep(gb, dev)
     return out
 
 
@@ -571,7 +614,8 @@ def main():
     ap.add_argument("--sweep", default=None,
                     help="write the config 2-4 shape sweep to this JSON file and exit")
     ap.add_argument("--gemm", default=None,
-                    help="M,N,K[,sparse]: run only this GEMM (warmup + steps launches; for profilers)")
+                    help="M,N,K[,sparse][,e4m3|e5m2,e4m3|e5m2]: run only this GEMM (warmup + "
+                         "steps launches; for profilers); the two formats are A's and B's")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -586,13 +630,17 @@ def main():
     if args.gemm:
         f = args.gemm.split(",")
         M, N, K = (int(v) for v in f[:3])
-        x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 1)
+        sparse = "sparse" in f[3:]
+        fmts = [{"e4m3": 0, "e5m2": 1}[t] for t in f[3:] if t != "sparse"] or [0, 0]
+        af, bf = fmts[0], fmts[-1]
+        x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 1, af, bf)
         C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
-        if len(f) > 3 and f[3] == "sparse":
+        if sparse:
             vals, meta = gb.prune24_compress(A)
-            fn = lambda: gb.gemm_fp8_sparse24(vals, meta, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C)
+            fn = lambda: gb.gemm_fp8_sparse24_fmt(vals, meta, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16,
+                                                  False, af, bf, C=C)
         else:
-            fn = lambda: gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C)
+            fn = lambda: gb.gemm_fp8_dense_fmt(A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, af, bf, C=C)
         for _ in range(args.warmup + args.steps):
             fn()
         torch.cuda.synchronize()

@@ -52,6 +52,16 @@ typedef enum {
     FP8_ERR_UNSUPPORTED = -8  /* no sm_103a device, or feature not built */
 } fp8_status;
 
+/* FP8 operand formats (the OCP 8-bit floating point variants; paper section
+ * 2 lists both as FP8 matrix-core operand types, "fp8" = E4M3 and "bf8" =
+ * E5M2, and Table 3 pairs them in all four combinations). */
+typedef enum {
+    FP8_E4M3 = 0,   /* sign, 4 exponent bits (bias 7), 3 mantissa bits; no
+                       infinities, S.1111.111 NaN; largest finite 448 */
+    FP8_E5M2 = 1    /* sign, 5 exponent bits (bias 15), 2 mantissa bits;
+                       IEEE-style infinities and NaNs; largest finite 57344 */
+} fp8_format;
+
 /* Static English text for a status code. */
 const char *fp8_status_string(int status);
 
@@ -88,6 +98,14 @@ int fp8_device_sm_count(void);
 int fp8_quantize_e4m3(const float *x, int64_t rows, int64_t cols, int64_t ldx, int scale_mode,
                       uint8_t *q, int64_t ldq, float *dequant_scale, fp8_stream_t stream);
 
+/* E5M2 quantisation: fp8_quantize_e4m3 with 57344, the largest finite E5M2
+ * value, in place of 448.  s = fl32(57344 / amax), d = fl32(amax / 57344),
+ * q = E5M2(fl32(x * s)) rounded to nearest even and saturated to +-57344,
+ * so no code is ever an infinity or NaN.  Arguments, layouts, ownership
+ * and errors as fp8_quantize_e4m3. */
+int fp8_quantize_e5m2(const float *x, int64_t rows, int64_t cols, int64_t ldx, int scale_mode,
+                      uint8_t *q, int64_t ldq, float *dequant_scale, fp8_stream_t stream);
+
 /* Per-row quantisation (scale_mode 1 above) of up to FP8_QUANT_GROUPED_MAX
  * independent fp32 matrices in one launch; each job follows the conventions
  * of fp8_quantize_e4m3 (FP8_ERR_SHAPE for more jobs).  Used by the request
@@ -110,9 +128,10 @@ int fp8_quantize_e4m3_rows_grouped(const fp8_quant_job *jobs, int num_jobs, fp8_
  * blames a fixed conversion + allocation + dispatch cost in section 6.1.1 —
  * this call allocates nothing and is one bandwidth-bound kernel).
  *
- * a: device E4M3 codes [M, K], row stride lda bytes; K % 4 == 0 (else
- * FP8_ERR_SHAPE).  For each row and each group g of four codes
- * a[4g..4g+3]: key = code & 0x7F (monotone in |value|); the two positions
+ * a: device FP8 codes [M, K] (E4M3 or E5M2), row stride lda bytes;
+ * K % 4 == 0 (else FP8_ERR_SHAPE).  For each row and each group g of four
+ * codes a[4g..4g+3]: key = code & 0x7F (monotone in |value| over the finite
+ * codes of either format); the two positions
  * first in (key descending, index ascending) order are kept.
  * a_vals: device [M, K/2] (row stride K/2): the kept codes of group g at
  *         2g, 2g+1 in increasing index order.
@@ -164,6 +183,17 @@ int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t ld
                    const uint8_t *B, int64_t ldb, const float *a_scale, int a_mode,
                    const float *b_scale, int b_mode, float alpha, void *C, int64_t ldc,
                    int out_dtype, fp8_stream_t stream);
+
+/* gemm_fp8_dense with a format for each operand: A's codes decode as
+ * a_format and B's as b_format, each an fp8_format (FP8_ERR_INVALID
+ * otherwise), so the four pairings of paper Table 3 (E4M3 x E4M3,
+ * E4M3 x E5M2, E5M2 x E4M3, E5M2 x E5M2) run on the same kernel; only the
+ * tensor-core instruction descriptor changes.  gemm_fp8_dense is this call
+ * with FP8_E4M3 for both.  Everything else as gemm_fp8_dense. */
+int gemm_fp8_dense_fmt(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
+                       const uint8_t *B, int64_t ldb, const float *a_scale, int a_mode,
+                       const float *b_scale, int b_mode, float alpha, void *C, int64_t ldc,
+                       int out_dtype, int a_format, int b_format, fp8_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gemm_fp8_dense without any device allocation.  (The paper has no
@@ -217,6 +247,16 @@ int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t *a_vals,
                       int a_mode, const float *b_scale, int b_mode, float alpha, void *C,
                       int64_t ldc, int out_dtype, int out_transposed, fp8_stream_t stream);
 
+/* gemm_fp8_sparse24 with a format for each operand (a_format for the kept
+ * codes of A, b_format for B; fp8_format values, FP8_ERR_INVALID otherwise).
+ * prune24_compress serves both formats: its key (code & 0x7F) orders the
+ * finite codes of either by magnitude. */
+int gemm_fp8_sparse24_fmt(int64_t M, int64_t N, int64_t K, const uint8_t *a_vals,
+                          const uint8_t *a_meta, const uint8_t *B, int64_t ldb,
+                          const float *a_scale, int a_mode, const float *b_scale, int b_mode,
+                          float alpha, void *C, int64_t ldc, int out_dtype, int out_transposed,
+                          int a_format, int b_format, fp8_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Grouped GEMM (row a7): many independent problems in one persistent launch.
  * Paper: section 7.1 (a transformer-style sequence of FP8 GEMMs) and the
@@ -247,6 +287,8 @@ typedef struct {
     int64_t ldc;
     int out_dtype;
     int out_transposed;
+    int a_format;           /* fp8_format of A (a zero-initialised problem is */
+    int b_format;           /* E4M3 x E4M3) and of B */
 } fp8_gemm_problem;
 
 int gemm_fp8_grouped(const fp8_gemm_problem *problems, int num_problems, fp8_stream_t stream);

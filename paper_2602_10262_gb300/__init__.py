@@ -1,4 +1,4 @@
-"""gb300fp8: FP8 E4M3 dense and 2:4-sparse GEMM for NVIDIA GB300 (sm_103a).
+"""gb300fp8: FP8 (E4M3 / E5M2) dense and 2:4-sparse GEMM for NVIDIA GB300 (sm_103a).
 
 Thin PyTorch-facing binding over the C ABI of ``libgb300fp8.so``
 (include/gb300fp8.h).  Every function has the C entry point's name and only
@@ -17,15 +17,18 @@ import torch
 from . import _lib
 
 __all__ = [
-    "Fp8Error", "library", "fp8_quantize_e4m3", "prune24_compress", "prune24_decompress",
-    "gemm_fp8_dense", "gemm_fp8_sparse24", "gemm_fp8_grouped", "fp8_last_device_error",
+    "Fp8Error", "library", "fp8_quantize_e4m3", "fp8_quantize_e5m2", "prune24_compress",
+    "prune24_decompress", "gemm_fp8_dense", "gemm_fp8_dense_fmt", "gemm_fp8_sparse24",
+    "gemm_fp8_sparse24_fmt", "gemm_fp8_grouped", "fp8_last_device_error",
     "fp8_device_sm_count", "fp8_gemm_set_tile_config", "gemm_fp8_grouped_autotune",
     "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
-    "GroupedGraph", "OUT_F32", "OUT_BF16",
+    "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2",
 ]
 
 OUT_F32 = 0
 OUT_BF16 = 1
+E4M3 = 0          # fp8_format values of the C ABI
+E5M2 = 1
 
 
 class Fp8Error(RuntimeError):
@@ -85,9 +88,7 @@ def fp8_gemm_set_tile_config(mt: int = 0, group_m: int = 0) -> None:
     _check(library().fp8_gemm_set_tile_config(int(mt), int(group_m)), "fp8_gemm_set_tile_config")
 
 
-def fp8_quantize_e4m3(x: torch.Tensor, scale_mode: int, q: Optional[torch.Tensor] = None,
-                      dequant_scale: Optional[torch.Tensor] = None, stream=None):
-    """fp32 [R, C] -> (E4M3 codes uint8 [R, C], dequant scales fp32 [1] or [R])."""
+def _quantize(name: str, x, scale_mode, q, dequant_scale, stream):
     _dev(x, "x", torch.float32, 2)
     R, C = x.shape
     if q is None:
@@ -95,10 +96,22 @@ def fp8_quantize_e4m3(x: torch.Tensor, scale_mode: int, q: Optional[torch.Tensor
     if dequant_scale is None:
         dequant_scale = torch.empty((1 if scale_mode == 0 else R,), dtype=torch.float32, device=x.device)
     _dev(q, "q", torch.uint8, 2)
-    rc = library().fp8_quantize_e4m3(_p(x), R, C, _ld(x), int(scale_mode), _p(q), _ld(q),
-                                     _p(dequant_scale), _stream(stream))
-    _check(rc, "fp8_quantize_e4m3")
+    rc = getattr(library(), name)(_p(x), R, C, _ld(x), int(scale_mode), _p(q), _ld(q),
+                                  _p(dequant_scale), _stream(stream))
+    _check(rc, name)
     return q, dequant_scale
+
+
+def fp8_quantize_e4m3(x: torch.Tensor, scale_mode: int, q: Optional[torch.Tensor] = None,
+                      dequant_scale: Optional[torch.Tensor] = None, stream=None):
+    """fp32 [R, C] -> (E4M3 codes uint8 [R, C], dequant scales fp32 [1] or [R])."""
+    return _quantize("fp8_quantize_e4m3", x, scale_mode, q, dequant_scale, stream)
+
+
+def fp8_quantize_e5m2(x: torch.Tensor, scale_mode: int, q: Optional[torch.Tensor] = None,
+                      dequant_scale: Optional[torch.Tensor] = None, stream=None):
+    """fp32 [R, C] -> (E5M2 codes uint8 [R, C], dequant scales fp32 [1] or [R])."""
+    return _quantize("fp8_quantize_e5m2", x, scale_mode, q, dequant_scale, stream)
 
 
 def prune24_compress(a: torch.Tensor, a_vals: Optional[torch.Tensor] = None,
@@ -152,6 +165,26 @@ def gemm_fp8_dense(A: torch.Tensor, B: torch.Tensor, a_scale: torch.Tensor, a_mo
     return C
 
 
+def gemm_fp8_dense_fmt(A: torch.Tensor, B: torch.Tensor, a_scale: torch.Tensor, a_mode: int,
+                       b_scale: torch.Tensor, b_mode: int, alpha: float = 1.0,
+                       out_dtype: int = OUT_BF16, a_format: int = E4M3, b_format: int = E4M3,
+                       C: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """gemm_fp8_dense with A's codes read as a_format and B's as b_format."""
+    _dev(A, "A", torch.uint8, 2)
+    _dev(B, "B", torch.uint8, 2)
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("K mismatch")
+    C = _out(C, M, N, out_dtype, A.device)
+    rc = library().gemm_fp8_dense_fmt(M, N, K, _p(A), _ld(A), _p(B), _ld(B), _p(a_scale),
+                                      int(a_mode), _p(b_scale), int(b_mode), float(alpha), _p(C),
+                                      _ld(C), int(out_dtype), int(a_format), int(b_format),
+                                      _stream(stream))
+    _check(rc, "gemm_fp8_dense_fmt")
+    return C
+
+
 def gemm_fp8_sparse24(a_vals: torch.Tensor, a_meta: torch.Tensor, B: torch.Tensor,
                       a_scale: torch.Tensor, a_mode: int, b_scale: torch.Tensor, b_mode: int,
                       alpha: float = 1.0, out_dtype: int = OUT_BF16, out_transposed: bool = False,
@@ -174,9 +207,35 @@ def gemm_fp8_sparse24(a_vals: torch.Tensor, a_meta: torch.Tensor, B: torch.Tenso
     return C
 
 
+def gemm_fp8_sparse24_fmt(a_vals: torch.Tensor, a_meta: torch.Tensor, B: torch.Tensor,
+                          a_scale: torch.Tensor, a_mode: int, b_scale: torch.Tensor, b_mode: int,
+                          alpha: float = 1.0, out_dtype: int = OUT_BF16,
+                          out_transposed: bool = False, a_format: int = E4M3,
+                          b_format: int = E4M3, C: Optional[torch.Tensor] = None,
+                          stream=None) -> torch.Tensor:
+    """gemm_fp8_sparse24 with the kept codes of A read as a_format and B as b_format."""
+    _dev(a_vals, "a_vals", torch.uint8, 2)
+    _dev(a_meta, "a_meta", torch.uint8, 2)
+    _dev(B, "B", torch.uint8, 2)
+    M = a_vals.shape[0]
+    K = a_vals.shape[1] * 2
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("K mismatch")
+    C = _out(C, N if out_transposed else M, M if out_transposed else N, out_dtype, B.device)
+    rc = library().gemm_fp8_sparse24_fmt(M, N, K, _p(a_vals), _p(a_meta), _p(B), _ld(B),
+                                         _p(a_scale), int(a_mode), _p(b_scale), int(b_mode),
+                                         float(alpha), _p(C), _ld(C), int(out_dtype),
+                                         int(bool(out_transposed)), int(a_format), int(b_format),
+                                         _stream(stream))
+    _check(rc, "gemm_fp8_sparse24_fmt")
+    return C
+
+
 def make_problem(A: torch.Tensor, B: torch.Tensor, a_scale, a_mode, b_scale, b_mode, C,
                  alpha: float = 1.0, out_dtype: int = OUT_BF16, A_meta=None, K: Optional[int] = None,
-                 out_transposed: bool = False) -> _lib.FP8Problem:
+                 out_transposed: bool = False, a_format: int = E4M3,
+                 b_format: int = E4M3) -> _lib.FP8Problem:
     """Build one ``fp8_gemm_problem`` entry (tensors must outlive the call)."""
     sparse = A_meta is not None
     M = A.shape[0]
@@ -186,7 +245,8 @@ def make_problem(A: torch.Tensor, B: torch.Tensor, a_scale, a_mode, b_scale, b_m
     return _lib.FP8Problem(M, B.shape[0], Kd, A.data_ptr(), 0 if A_meta is None else A_meta.data_ptr(),
                            _ld(A), B.data_ptr(), _ld(B), a_scale.data_ptr(), int(a_mode),
                            b_scale.data_ptr(), int(b_mode), float(alpha), C.data_ptr(), _ld(C),
-                           int(out_dtype), int(bool(out_transposed)))
+                           int(out_dtype), int(bool(out_transposed)), int(a_format),
+                           int(b_format))
 
 
 def gemm_fp8_grouped(problems: Sequence[_lib.FP8Problem], stream=None) -> None:

@@ -32,6 +32,7 @@ class FP8Problem(ctypes.Structure):
         ("alpha", F32),
         ("C", P), ("ldc", I64),
         ("out_dtype", I32), ("out_transposed", I32),
+        ("a_format", I32), ("b_format", I32),
     ]
 
 
@@ -79,11 +80,16 @@ SIGNATURES = {
     "fp8_last_device_error": (I32, [P]),
     "fp8_device_sm_count": (I32, []),
     "fp8_quantize_e4m3": (I32, [P, I64, I64, I64, I32, P, I64, P, P]),
+    "fp8_quantize_e5m2": (I32, [P, I64, I64, I64, I32, P, I64, P, P]),
     "prune24_compress": (I32, [P, I64, I64, I64, P, P, P]),
     "prune24_decompress": (I32, [P, P, I64, I64, P, P]),
     "gemm_fp8_dense": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32, P]),
     "gemm_fp8_dense_noalloc": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32, P]),
+    "gemm_fp8_dense_fmt": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32,
+                                 I32, I32, P]),
     "gemm_fp8_sparse24": (I32, [I64, I64, I64, P, P, P, I64, P, I32, P, I32, F32, P, I64, I32, I32, P]),
+    "gemm_fp8_sparse24_fmt": (I32, [I64, I64, I64, P, P, P, I64, P, I32, P, I32, F32, P, I64, I32,
+                                    I32, I32, I32, P]),
     "gemm_fp8_grouped": (I32, [ctypes.POINTER(FP8Problem), I32, P]),
     "gemm_fp8_grouped_ex": (I32, [ctypes.POINTER(FP8Problem), I32, I32, P]),
     "fp8_quantize_e4m3_rows_grouped": (I32, [ctypes.POINTER(FP8QuantJob), I32, P]),

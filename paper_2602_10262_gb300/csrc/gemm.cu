@@ -1,5 +1,6 @@
-// FP8 E4M3 GEMM on tcgen05 tensor cores: gemm_fp8_dense, gemm_fp8_sparse24
-// and gemm_fp8_grouped all run the kernel below.
+// FP8 GEMM on tcgen05 tensor cores: gemm_fp8_dense(_fmt), gemm_fp8_sparse24(_fmt)
+// and gemm_fp8_grouped all run the kernel below.  Each operand is E4M3 or
+// E5M2; the format only sets two fields of the MMA instruction descriptor.
 //
 // Roles of one CTA (192 threads, one CTA per SM, persistent over tiles):
 //   warp 0, lane 0   TMA producer: for each (tile, k-block) waits for a free
@@ -1040,7 +1041,18 @@ struct Job {
     int64_t ldc;
     int out_bf16;
     int trans_out;
+    int fmt_p, fmt_q;       // fp8_format of P and Q (instruction-descriptor A / B format)
 };
+
+bool valid_format(int f)
+{
+    return f == FP8_E4M3 || f == FP8_E5M2;
+}
+
+uint32_t mma_format(int f)
+{
+    return f == FP8_E5M2 ? kMmaFmtE5M2 : kMmaFmtE4M3;
+}
 
 // Argument checks shared by every entry point.  `sparse`: A is the kept-code
 // array [M, K/2] (contiguous) and A_meta the metadata [M, K/8] (contiguous).
@@ -1165,7 +1177,7 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
     pr.splits = split_count(j);
     pr.kb_per_split = pr.splits > 1 ? slice_kblocks(pr.k_blocks, pr.splits) : pr.k_blocks;
     pr.splits = (pr.k_blocks + pr.kb_per_split - 1) / pr.kb_per_split;     // no empty slice
-    pr.idesc = idesc_e4m3_f32(BM, bn, pr.sparse != 0, 0);
+    pr.idesc = idesc_f8_f32(BM, bn, pr.sparse != 0, 0, mma_format(j.fmt_p), mma_format(j.fmt_q));
     return FP8_OK;
 }
 
@@ -1722,7 +1734,7 @@ int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_
 Job make_job(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
              const uint8_t* A_meta, const uint8_t* B, int64_t ldb, const float* a_scale, int a_mode,
              const float* b_scale, int b_mode, float alpha, void* C, int64_t ldc, int out_dtype,
-             int out_transposed)
+             int out_transposed, int a_fmt, int b_fmt)
 {
     Job j{};
     const bool swap = A_meta == nullptr && M <= 128 && N > M;
@@ -1734,10 +1746,12 @@ Job make_job(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
     if (!swap) {
         j.rows_p = M, j.P = A, j.E = A_meta, j.ldp = lda, j.sp = a_scale, j.sp_mode = a_mode;
         j.rows_q = N, j.Q = B, j.ldq = ldb, j.sq = b_scale, j.sq_mode = b_mode;
+        j.fmt_p = a_fmt, j.fmt_q = b_fmt;
         j.trans_out = out_transposed;
     } else {
         j.rows_p = N, j.P = B, j.E = nullptr, j.ldp = ldb, j.sp = b_scale, j.sp_mode = b_mode;
         j.rows_q = M, j.Q = A, j.ldq = lda, j.sq = a_scale, j.sq_mode = a_mode;
+        j.fmt_p = b_fmt, j.fmt_q = a_fmt;
         j.trans_out = !out_transposed;
     }
     return j;
@@ -1751,7 +1765,19 @@ extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A,
                               const float* b_scale, int b_mode, float alpha, void* C, int64_t ldc,
                               int out_dtype, fp8_stream_t stream)
 {
+    return gemm_fp8_dense_fmt(M, N, K, A, lda, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
+                              ldc, out_dtype, FP8_E4M3, FP8_E4M3, stream);
+}
+
+extern "C" int gemm_fp8_dense_fmt(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
+                                  const uint8_t* B, int64_t ldb, const float* a_scale, int a_mode,
+                                  const float* b_scale, int b_mode, float alpha, void* C,
+                                  int64_t ldc, int out_dtype, int a_format, int b_format,
+                                  fp8_stream_t stream)
+{
     using namespace gb300;
+    if (!valid_format(a_format) || !valid_format(b_format))
+        return FP8_ERR_INVALID;
     int rc = validate(M, N, K, A, lda, nullptr, false, B, ldb, a_scale, a_mode, b_scale, b_mode, C,
                       ldc, out_dtype, 0);
     if (rc != FP8_OK || M == 0 || N == 0)
@@ -1762,7 +1788,7 @@ extern "C" int gemm_fp8_dense(int64_t M, int64_t N, int64_t K, const uint8_t* A,
     if (K == 0)
         return write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
-                     ldc, out_dtype, 0);
+                     ldc, out_dtype, 0, a_format, b_format);
     const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
@@ -1816,7 +1842,7 @@ extern "C" int gemm_fp8_dense_noalloc(int64_t M, int64_t N, int64_t K, const uin
     if (K == 0)
         return write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, a_scale, a_mode, b_scale, b_mode, alpha, C,
-                     ldc, out_dtype, 0);
+                     ldc, out_dtype, 0, FP8_E4M3, FP8_E4M3);
     const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
@@ -1845,7 +1871,21 @@ extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t*
                                  float alpha, void* C, int64_t ldc, int out_dtype,
                                  int out_transposed, fp8_stream_t stream)
 {
+    return gemm_fp8_sparse24_fmt(M, N, K, a_vals, a_meta, B, ldb, a_scale, a_mode, b_scale, b_mode,
+                                 alpha, C, ldc, out_dtype, out_transposed, FP8_E4M3, FP8_E4M3,
+                                 stream);
+}
+
+extern "C" int gemm_fp8_sparse24_fmt(int64_t M, int64_t N, int64_t K, const uint8_t* a_vals,
+                                     const uint8_t* a_meta, const uint8_t* B, int64_t ldb,
+                                     const float* a_scale, int a_mode, const float* b_scale,
+                                     int b_mode, float alpha, void* C, int64_t ldc, int out_dtype,
+                                     int out_transposed, int a_format, int b_format,
+                                     fp8_stream_t stream)
+{
     using namespace gb300;
+    if (!valid_format(a_format) || !valid_format(b_format))
+        return FP8_ERR_INVALID;
     int rc = validate(M, N, K, a_vals, K / 2, a_meta, true, B, ldb, a_scale, a_mode, b_scale,
                       b_mode, C, ldc, out_dtype, out_transposed);
     if (rc != FP8_OK || M == 0 || N == 0)
@@ -1857,7 +1897,7 @@ extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t*
         return out_transposed ? write_zeros(C, ldc, N, M, out_dtype, st)
                               : write_zeros(C, ldc, M, N, out_dtype, st);
     Job j = make_job(M, N, K, a_vals, K / 2, a_meta, B, ldb, a_scale, a_mode, b_scale, b_mode,
-                     alpha, C, ldc, out_dtype, out_transposed);
+                     alpha, C, ldc, out_dtype, out_transposed, a_format, b_format);
     const int bn = pick_bn(j.rows_p, j.rows_q, j.K, SPARSE_BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
@@ -1892,6 +1932,8 @@ int grouped_jobs(const fp8_gemm_problem* problems, int num_problems, cudaStream_
                           g.out_transposed);
         if (rc != FP8_OK)
             return rc;
+        if (!valid_format(g.a_format) || !valid_format(g.b_format))
+            return FP8_ERR_INVALID;
         if (!zeros_ok && g.M > 0 && g.N > 0 && g.K == 0)
             return FP8_ERR_SHAPE;
         any_sparse |= sp && g.M > 0 && g.N > 0 && g.K > 0;
@@ -1918,7 +1960,7 @@ int grouped_jobs(const fp8_gemm_problem* problems, int num_problems, cudaStream_
         const bool sp = g.A_meta != nullptr;
         jobs[n] = make_job(g.M, g.N, g.K, g.A, sp ? g.K / 2 : g.lda, g.A_meta, g.B, g.ldb,
                            g.a_scale, g.a_mode, g.b_scale, g.b_mode, g.alpha, g.C, g.ldc,
-                           g.out_dtype, g.out_transposed);
+                           g.out_dtype, g.out_transposed, g.a_format, g.b_format);
         bns[n] = pick_bn(jobs[n].rows_p, jobs[n].rows_q, jobs[n].K, bn_max);
         ++n;
     }

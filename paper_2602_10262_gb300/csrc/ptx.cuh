@@ -373,16 +373,20 @@ __device__ __forceinline__ void tmem_cp_128x128b(uint32_t taddr, uint64_t sdesc)
     asm volatile("tcgen05.cp.cta_group::1.128x128b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
 }
 
-// Instruction descriptor, kind::f8f6f4: E4M3 A and B, both K-major, F32
+// Instruction descriptor, kind::f8f6f4: FP8 A and B, both K-major, F32
 // accumulator, M x N tile.
 //   bits 0-1 sparsity selector, bit 2 sparse flag, bits 4-5 D format (1 = F32),
-//   bits 7-9 A format (0 = E4M3), bits 10-12 B format (0 = E4M3),
+//   bits 7-9 A format, bits 10-12 B format (0 = E4M3, 1 = E5M2),
 //   bit 15/16 A/B major (0 = K), bits 17-22 N >> 3, bits 24-28 M >> 4.
-__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N, bool sparse = false,
-                                                      int selector = 0)
+constexpr uint32_t kMmaFmtE4M3 = 0u;
+constexpr uint32_t kMmaFmtE5M2 = 1u;
+
+__host__ __device__ constexpr uint32_t idesc_f8_f32(int M, int N, bool sparse, int selector,
+                                                    uint32_t a_fmt, uint32_t b_fmt)
 {
     return (static_cast<uint32_t>(selector) & 3u) | (sparse ? (1u << 2) : 0u) | (1u << 4) |
-           (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+           ((a_fmt & 7u) << 7) | ((b_fmt & 7u) << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 }  // namespace gb300

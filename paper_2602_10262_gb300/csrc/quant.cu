@@ -1,4 +1,4 @@
-// Scale selection + E4M3 quantisation (fp8_quantize_e4m3).
+// Scale selection + FP8 quantisation (fp8_quantize_e4m3, fp8_quantize_e5m2).
 //
 // Per row (scale_mode 1): one CTA per row.  Pass 1 takes amax of the row with
 // 16-byte loads and a warp/CTA max reduction on the fp32 bit patterns of |x|
@@ -14,8 +14,10 @@
 // dequant_scale[0] slot with atomicMax, an encode kernel reads it, and a
 // one-thread kernel turns the slot into d = amax / 448.
 //
-// The scale is s = 448 / amax with an IEEE-rounded division (__fdiv_rn) and
-// each code is cvt.rn.satfinite.e4m3 of the IEEE product x * s (__fmul_rn).
+// The scale is s = T / amax with an IEEE-rounded division (__fdiv_rn), T the
+// format's largest finite value (448 for E4M3, 57344 for E5M2), and each code
+// is cvt.rn.satfinite of the IEEE product x * s (__fmul_rn) to that format.
+// Every kernel is a template on the format (FMT 0: E4M3, 1: E5M2).
 #include <cuda_fp8.h>
 
 #include "common.cuh"
@@ -31,17 +33,27 @@ __device__ __forceinline__ uint32_t abs_bits(float v)
     return __float_as_uint(v) & 0x7FFFFFFFu;
 }
 
-// Two fp32 values -> two E4M3 codes (a in the low byte).
-__device__ __forceinline__ uint32_t enc2(float a, float b)
+// Largest finite value of the format: the target of amax.
+template <int FMT>
+__device__ __forceinline__ float fmt_max()
 {
-    return static_cast<uint32_t>(
-        __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3));
+    return FMT == 1 ? 57344.0f : 448.0f;
 }
 
+// Two fp32 values -> two codes (a in the low byte), round to nearest even,
+// saturating to the largest finite value.
+template <int FMT>
+__device__ __forceinline__ uint32_t enc2(float a, float b)
+{
+    return static_cast<uint32_t>(__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE,
+                                                          FMT == 1 ? __NV_E5M2 : __NV_E4M3));
+}
+
+template <int FMT>
 __device__ __forceinline__ uint32_t enc4(float4 v, float s)
 {
-    return enc2(__fmul_rn(v.x, s), __fmul_rn(v.y, s)) |
-           (enc2(__fmul_rn(v.z, s), __fmul_rn(v.w, s)) << 16);
+    return enc2<FMT>(__fmul_rn(v.x, s), __fmul_rn(v.y, s)) |
+           (enc2<FMT>(__fmul_rn(v.z, s), __fmul_rn(v.w, s)) << 16);
 }
 
 __device__ __forceinline__ uint32_t block_max_u32(uint32_t v, uint32_t* red)
@@ -64,6 +76,7 @@ __device__ __forceinline__ uint32_t block_max_u32(uint32_t v, uint32_t* red)
 }
 
 // scale and dequant factor from the amax bit pattern
+template <int FMT>
 __device__ __forceinline__ void scale_from_amax(uint32_t amax_bits, float& s, float& d)
 {
     const float amax = __uint_as_float(amax_bits);
@@ -71,13 +84,14 @@ __device__ __forceinline__ void scale_from_amax(uint32_t amax_bits, float& s, fl
         s = 1.0f;
         d = 1.0f;
     } else {
-        s = __fdiv_rn(448.0f, amax);
-        d = __fdiv_rn(amax, 448.0f);
+        s = __fdiv_rn(fmt_max<FMT>(), amax);
+        d = __fdiv_rn(amax, fmt_max<FMT>());
     }
 }
 
 // One row: amax (CTA reduction), scale, codes.  vec: the row allows 16-byte
 // loads and 4-byte stores (x 16-aligned, q 4-aligned).
+template <int FMT>
 __device__ __forceinline__ void quantize_row(const float* __restrict__ xr, int64_t cols,
                                              uint8_t* __restrict__ qr, float* __restrict__ d_out,
                                              int vec, int* err, uint32_t* red)
@@ -94,19 +108,20 @@ __device__ __forceinline__ void quantize_row(const float* __restrict__ xr, int64
     if (m >= kInfBits && threadIdx.x == 0)
         report_device_error(err, FP8_ERR_NONFINITE);
     float s, dq;
-    scale_from_amax(m, s, dq);
+    scale_from_amax<FMT>(m, s, dq);
     if (threadIdx.x == 0)
         *d_out = dq;
     for (int64_t i = threadIdx.x; i < nvec; i += kThreads) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(xr) + i);
-        reinterpret_cast<uint32_t*>(qr)[i] = enc4(v, s);
+        reinterpret_cast<uint32_t*>(qr)[i] = enc4<FMT>(v, s);
     }
     for (int64_t c = nvec * 4 + threadIdx.x; c < cols; c += kThreads)
-        qr[c] = static_cast<uint8_t>(enc2(__fmul_rn(xr[c], s), 0.0f) & 0xFFu);
+        qr[c] = static_cast<uint8_t>(enc2<FMT>(__fmul_rn(xr[c], s), 0.0f) & 0xFFu);
 }
 
 // vec: x rows and q rows allow 16-byte loads / 4-byte stores (x 16-aligned,
 // ldx % 4 == 0, q 4-aligned, ldq % 4 == 0).
+template <int FMT>
 __global__ void __launch_bounds__(kThreads) quant_row_kernel(const float* __restrict__ x,
                                                              int64_t rows, int64_t cols,
                                                              int64_t ldx, uint8_t* __restrict__ q,
@@ -116,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) quant_row_kernel(const float* __rest
     grid_launch_dependents();
     __shared__ uint32_t red[kThreads / 32];
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
-        quantize_row(x + r * ldx, cols, q + r * ldq, d + r, vec, err, red);
+        quantize_row<FMT>(x + r * ldx, cols, q + r * ldq, d + r, vec, err, red);
 }
 
 // Many independent per-row quantisations in one launch: the job table is
@@ -141,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) quant_rows_grouped_kernel(const __gr
             ++j;
         const fp8_quant_job& J = jobs.job[j];
         const int64_t r = g - jobs.row_start[j];
-        quantize_row(J.x + r * J.ldx, J.cols, J.q + r * J.ldq, J.dequant_scale + r, jobs.vec[j], err,
+        quantize_row<0>(J.x + r * J.ldx, J.cols, J.q + r * J.ldq, J.dequant_scale + r, jobs.vec[j], err,
                      red);
     }
 }
@@ -173,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) quant_amax_kernel(const float* __res
         atomicMax(slot, m);
 }
 
+template <int FMT>
 __global__ void __launch_bounds__(kThreads) quant_encode_kernel(const float* __restrict__ x,
                                                                 int64_t rows, int64_t cols,
                                                                 int64_t ldx, uint8_t* __restrict__ q,
@@ -180,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) quant_encode_kernel(const float* __r
                                                                 const uint32_t* __restrict__ slot)
 {
     float s, dq;
-    scale_from_amax(*slot, s, dq);
+    scale_from_amax<FMT>(*slot, s, dq);
     const int64_t per_row = vec ? cols / 4 : 0;
     const int64_t total_vec = per_row * rows;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
@@ -188,16 +204,17 @@ __global__ void __launch_bounds__(kThreads) quant_encode_kernel(const float* __r
          i += stride) {
         const int64_t r = i / per_row, c4 = i - r * per_row;
         const float4 v = __ldg(reinterpret_cast<const float4*>(x + r * ldx) + c4);
-        reinterpret_cast<uint32_t*>(q + r * ldq)[c4] = enc4(v, s);
+        reinterpret_cast<uint32_t*>(q + r * ldq)[c4] = enc4<FMT>(v, s);
     }
     const int64_t tail = cols - per_row * 4;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < tail * rows;
          i += stride) {
         const int64_t r = i / tail, c = per_row * 4 + (i - r * tail);
-        q[r * ldq + c] = static_cast<uint8_t>(enc2(__fmul_rn(x[r * ldx + c], s), 0.0f) & 0xFFu);
+        q[r * ldq + c] = static_cast<uint8_t>(enc2<FMT>(__fmul_rn(x[r * ldx + c], s), 0.0f) & 0xFFu);
     }
 }
 
+template <int FMT>
 __global__ void quant_finalize_kernel(uint32_t* slot, int* err)
 {
     grid_launch_dependents();
@@ -205,18 +222,14 @@ __global__ void quant_finalize_kernel(uint32_t* slot, int* err)
     if (m >= kInfBits)
         report_device_error(err, FP8_ERR_NONFINITE);
     float s, dq;
-    scale_from_amax(m, s, dq);
+    scale_from_amax<FMT>(m, s, dq);
     *reinterpret_cast<float*>(slot) = dq;
 }
 
-}  // namespace
-}  // namespace gb300
-
-extern "C" int fp8_quantize_e4m3(const float* x, int64_t rows, int64_t cols, int64_t ldx,
-                                 int scale_mode, uint8_t* q, int64_t ldq, float* dequant_scale,
-                                 fp8_stream_t stream)
+template <int FMT>
+int quantize(const float* x, int64_t rows, int64_t cols, int64_t ldx, int scale_mode, uint8_t* q,
+             int64_t ldq, float* dequant_scale, cudaStream_t st)
 {
-    using namespace gb300;
     if (rows < 0 || cols < 0 || (scale_mode != 0 && scale_mode != 1))
         return FP8_ERR_INVALID;
     if (rows == 0 || cols == 0)
@@ -230,13 +243,12 @@ extern "C" int fp8_quantize_e4m3(const float* x, int64_t rows, int64_t cols, int
     if (!device_supported())
         return FP8_ERR_UNSUPPORTED;
     int* err = device_error_word();
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int vec = aligned16(x) && (ldx % 4 == 0) &&
                     (reinterpret_cast<uintptr_t>(q) % 4 == 0) && (ldq % 4 == 0);
     const int sms = sm_count();
     if (scale_mode == 1) {
         const int64_t grid = rows < 65535LL * 8 ? rows : 65535LL * 8;
-        quant_row_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(
+        quant_row_kernel<FMT><<<static_cast<unsigned>(grid), kThreads, 0, st>>>(
             x, rows, cols, ldx, q, ldq, dequant_scale, vec, err);
         GB_CUDA_OK(cudaGetLastError());
         return FP8_OK;
@@ -248,12 +260,31 @@ extern "C" int fp8_quantize_e4m3(const float* x, int64_t rows, int64_t cols, int
     quant_amax_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(x, rows, cols, ldx, vec,
                                                                         slot);
     GB_CUDA_OK(cudaGetLastError());
-    quant_encode_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(x, rows, cols, ldx, q,
-                                                                          ldq, vec, slot);
+    quant_encode_kernel<FMT><<<static_cast<unsigned>(grid), kThreads, 0, st>>>(x, rows, cols, ldx,
+                                                                               q, ldq, vec, slot);
     GB_CUDA_OK(cudaGetLastError());
-    quant_finalize_kernel<<<1, 1, 0, st>>>(slot, err);
+    quant_finalize_kernel<FMT><<<1, 1, 0, st>>>(slot, err);
     GB_CUDA_OK(cudaGetLastError());
     return FP8_OK;
+}
+
+}  // namespace
+}  // namespace gb300
+
+extern "C" int fp8_quantize_e4m3(const float* x, int64_t rows, int64_t cols, int64_t ldx,
+                                 int scale_mode, uint8_t* q, int64_t ldq, float* dequant_scale,
+                                 fp8_stream_t stream)
+{
+    return gb300::quantize<0>(x, rows, cols, ldx, scale_mode, q, ldq, dequant_scale,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fp8_quantize_e5m2(const float* x, int64_t rows, int64_t cols, int64_t ldx,
+                                 int scale_mode, uint8_t* q, int64_t ldq, float* dequant_scale,
+                                 fp8_stream_t stream)
+{
+    return gb300::quantize<1>(x, rows, cols, ldx, scale_mode, q, ldq, dequant_scale,
+                              reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int fp8_quantize_e4m3_rows_grouped(const fp8_quant_job* jobs, int num_jobs,

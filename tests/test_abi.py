@@ -31,7 +31,8 @@ def lib():
 
 def test_header_declares_the_path():
     names = _declared_functions()
-    for n in ("fp8_quantize_e4m3", "prune24_compress", "gemm_fp8_dense", "gemm_fp8_sparse24",
+    for n in ("fp8_quantize_e4m3", "fp8_quantize_e5m2", "prune24_compress", "gemm_fp8_dense",
+              "gemm_fp8_dense_fmt", "gemm_fp8_sparse24", "gemm_fp8_sparse24_fmt",
               "gemm_fp8_grouped", "fp8_last_device_error", "fp8_status_string"):
         assert n in names
 
@@ -59,9 +60,34 @@ def test_host_validation_without_gpu(lib):
     assert lib.prune24_compress(P(16), 4, 6, 16, P(16), P(16), None) == -2
     assert lib.fp8_quantize_e4m3(P(16), 4, 4, 4, 3, P(16), 4, P(16), None) == -1
     assert lib.fp8_quantize_e4m3(P(16), 4, 8, 4, 0, P(16), 8, P(16), None) == -2
+    assert lib.fp8_quantize_e5m2(P(16), 4, 4, 4, 3, P(16), 4, P(16), None) == -1
+    assert lib.fp8_quantize_e5m2(P(16), 4, 8, 4, 0, P(16), 8, P(16), None) == -2
+    # operand formats other than E4M3 (0) and E5M2 (1) are rejected
+    ok = (4, 4, 32, P(16), 32, P(16), 32, P(16), 0, P(16), 0, 1.0, P(16), 4, 0)
+    for af, bf in ((2, 0), (0, -1), (7, 7)):
+        assert lib.gemm_fp8_dense_fmt(*ok, af, bf, None) == -1
+    sp = (4, 4, 128, P(16), P(16), P(16), 128, P(16), 0, P(16), 0, 1.0, P(16), 4, 0, 0)
+    assert lib.gemm_fp8_sparse24_fmt(*sp, 0, 2, None) == -1
+    assert lib.gemm_fp8_sparse24_fmt(4, 4, 96, P(16), P(16), P(16), 128, P(16), 0, P(16), 0, 1.0,
+                                     P(16), 4, 0, 0, 1, 1, None) == -2
     # empty problems are a no-op
     assert lib.gemm_fp8_dense(0, 4, 4, None, 16, None, 16, None, 0, None, 0, 1.0, None, 4, 0, None) == 0
+    assert lib.gemm_fp8_dense_fmt(0, 4, 4, None, 16, None, 16, None, 0, None, 0, 1.0, None, 4, 0,
+                                  1, 1, None) == 0
     assert lib.fp8_quantize_e4m3(None, 0, 4, 4, 0, None, 4, None, None) == 0
+    assert lib.fp8_quantize_e5m2(None, 0, 4, 4, 0, None, 4, None, None) == 0
+
+
+def test_grouped_rejects_bad_format(lib):
+    from paper_2602_10262_gb300 import _lib
+    pr = _lib.FP8Problem(4, 4, 32, 16, 0, 32, 16, 32, 16, 0, 16, 0, 1.0, 16, 4, 0, 0, 0, 0)
+    good = (_lib.FP8Problem * 1)(pr)
+    pr.b_format = 2
+    bad = (_lib.FP8Problem * 1)(pr)
+    assert lib.gemm_fp8_grouped(bad, 1, None) == -1
+    # the same problem with valid formats passes the host checks and stops
+    # only where a device is needed (no GPU here)
+    assert lib.gemm_fp8_grouped(good, 1, None) == -8
 
 
 def test_grouped_rejects_too_many(lib):
