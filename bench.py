@@ -173,13 +173,17 @@ class OracleSample:
         self.B, self.dB = self.orc.quantize(w, 1)
         self.vals, self.meta = self.orc.prune24(self.A)
 
-    def run(self):
-        """Returns (FLOPs, seconds) of one dense + one sparse sub-block."""
+    def run(self, a=None, b=None):
+        """Returns (FLOPs, seconds) of one dense + one sparse sub-block (the
+        first a rows of A and b rows of B; default: all of the sample)."""
+        a = self.a if a is None else min(a, self.a)
+        b = self.b if b is None else min(b, self.b)
         t0 = time.perf_counter()
-        self.orc.gemm(self.A, self.B, self.dA, 1, self.dB, 1)
-        self.orc.gemm_sparse24(self.vals, self.meta, self.B, self.size, self.dA, 1, self.dB, 1)
+        self.orc.gemm(self.A[:a], self.B[:b], self.dA[:a], 1, self.dB[:b], 1)
+        self.orc.gemm_sparse24(self.vals[:a], self.meta[:a], self.B[:b], self.size, self.dA[:a], 1,
+                               self.dB[:b], 1)
         dt = time.perf_counter() - t0
-        return 2.0 * 2.0 * self.a * self.b * self.size, dt
+        return 2.0 * 2.0 * a * b * self.size, dt
 
     def describe(self):
         return (f"A rows [0,{self.a}) x B rows [0,{self.b}) at K={self.size}: "
@@ -345,7 +349,11 @@ class ServingBench:
         return np.array(out)
 
 
-def serving_report(gb, dev, n_cap=1500, n_load=1500, load=0.8):
+def serving_report(gb, dev, n_cap=1500, n_load=1500, loads=(0.8,)):
+    """Capacity of each serving mode, then the same seeded Poisson trace
+    offered at each fraction of the per-call capacity in `loads`.  The first
+    load's results sit at the top level; further loads under "other_loads"."""
+    from paper_2602_10262_gb300.server import overlap_efficiency
     sb = ServingBench(dev, gb)
     cap_reqs = sb.trace(n_cap, workloads.SEED_REQUESTS + 1)
     cap = {}
@@ -355,30 +363,38 @@ def serving_report(gb, dev, n_cap=1500, n_load=1500, load=0.8):
         cap[mode] = {"tflops": sb.flops(cap_reqs) / (span * 1e-6) / 1e12,
                      "req_per_s": n_cap / (span * 1e-6),
                      "kernel_launches": stats["kernel_launches"], "batches": stats["batches"]}
-    rate = load * min(c["req_per_s"] for c in cap.values())
     reqs = sb.trace(n_load, workloads.SEED_REQUESTS)
     iso = sb.isolated(reqs)
     tenant = np.array([r["tenant"] for r in reqs])
     out = {"workload": "Poisson two-tenant GEMM stream, M log-uniform [1,4096], "
                        "(N,K) in {4096,8192,14336}^2, 50% 2:4-sparse weights",
-           "offered_load": f"{load} x per-call capacity = {rate:.0f} req/s",
            "capacity": cap}
-    for mode in ServingBench.MODES:
-        lat, span, stats, res = sb.run(reqs, mode, rate)
-        slow = iso / lat
-        x = [float(np.mean(slow[tenant == t])) for t in (0, 1)]
-        mean_lat = [float(np.mean(lat[tenant == t])) for t in (0, 1)]
-        out[mode] = {
-            "p50_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 50)) for t in (0, 1)},
-            "p99_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 99)) for t in (0, 1)},
-            "p99_all_us": float(np.percentile(lat, 99)),
-            "tflops": sb.flops(reqs) / (span * 1e-6) / 1e12,
-            "jain": (sum(x) ** 2) / (2 * sum(v * v for v in x)),
-            "fairness_1_minus_range_over_mean": 1.0 - (max(mean_lat) - min(mean_lat)) / np.mean(mean_lat),
-            "fairness_min_over_max": min(mean_lat) / max(mean_lat),
-            "mean_batch": float(np.mean([r.batch_size for r in res])),
-            "kernel_launches": stats["kernel_launches"],
-        }
+    for i, load in enumerate(loads):
+        base = min(cap, key=lambda m: cap[m]["req_per_s"])
+        rate = load * cap[base]["req_per_s"]
+        block = {"offered_load": f"{load} x {base} capacity = {rate:.0f} req/s"}
+        for mode in ServingBench.MODES:
+            lat, span, stats, res = sb.run(reqs, mode, rate)
+            slow = iso / lat
+            x = [float(np.mean(slow[tenant == t])) for t in (0, 1)]
+            mean_lat = [float(np.mean(lat[tenant == t])) for t in (0, 1)]
+            block[mode] = {
+                "p50_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 50)) for t in (0, 1)},
+                "p99_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 99)) for t in (0, 1)},
+                "p99_all_us": float(np.percentile(lat, 99)),
+                "tflops": sb.flops(reqs) / (span * 1e-6) / 1e12,
+                "jain": (sum(x) ** 2) / (2 * sum(v * v for v in x)),
+                "fairness_1_minus_range_over_mean":
+                    1.0 - (max(mean_lat) - min(mean_lat)) / np.mean(mean_lat),
+                "fairness_min_over_max": min(mean_lat) / max(mean_lat),
+                "overlap_efficiency": overlap_efficiency(res),
+                "mean_batch": float(np.mean([r.batch_size for r in res])),
+                "kernel_launches": stats["kernel_launches"],
+            }
+        if i == 0:
+            out.update(block)
+        else:
+            out.setdefault("other_loads", {})[str(load)] = block
     return out
 
 
@@ -454,6 +470,70 @@ def _operands(gb, M, N, K, dev, seed, a_fmt=0, b_fmt=0):
 FORMAT_NAMES = {0: "e4m3", 1: "e5m2"}
 
 
+def occupancy_sweep(gb, dev, peak_fp8):
+    """Throughput against the number of CTAs of the persistent kernel (one
+    CTA per SM), for one fixed dense and one fixed 2:4 GEMM: the analogue of
+    the paper's throughput-vs-active-wavefronts sweep (section 4.2), with
+    the grid capped through gemm_fp8_grouped_ex."""
+    M = N = K = 8192
+    sms = gb.fp8_device_sm_count()
+    caps = sorted({c for c in (1, 2, 4, 8, 16, 32, 64, 76, 96, 128, sms) if c <= sms})
+    x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 4242)
+    del x, w
+    vals, meta = gb.prune24_compress(A)
+    n8 = _l2_copies(dev, M * K + N * K + 2 * M * N)
+    sets = []
+    for i in range(n8):
+        a, b, v, m = (A, B, vals, meta) if i == 0 else (A.clone(), B.clone(), vals.clone(), meta.clone())
+        C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+        sets.append((a, b, v, m, C, [gb.make_problem(a, b, dA, 1, dB, 1, C, 1.0, gb.OUT_BF16)],
+                     [gb.make_problem(v, b, dA, 1, dB, 1, C, 1.0, gb.OUT_BF16, A_meta=m)]))
+    rows = []
+    flops = 2.0 * M * N * K
+    for cap in caps:
+        row = {"ctas": cap}
+        for kind, idx in (("dense", 5), ("sparse", 6)):
+            ms = _time_ms([lambda p=st[idx]: gb.gemm_fp8_grouped_ex(p, cap) for st in sets])
+            row[f"{kind}_ms"] = ms
+            row[f"{kind}_tflops"] = flops / ms / 1e9
+            row[f"{kind}_frac_of_peak"] = flops / ms / 1e9 / peak_fp8
+        rows.append(row)
+    del sets
+    torch.cuda.empty_cache()
+    return {"M": M, "N": N, "K": K, "peak_fp8_tflops": peak_fp8, "operand_copies": n8,
+            "rows": rows}
+
+
+def aspect_sweep(gb, dev):
+    """Throughput against the aspect ratio M/N at fixed work (M * N = 8192^2
+    outputs, K = 4096): the analogue of the paper's shape sweep at fixed
+    total blocks (section 4.3).  FP8 dense against BF16 torch.matmul."""
+    K = 4096
+    rows = []
+    for lg in (-6, -4, -2, 0, 2, 4, 6):
+        M = int(8192 * 2.0 ** (lg / 2))
+        N = 8192 * 8192 // M
+        x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 77 + lg)
+        n8 = _l2_copies(dev, M * K + N * K + 2 * M * N)
+        sets = [(A, B, torch.empty((M, N), dtype=torch.bfloat16, device=dev))] + \
+               [(A.clone(), B.clone(), torch.empty((M, N), dtype=torch.bfloat16, device=dev))
+                for _ in range(n8 - 1)]
+        ms = _time_ms([lambda a=a, b=b, c=c: gb.gemm_fp8_dense(a, b, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=c)
+                       for a, b, c in sets])
+        del sets
+        nb = _l2_copies(dev, 2 * M * K + 2 * N * K + 2 * M * N)
+        bsets = [(x.bfloat16(), w.bfloat16()) for _ in range(nb)]
+        ms_bf16 = _time_ms([lambda xb=xb, wb=wb: torch.matmul(xb, wb.T) for xb, wb in bsets])
+        del bsets, x, w, A, B
+        torch.cuda.empty_cache()
+        flops = 2.0 * M * N * K
+        rows.append({"M": M, "N": N, "K": K, "m_over_n": M / N, "fp8_ms": ms,
+                     "fp8_tflops": flops / ms / 1e9, "bf16_ms": ms_bf16,
+                     "bf16_tflops": flops / ms_bf16 / 1e9, "speedup_vs_bf16": ms_bf16 / ms,
+                     "operand_copies": [n8, nb]})
+    return rows
+
+
 def format_sweep(gb, dev):
     """The four operand-format pairings (E4M3 / E5M2 for each operand, paper
     Table 3) on the same dense shapes, plus the quantisation rate of each
@@ -492,7 +572,28 @@ def format_sweep(gb, dev):
     return {"dense": rows, "quantize": quant}
 
 
-def sweep(gb, dev):
+SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving")
+
+
+def sweep(gb, dev, sections=SWEEP_SECTIONS):
+    """The measurement tables beyond the one-line step: `sections` picks
+    from SWEEP_SECTIONS."""
+    pk, _ = peaks()
+    out = {}
+    if "shapes" in sections:
+        out.update(shape_sweep(gb, dev))
+    if "formats" in sections:
+        out["formats"] = format_sweep(gb, dev)
+    if "occupancy" in sections:
+        out["occupancy"] = occupancy_sweep(gb, dev, pk["bf16_tflops"] * FP8_PER_BF16)
+    if "aspect" in sections:
+        out["aspect_ratio"] = aspect_sweep(gb, dev)
+    if "serving" in sections:
+        out["serving"] = serving_report(gb, dev, loads=(0.8, 0.5, 0.95))
+    return out
+
+
+def shape_sweep(gb, dev):
     """Configs 2-4: dense square and skinny vs BF16 torch.matmul, 2:4 sparse
     vs dense on the same pruned A, the transformer layer as one grouped
     persistent launch vs per-call.  Every row rotates through copies of its
@@ -593,7 +694,6 @@ def sweep(gb, dev):
         "speedup_vs_bf16_per_call": ms_bf16 / ms_graph}
     del keep
     torch.cuda.empty_cache()
-    out["formats"] = format_sweep(gb, dev)
     return out
 
 
@@ -612,7 +712,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--sweep", default=None,
-                    help="write the config 2-4 shape sweep to this JSON file and exit")
+                    help="write the measurement tables to this JSON file and exit")
+    ap.add_argument("--sections", default=",".join(SWEEP_SECTIONS),
+                    help="comma list of sweep tables: " + ", ".join(SWEEP_SECTIONS))
     ap.add_argument("--gemm", default=None,
                     help="M,N,K[,sparse][,e4m3|e5m2,e4m3|e5m2]: run only this GEMM (warmup + "
                          "steps launches; for profilers); the two formats are A's and B's")
@@ -648,7 +750,7 @@ def main():
         print(json.dumps({"gemm": args.gemm, "ms": ms, "tflops": 2.0 * M * N * K / ms / 1e9}))
         return 0
     if args.sweep:
-        res = sweep(gb, dev)
+        res = sweep(gb, dev, [t for t in args.sections.split(",") if t])
         pk, pk_kind = peaks()
         res["peaks"] = {"fp8_dense_tflops": pk["bf16_tflops"] * FP8_PER_BF16, "kind": pk_kind,
                         "hbm_gbs": pk["hbm_gbs"]}
@@ -853,6 +955,13 @@ def main():
         f, t = smp.run()
         cpu = {"value": f / t / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": smp.describe() + f", {t:.1f} s"}
+        # the same oracle on one host thread, on a smaller block
+        a1, b1 = max(1, args.cpu_rows // 32), max(1, args.cpu_cols // 16)
+        smp.orc.set_threads(1)
+        f1, t1 = smp.run(a1, b1)
+        smp.orc.set_threads(cores)
+        cpu["single_thread"] = {"value": f1 / t1 / 1e12, "unit": UNIT, "cores": 1,
+                                "sample": f"A rows [0,{a1}) x B rows [0,{b1}) at K={S}, {t1:.1f} s"}
 
     if rank == 0:
         line = {

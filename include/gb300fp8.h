@@ -412,6 +412,9 @@ typedef struct {
     double t_submit_us;       /* host clock, microseconds since server creation */
     double t_launch_us;       /* when its batch was enqueued */
     double t_end_us;          /* when the GPU finished its batch */
+    double t_start_us;        /* when the batch's stream reached it (the work
+                                 queued before it on that stream was done):
+                                 its kernels ran within [t_start_us, t_end_us] */
 } fp8_result;
 
 typedef struct {

@@ -19,7 +19,7 @@ from . import _lib
 __all__ = [
     "Fp8Error", "library", "fp8_quantize_e4m3", "fp8_quantize_e5m2", "prune24_compress",
     "prune24_decompress", "gemm_fp8_dense", "gemm_fp8_dense_fmt", "gemm_fp8_sparse24",
-    "gemm_fp8_sparse24_fmt", "gemm_fp8_grouped", "fp8_last_device_error",
+    "gemm_fp8_sparse24_fmt", "gemm_fp8_grouped", "gemm_fp8_grouped_ex", "fp8_last_device_error",
     "fp8_device_sm_count", "fp8_gemm_set_tile_config", "gemm_fp8_grouped_autotune",
     "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
     "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2",
@@ -254,6 +254,15 @@ def gemm_fp8_grouped(problems: Sequence[_lib.FP8Problem], stream=None) -> None:
     arr = (_lib.FP8Problem * len(problems))(*problems)
     rc = library().gemm_fp8_grouped(arr, len(problems), _stream(stream))
     _check(rc, "gemm_fp8_grouped")
+
+
+def gemm_fp8_grouped_ex(problems: Sequence[_lib.FP8Problem], max_ctas: int = 0,
+                        stream=None) -> None:
+    """gemm_fp8_grouped with the persistent grid capped at max_ctas CTAs
+    (0: every SM)."""
+    arr = (_lib.FP8Problem * len(problems))(*problems)
+    rc = library().gemm_fp8_grouped_ex(arr, len(problems), int(max_ctas), _stream(stream))
+    _check(rc, "gemm_fp8_grouped_ex")
 
 
 def gemm_fp8_grouped_autotune(problems: Sequence[_lib.FP8Problem], max_ctas: int = 0,

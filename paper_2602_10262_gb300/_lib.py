@@ -63,7 +63,8 @@ class FP8Request(ctypes.Structure):
 class FP8Result(ctypes.Structure):
     """Mirror of ``fp8_result``."""
     _fields_ = [("status", I32), ("batch_size", I32), ("t_submit_us", ctypes.c_double),
-                ("t_launch_us", ctypes.c_double), ("t_end_us", ctypes.c_double)]
+                ("t_launch_us", ctypes.c_double), ("t_end_us", ctypes.c_double),
+                ("t_start_us", ctypes.c_double)]
 
 
 class FP8ServerStats(ctypes.Structure):

@@ -50,7 +50,7 @@ struct Req {
     size_t ws_off = 0, ws_bytes = 0;
     int status = FP8_PENDING;
     int batch_size = 0;
-    double t_submit = 0, t_launch = 0, t_end = 0;
+    double t_submit = 0, t_launch = 0, t_start = 0, t_end = 0;
 };
 
 // workspace of a request: codes [M, ldq] then scales [M]
@@ -129,8 +129,9 @@ public:
     // Enqueue the batch on the tenant's stream; *launches = kernel launches.
     virtual int launch(int tenant, const std::vector<Req*>& batch, bool batched, int max_ctas,
                        double now_us, void** handle, int* launches) = 0;
-    // FP8_OK (finished; *t_end_us set), FP8_PENDING, or the batch's error.
-    virtual int query(void* handle, double now_us, double* t_end_us) = 0;
+    // FP8_OK (finished; *t_start_us and *t_end_us set: the batch's stream
+    // reached it, and its last kernel ended), FP8_PENDING, or the batch's error.
+    virtual int query(void* handle, double now_us, double* t_start_us, double* t_end_us) = 0;
     virtual void release(void* handle) = 0;
     virtual void shutdown() = 0;
     // Called first on the scheduler thread.
@@ -161,18 +162,20 @@ public:
             work += gflop(q);
         const double cost = launch_us_ * (batched ? 1.0 : double(batch.size())) + us_per_gflop_ * work;
         auto* b = new SimBatch;
-        b->end = std::max(now_us, busy_[tenant]) + cost;
+        b->start = std::max(now_us, busy_[tenant]);
+        b->end = b->start + cost;
         b->status = (fail_every_ > 0 && count_ % fail_every_ == 0) ? FP8_ERR_CUDA : FP8_OK;
         busy_[tenant] = b->end;
         *handle = b;
         *launches = batched ? 2 : 2 * static_cast<int>(batch.size());
         return FP8_OK;
     }
-    int query(void* handle, double now_us, double* t_end_us) override
+    int query(void* handle, double now_us, double* t_start_us, double* t_end_us) override
     {
         auto* b = static_cast<SimBatch*>(handle);
         if (now_us < b->end)
             return FP8_PENDING;
+        *t_start_us = b->start;
         *t_end_us = b->end;
         return b->status;
     }
@@ -181,7 +184,7 @@ public:
 
 private:
     struct SimBatch {
-        double end;
+        double start, end;
         int status;
     };
     double launch_us_, us_per_gflop_;
@@ -239,6 +242,14 @@ public:
         fp8_stream_t fst = reinterpret_cast<fp8_stream_t>(st);
         int rc = FP8_OK;
         *launches = 0;
+        // the start event completes when the stream reaches the batch
+        cudaEvent_t ev0 = take_event();
+        if (!ev0)
+            return FP8_ERR_CUDA;
+        if (cudaEventRecord(ev0, st) != cudaSuccess) {
+            events_.push_back(ev0);
+            return FP8_ERR_CUDA;
+        }
         if (batched) {
             std::vector<fp8_quant_job> jobs(batch.size());
             std::vector<fp8_gemm_problem> probs(batch.size());
@@ -269,31 +280,43 @@ public:
                 *launches += 2;
             }
         }
-        if (rc != FP8_OK)
+        cudaEvent_t ev1 = rc == FP8_OK ? take_event() : nullptr;
+        if (rc == FP8_OK && (!ev1 || cudaEventRecord(ev1, st) != cudaSuccess))
+            rc = FP8_ERR_CUDA;
+        if (rc != FP8_OK) {
+            events_.push_back(ev0);
+            if (ev1)
+                events_.push_back(ev1);
             return rc;
-        cudaEvent_t ev = take_event();
-        if (!ev || cudaEventRecord(ev, st) != cudaSuccess)
-            return FP8_ERR_CUDA;
-        *handle = ev;
+        }
+        *handle = new EventPair{ev0, ev1};
         return FP8_OK;
     }
 
-    int query(void* handle, double, double* t_end_us) override
+    int query(void* handle, double, double* t_start_us, double* t_end_us) override
     {
-        cudaEvent_t ev = static_cast<cudaEvent_t>(handle);
-        cudaError_t e = cudaEventQuery(ev);
+        const EventPair* b = static_cast<const EventPair*>(handle);
+        cudaError_t e = cudaEventQuery(b->end);
         if (e == cudaErrorNotReady)
             return FP8_PENDING;
         if (e != cudaSuccess)
             return FP8_ERR_CUDA;
-        float ms = 0;
-        if (cudaEventElapsedTime(&ms, epoch_, ev) != cudaSuccess)
+        float ms0 = 0, ms1 = 0;
+        if (cudaEventElapsedTime(&ms0, epoch_, b->start) != cudaSuccess ||
+            cudaEventElapsedTime(&ms1, epoch_, b->end) != cudaSuccess)
             return FP8_ERR_CUDA;
-        *t_end_us = epoch_host_us + 1e3 * static_cast<double>(ms);
+        *t_start_us = epoch_host_us + 1e3 * static_cast<double>(ms0);
+        *t_end_us = epoch_host_us + 1e3 * static_cast<double>(ms1);
         return FP8_OK;
     }
 
-    void release(void* handle) override { events_.push_back(static_cast<cudaEvent_t>(handle)); }
+    void release(void* handle) override
+    {
+        EventPair* b = static_cast<EventPair*>(handle);
+        events_.push_back(b->start);
+        events_.push_back(b->end);
+        delete b;
+    }
 
     void thread_init() override { cudaSetDevice(device_); }
 
@@ -361,6 +384,10 @@ private:
         }
         return p;
     }
+
+    struct EventPair {
+        cudaEvent_t start, end;
+    };
 
     cudaEvent_t take_event()
     {
@@ -456,12 +483,13 @@ struct fp8_server {
         for (int t = 0; t < cfg.num_tenants; ++t) {
             while (!inflight[t].empty()) {
                 Batch& b = inflight[t].front();
-                double t_end = now;
-                const int rc = exec->query(b.handle, now, &t_end);
+                double t_start = now, t_end = now;
+                const int rc = exec->query(b.handle, now, &t_start, &t_end);
                 if (rc == FP8_PENDING)
                     break;
                 for (Req* q : b.reqs) {
                     q->status = rc;
+                    q->t_start = t_start;
                     q->t_end = t_end;
                     pool.release(q->ws_off, q->ws_bytes);
                     if (rc == FP8_OK)
@@ -510,7 +538,7 @@ struct fp8_server {
                 if (rc != FP8_OK) {
                     for (Req* q : batch) {
                         q->status = rc;
-                        q->t_launch = q->t_end = now;
+                        q->t_launch = q->t_start = q->t_end = now;
                         pool.release(q->ws_off, q->ws_bytes);
                         ++stats.failed;
                     }
@@ -708,6 +736,7 @@ int collect_locked(fp8_server* s, uint64_t ticket, fp8_result* res, bool* found)
         res->t_submit_us = q->t_submit;
         res->t_launch_us = q->t_launch;
         res->t_end_us = q->t_end;
+        res->t_start_us = q->t_start;
     }
     const int st = q->status;
     s->reqs.erase(it);

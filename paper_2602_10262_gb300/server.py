@@ -30,6 +30,7 @@ class Result:
     t_submit_us: float
     t_launch_us: float
     t_end_us: float
+    t_start_us: float
 
     @property
     def latency_us(self) -> float:
@@ -37,7 +38,34 @@ class Result:
 
 
 def _result(r: _lib.FP8Result) -> Result:
-    return Result(r.status, r.batch_size, r.t_submit_us, r.t_launch_us, r.t_end_us)
+    return Result(r.status, r.batch_size, r.t_submit_us, r.t_launch_us, r.t_end_us, r.t_start_us)
+
+
+def overlap_efficiency(results) -> float:
+    """Fraction of the GPU's busy time during which two or more batches ran
+    at once (the overlap-efficiency metric of the paper, section 3.2).
+
+    Each batch runs within [t_start_us, t_end_us] of its results (requests
+    of one batch share the interval and count once).  Busy time is the
+    union of the intervals; the concurrent time is where at least two
+    intervals cover the clock.  Batches of one tenant share a stream and
+    never overlap, so overlap comes from different tenants' streams.  0.0
+    when nothing ran."""
+    spans = sorted({(r.t_start_us, r.t_end_us) for r in results if r.t_end_us > r.t_start_us})
+    events = sorted([(a, 1) for a, _ in spans] + [(b, -1) for _, b in spans],
+                    key=lambda e: (e[0], e[1]))
+    busy = both = 0.0
+    active = 0
+    prev = None
+    for t, d in events:
+        if prev is not None:
+            if active >= 1:
+                busy += t - prev
+            if active >= 2:
+                both += t - prev
+        active += d
+        prev = t
+    return both / busy if busy > 0 else 0.0
 
 
 class Server:

@@ -179,3 +179,37 @@ def test_latency_tenant_not_blocked_by_bulk_queue():
         rb = [s.wait(t, 5) for t in bulk]
         assert rl.t_end_us < max(r.t_end_us for r in rb)
         assert rl.t_end_us - rl.t_submit_us < 40000.0
+
+
+def _res(a, b):
+    from paper_2602_10262_gb300.server import Result
+    return Result(OK, 1, 0.0, 0.0, b, a)
+
+
+def test_overlap_efficiency_intervals():
+    from paper_2602_10262_gb300.server import overlap_efficiency
+    assert overlap_efficiency([]) == 0.0
+    assert overlap_efficiency([_res(0, 10), _res(5, 15)]) == pytest.approx(5 / 15)
+    assert overlap_efficiency([_res(0, 10), _res(10, 20)]) == 0.0          # touching only
+    assert overlap_efficiency([_res(0, 10), _res(0, 10)]) == 0.0          # one batch, two requests
+    assert overlap_efficiency([_res(0, 10), _res(2, 4)]) == pytest.approx(2 / 10)
+    assert overlap_efficiency([_res(0, 4), _res(1, 3), _res(2, 6), _res(8, 9)]) == pytest.approx(3 / 7)
+
+
+def test_batch_start_times_and_overlap_in_simulation():
+    from paper_2602_10262_gb300.server import overlap_efficiency
+    # 5 ms per launch; one tenant's batches queue on its stream, two tenants
+    # run side by side
+    with _server(num_tenants=2, latency_tenant=0, batching=0, simulate=(5000.0, 0.0, 0)) as s:
+        w = _weight(s)
+        t0 = [s.submit(0, w, 8, FAKE, 4096, FAKE, 4096) for _ in range(3)]
+        rs0 = [s.wait(t, 5) for t in t0]
+        for r in rs0:
+            assert r.t_launch_us <= r.t_start_us < r.t_end_us
+            assert r.t_end_us - r.t_start_us >= 4999.0
+        spans = sorted((r.t_start_us, r.t_end_us) for r in rs0)
+        assert all(spans[i][1] <= spans[i + 1][0] for i in range(2))    # serialised
+        assert overlap_efficiency(rs0) == 0.0
+        both = [s.submit(k % 2, w, 8, FAKE, 4096, FAKE, 4096) for k in range(4)]
+        rs = [s.wait(t, 5) for t in both]
+        assert overlap_efficiency(rs) > 0.5
