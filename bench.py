@@ -504,6 +504,177 @@ def occupancy_sweep(gb, dev, peak_fp8):
             "rows": rows}
 
 
+class _Span:
+    def __init__(self, a, b):
+        self.t_start_us, self.t_end_us = a, b
+
+
+def _concurrent(graphs, streams):
+    """Replay graphs[i] on streams[i], all released together by one event;
+    returns (per-stream [start, end] in ms from the release, makespan ms)."""
+    cur = torch.cuda.current_stream()
+    go = torch.cuda.Event(enable_timing=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in graphs]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in graphs]
+    torch.cuda.synchronize()
+    go.record(cur)
+    for g, st, e0, e1 in zip(graphs, streams, starts, ends):
+        st.wait_event(go)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            g.replay()
+            e1.record(st)
+    for st in streams:
+        cur.wait_stream(st)
+    torch.cuda.synchronize()
+    spans = [(go.elapsed_time(a), go.elapsed_time(b)) for a, b in zip(starts, ends)]
+    return spans, max(b for _, b in spans)
+
+
+def _capture(fn, iters, stream):
+    """fn(stream) `iters` times captured into one CUDA graph on `stream`."""
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            fn(stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for _ in range(iters):
+            fn(stream)
+    torch.cuda.synchronize()
+    return g
+
+
+def _concurrency_stats(spans, makespan, iso_ms):
+    """The paper's concurrency metrics (sections 3.2, 5, 6.2) for one run:
+    speedup = serial time of the same work / makespan; per-stream times,
+    their CV, fairness 1 - (max - min) / mean and min / max; overlap
+    efficiency = share of busy time with two or more streams active."""
+    from paper_2602_10262_gb300.server import overlap_efficiency
+    t = np.array([b - a for a, b in spans])
+    return {"streams": len(spans), "makespan_ms": makespan, "serial_ms": float(sum(iso_ms)),
+            "speedup": float(sum(iso_ms) / makespan),
+            "per_stream_ms": [float(v) for v in t],
+            "per_stream_speedup": [float(i / v) for i, v in zip(iso_ms, t)],
+            "cv": float(t.std() / t.mean()), "fairness_1_minus_range_over_mean":
+                float(1.0 - (t.max() - t.min()) / t.mean()),
+            "fairness_min_over_max": float(t.min() / t.max()),
+            "overlap_efficiency": overlap_efficiency([_Span(a * 1e3, b * 1e3) for a, b in spans],
+                                                     one_per_interval=False)}
+
+
+def concurrency_sweep(gb, dev, iters=100, trials=5):
+    """The paper's concurrency experiments replayed on GB300 streams: each
+    stream replays a CUDA graph of `iters` GEMMs (so host issue does not
+    limit it), all streams released by one event; medians over `trials`.
+      - streams: 1, 2, 4, 8 streams of 512^3 GEMMs, FP8 dense, FP8 2:4 and
+        BF16 torch.matmul (section 5.1), and dense/sparse alternating
+        ("mixed", section 6.2);
+      - fragmentation: pairs 512^3 + 512^3, 1024^3 + 512^3, 2048^3 + 512^3
+        (section 5.3), unpartitioned and with the SMs split between the two
+        streams in proportion to their work (grid caps via
+        gemm_fp8_grouped_ex: occupancy-matched co-scheduling, section 8.2);
+      - transformer: two instances of the transformer layer (grouped,
+        graph-captured) on two streams against one after the other
+        (section 7.2)."""
+    sms = gb.fp8_device_sm_count()
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    keep = []
+
+    def dense_fn(n, seed, max_ctas=0):
+        x, w, A, dA, B, dB = _operands(gb, n, n, n, dev, seed)
+        C = torch.empty((n, n), dtype=torch.bfloat16, device=dev)
+        keep.extend([A, dA, B, dB, C])
+        pr = [gb.make_problem(A, B, dA, 1, dB, 1, C, 1.0, gb.OUT_BF16)]
+        return lambda st: gb.gemm_fp8_grouped_ex(pr, max_ctas, stream=st)
+
+    def sparse_fn(n, seed):
+        x, w, A, dA, B, dB = _operands(gb, n, n, n, dev, seed)
+        vals, meta = gb.prune24_compress(A)
+        C = torch.empty((n, n), dtype=torch.bfloat16, device=dev)
+        keep.extend([vals, meta, dA, B, dB, C])
+        return lambda st: gb.gemm_fp8_sparse24(vals, meta, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C,
+                                               stream=st)
+
+    def bf16_fn(n, seed):
+        g = torch.Generator(device=dev).manual_seed(seed)
+        xb = torch.randn((n, n), generator=g, device=dev).bfloat16()
+        wb = torch.randn((n, n), generator=g, device=dev).bfloat16()
+        C = torch.empty((n, n), dtype=torch.bfloat16, device=dev)
+        keep.extend([xb, wb, C])
+        return lambda st: torch.matmul(xb, wb.T, out=C)
+
+    def run(fns, iso=None, n_iter=iters):
+        graphs = [_capture(f, n_iter, streams[i]) for i, f in enumerate(fns)]
+        if iso is None:                                  # each graph alone
+            iso = [float(np.median([_concurrent([g], [streams[i]])[1] for _ in range(trials)]))
+                   for i, g in enumerate(graphs)]
+        _concurrent(graphs, streams[:len(graphs)])       # warm-up
+        res = [_concurrency_stats(*_concurrent(graphs, streams[:len(graphs)]), iso)
+               for _ in range(trials)]
+        med = {}
+        for k, v in res[0].items():
+            if isinstance(v, float):
+                med[k] = float(np.median([r[k] for r in res]))
+            elif isinstance(v, list):
+                med[k] = [float(np.median([r[k][i] for r in res])) for i in range(len(v))]
+            else:
+                med[k] = v
+        del graphs
+        return med, iso
+
+    out = {"iters_per_stream": iters, "trials": trials, "streams": [], "fragmentation": []}
+    n = 512
+    makers = {"fp8_dense": lambda i: dense_fn(n, 1000 + i), "fp8_sparse": lambda i: sparse_fn(n, 1000 + i),
+              "bf16": lambda i: bf16_fn(n, 1000 + i),
+              "fp8_mixed": lambda i: dense_fn(n, 1000 + i) if i % 2 == 0 else sparse_fn(n, 1000 + i)}
+    for kind, mk in makers.items():
+        fns = [mk(i) for i in range(8)]
+        iso1 = None
+        for ns in (1, 2, 4, 8):
+            if kind == "fp8_mixed" and ns > 4:
+                continue
+            med, iso = run(fns[:ns])
+            iso1 = iso if iso1 is None else iso1
+            med.update({"kind": kind, "n": n, "gflops_aggregate": 2.0 * n ** 3 * iters * ns / med["makespan_ms"] / 1e6})
+            out["streams"].append(med)
+    for big in (512, 1024, 2048):
+        work = [big ** 3, n ** 3]
+        share = max(1, min(sms - 1, round(sms * work[0] / sum(work))))
+        for mode, caps in (("shared", (0, 0)), ("partitioned", (share, sms - share))):
+            fns = [dense_fn(big, 2000 + big, caps[0]), dense_fn(n, 2001, caps[1])]
+            iso = None
+            if mode == "partitioned":
+                iso = out["fragmentation"][-1]["isolated_ms"]      # unpartitioned, alone
+            med, iso = run(fns, iso)
+            med.update({"pair": [big, n], "ratio": f"{big ** 3 // n ** 3}:1" if big > n else "1:1",
+                        "mode": mode, "ctas": list(caps), "isolated_ms": iso})
+            out["fragmentation"].append(med)
+    # two transformer-layer instances
+    inst = []
+    flops = 0.0
+    for r in range(2):
+        probs = []
+        for i, (name, M, N, K) in enumerate(workloads.TRANSFORMER_LAYER):
+            x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 3000 + 10 * r + i)
+            del x, w
+            C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+            keep.extend([A, dA, B, dB, C])
+            probs.append(gb.make_problem(A, B, dA, 1, dB, 1, C, 1.0, gb.OUT_BF16))
+            if r == 0:
+                flops += 2.0 * M * N * K
+        inst.append(lambda st, p=probs: gb.gemm_fp8_grouped(p, stream=st))
+    tf_iters = 10
+    med, iso = run(inst, n_iter=tf_iters)
+    med.update({"gflop_per_layer": flops / 1e9, "layers_per_instance": tf_iters,
+                "aggregate_tflops": 2 * flops * tf_iters / med["makespan_ms"] / 1e9,
+                "isolated_ms": iso})
+    out["transformer_two_instances"] = med
+    del keep
+    torch.cuda.empty_cache()
+    return out
+
+
 def aspect_sweep(gb, dev):
     """Throughput against the aspect ratio M/N at fixed work (M * N = 8192^2
     outputs, K = 4096): the analogue of the paper's shape sweep at fixed
@@ -572,7 +743,7 @@ def format_sweep(gb, dev):
     return {"dense": rows, "quantize": quant}
 
 
-SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving")
+SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency")
 
 
 def sweep(gb, dev, sections=SWEEP_SECTIONS):
@@ -590,6 +761,8 @@ def sweep(gb, dev, sections=SWEEP_SECTIONS):
         out["aspect_ratio"] = aspect_sweep(gb, dev)
     if "serving" in sections:
         out["serving"] = serving_report(gb, dev, loads=(0.8, 0.5, 0.95))
+    if "concurrency" in sections:
+        out["concurrency"] = concurrency_sweep(gb, dev)
     return out
 
 

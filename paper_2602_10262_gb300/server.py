@@ -41,7 +41,7 @@ def _result(r: _lib.FP8Result) -> Result:
     return Result(r.status, r.batch_size, r.t_submit_us, r.t_launch_us, r.t_end_us, r.t_start_us)
 
 
-def overlap_efficiency(results) -> float:
+def overlap_efficiency(results, one_per_interval: bool = True) -> float:
     """Fraction of the GPU's busy time during which two or more batches ran
     at once (the overlap-efficiency metric of the paper, section 3.2).
 
@@ -50,8 +50,11 @@ def overlap_efficiency(results) -> float:
     union of the intervals; the concurrent time is where at least two
     intervals cover the clock.  Batches of one tenant share a stream and
     never overlap, so overlap comes from different tenants' streams.  0.0
-    when nothing ran."""
-    spans = sorted({(r.t_start_us, r.t_end_us) for r in results if r.t_end_us > r.t_start_us})
+    when nothing ran.  one_per_interval=False counts identical intervals
+    separately (for intervals that are not requests of one batch)."""
+    spans = [(r.t_start_us, r.t_end_us) for r in results if r.t_end_us > r.t_start_us]
+    if one_per_interval:
+        spans = sorted(set(spans))
     events = sorted([(a, 1) for a, _ in spans] + [(b, -1) for _, b in spans],
                     key=lambda e: (e[0], e[1]))
     busy = both = 0.0

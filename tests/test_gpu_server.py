@@ -75,6 +75,22 @@ def test_mix_equals_alone_bitwise(gb, setup, cfg):
         assert stats["kernel_launches"] == 2 * len(outs)
 
 
+@pytest.mark.parametrize("batching", [True, False])
+def test_batch_intervals(gb, setup, batching):
+    """Device start and end of each batch: start <= end; the batches of one
+    tenant share a stream and do not overlap (1 us of clock-mapping slack);
+    requests of one batch share the interval."""
+    from paper_2602_10262_gb300.server import overlap_efficiency
+    _, res, _ = _serve(gb, setup, batching=batching)
+    for r in res:
+        assert r.t_start_us <= r.t_end_us
+    for t in (0, 1):
+        spans = sorted({(r.t_start_us, r.t_end_us) for i, r in enumerate(res) if i % 2 == t})
+        for (a0, b0), (a1, b1) in zip(spans, spans[1:]):
+            assert a1 >= b0 - 1.0, (t, spans)
+    assert 0.0 <= overlap_efficiency(res) <= 1.0
+
+
 def test_server_results_vs_oracle(gb, orc, setup):
     outs, _, _ = _serve(gb, setup, batching=True)
     Wd = setup["Wd"].cpu().numpy()
