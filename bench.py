@@ -571,9 +571,10 @@ def concurrency_sweep(gb, dev, iters=100, trials=5):
         BF16 torch.matmul (section 5.1), and dense/sparse alternating
         ("mixed", section 6.2);
       - fragmentation: pairs 512^3 + 512^3, 1024^3 + 512^3, 2048^3 + 512^3
-        (section 5.3), unpartitioned and with the SMs split between the two
-        streams in proportion to their work (grid caps via
-        gemm_fp8_grouped_ex: occupancy-matched co-scheduling, section 8.2);
+        (section 5.3), sharing the SMs freely and with 24 SMs reserved for
+        the small stream (the larger GEMM's grid capped at SMs - 24 through
+        gemm_fp8_grouped_ex, as the server's co-scheduled mode does;
+        occupancy-aware co-scheduling, section 8.2);
       - transformer: two instances of the transformer layer (grouped,
         graph-captured) on two streams against one after the other
         (section 7.2)."""
@@ -629,25 +630,22 @@ def concurrency_sweep(gb, dev, iters=100, trials=5):
               "bf16": lambda i: bf16_fn(n, 1000 + i),
               "fp8_mixed": lambda i: dense_fn(n, 1000 + i) if i % 2 == 0 else sparse_fn(n, 1000 + i)}
     for kind, mk in makers.items():
-        fns = [mk(i) for i in range(8)]
-        iso1 = None
+        fns = [mk(i) for i in range(4 if kind == "fp8_mixed" else 8)]
         for ns in (1, 2, 4, 8):
-            if kind == "fp8_mixed" and ns > 4:
+            if ns > len(fns):
                 continue
-            med, iso = run(fns[:ns])
-            iso1 = iso if iso1 is None else iso1
+            med, _ = run(fns[:ns])
             med.update({"kind": kind, "n": n, "gflops_aggregate": 2.0 * n ** 3 * iters * ns / med["makespan_ms"] / 1e6})
             out["streams"].append(med)
+    reserve = min(24, sms // 2)
     for big in (512, 1024, 2048):
-        work = [big ** 3, n ** 3]
-        share = max(1, min(sms - 1, round(sms * work[0] / sum(work))))
-        for mode, caps in (("shared", (0, 0)), ("partitioned", (share, sms - share))):
+        for mode, caps in (("shared", (0, 0)), ("reserved", (sms - reserve, reserve))):
             fns = [dense_fn(big, 2000 + big, caps[0]), dense_fn(n, 2001, caps[1])]
             iso = None
-            if mode == "partitioned":
-                iso = out["fragmentation"][-1]["isolated_ms"]      # unpartitioned, alone
+            if mode == "reserved":
+                iso = out["fragmentation"][-1]["isolated_ms"]      # uncapped, alone
             med, iso = run(fns, iso)
-            med.update({"pair": [big, n], "ratio": f"{big ** 3 // n ** 3}:1" if big > n else "1:1",
+            med.update({"pair": [big, n], "ratio": f"{big // n}:1",
                         "mode": mode, "ctas": list(caps), "isolated_ms": iso})
             out["fragmentation"].append(med)
     # two transformer-layer instances
