@@ -327,3 +327,26 @@ def test_dependent_chain_back_to_back_equals_synchronised(gb, M, N, K):
         h, y = chain(False)
         assert torch.equal(h, h_ref) and torch.equal(y, y_ref)
     assert gb.fp8_last_device_error() == 0
+
+
+def _int_values(shape, seed):
+    """The integers behind workloads.small_int_codes(shape, seed) (same draw)."""
+    return workloads.randint_f32(shape, seed, -4, 4).astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 262144), (16, 2048, 131072), (1, 4096, 131072),
+                                   (1 << 20, 16, 128), (16, 1 << 20, 128), (3, 5, 262160)])
+def test_extreme_shapes_small_integers_exact(gb, orc, M, N, K):
+    """Very long K (split-K over many k-blocks; partial sums up to 4.2e6,
+    still exact in FP32), a million-row M or N (8192 tiles; the swapped
+    skinny path for N), and a ragged long K: every entry equals the integer
+    product (float64 BLAS on the integers is exact below 2^53), and sampled
+    entries equal the oracle's."""
+    A = workloads.small_int_codes((M, K), seed=M + 11)
+    B = workloads.small_int_codes((N, K), seed=N + 12)
+    one = np.ones(1, np.float32)
+    C = _gemm(gb, A, B, one, 0, one, 0, 1.0, gb.OUT_F32)
+    exact = _int_values((M, K), M + 11) @ _int_values((N, K), N + 12).T
+    assert np.array_equal(C.astype(np.float64), exact)
+    ms, ns = workloads.sample_pairs(M, N, 256, seed=9)
+    assert np.array_equal(C[ms, ns].astype(np.float64), orc.gemm_sampled(A, B, one, 0, one, 0, 1.0, ms, ns))

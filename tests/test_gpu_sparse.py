@@ -164,3 +164,21 @@ def test_sparse_small_integers_mt2_bit_exact(gb, orc, tile_cfg):
     tile_cfg(2, 0)
     C = _sparse(gb, vals, meta, B, one, 0, one, 0, 1.0, gb.OUT_F32)
     assert np.array_equal(C.astype(np.float64), orc.gemm_sparse24(vals, meta, B, 1024, one, 0, one, 0))
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 128, 262144), (128, 16, 131072), (1 << 19, 16, 128)])
+def test_sparse_extreme_shapes_small_integers_exact(gb, orc, M, N, K):
+    """2:4 products at very long K and at half a million rows: every entry
+    equals the integer product of the pruned matrix with B, sampled entries
+    equal the oracle's."""
+    A = workloads.small_int_codes((M, K), seed=M + 21)
+    B = workloads.small_int_codes((N, K), seed=N + 22)
+    vals, meta = orc.prune24(A)
+    one = np.ones(1, np.float32)
+    C = _sparse(gb, vals, meta, B, one, 0, one, 0, 1.0, gb.OUT_F32)
+    Ap = orc.decompress24(vals, meta, K)
+    exact = torch.from_numpy(Ap).view(torch.float8_e4m3fn).double().numpy() @ \
+        workloads.randint_f32((N, K), N + 22, -4, 4).astype(np.float64).T
+    assert np.array_equal(C.astype(np.float64), exact)
+    ms, ns = workloads.sample_pairs(M, N, 256, seed=10)
+    assert np.array_equal(C[ms, ns].astype(np.float64), orc.gemm_sampled(Ap, B, one, 0, one, 0, 1.0, ms, ns))
