@@ -438,13 +438,21 @@ int fp8_server_create_simulated(const fp8_server_config *cfg, double launch_us,
  * frees the pool and streams. */
 int fp8_server_destroy(fp8_server *srv);
 
-/* Registers a resident weight: W E4M3 [N, K] (row stride ldw) for dense, or
+/* Registers a resident E4M3 weight: W [N, K] (row stride ldw) for dense, or
  * the 2:4 pair (W = kept codes [N, K/2], W_meta = metadata [N, K/8], K %
  * 128 == 0) when W_meta != NULL; w_scale fp32 [1] (w_mode 0) or [N]
  * (w_mode 1).  K % 16 == 0. */
 int fp8_server_register_weight(fp8_server *srv, int64_t N, int64_t K, const uint8_t *W, int64_t ldw,
                                const uint8_t *W_meta, const float *w_scale, int w_mode,
                                uint64_t *handle);
+
+/* fp8_server_register_weight for weights stored as w_format (an
+ * fp8_format; FP8_ERR_INVALID otherwise).  Requests against it quantise
+ * their activations to E4M3 as always, so an E5M2 weight runs the E4M3 x
+ * E5M2 pairing (paper Table 3's FP8 x BF8) on the same kernels. */
+int fp8_server_register_weight_fmt(fp8_server *srv, int64_t N, int64_t K, const uint8_t *W,
+                                   int64_t ldw, const uint8_t *W_meta, const float *w_scale,
+                                   int w_mode, int w_format, uint64_t *handle);
 
 /* Queues a request; *ticket identifies it.  FP8_ERR_OOM if its workspace
  * can never fit in the pool; FP8_ERR_INVALID / FP8_ERR_SHAPE for bad

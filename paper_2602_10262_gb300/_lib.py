@@ -110,6 +110,8 @@ SIGNATURES = {
     "fp8_server_destroy": (I32, [P]),
     "fp8_server_register_weight": (I32, [P, I64, I64, P, I64, P, P, I32,
                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "fp8_server_register_weight_fmt": (I32, [P, I64, I64, P, I64, P, P, I32, I32,
+                                             ctypes.POINTER(ctypes.c_uint64)]),
     "fp8_server_submit": (I32, [P, ctypes.POINTER(FP8Request), ctypes.POINTER(ctypes.c_uint64)]),
     "fp8_server_poll": (I32, [P, ctypes.c_uint64, ctypes.POINTER(FP8Result)]),
     "fp8_server_wait": (I32, [P, ctypes.c_uint64, ctypes.POINTER(FP8Result), ctypes.c_double]),

@@ -41,6 +41,7 @@ struct Weight {
     const uint8_t* meta = nullptr;
     const float* scale = nullptr;
     int mode = 0;
+    int format = FP8_E4M3;      // fp8_format of the weight codes
 };
 
 struct Req {
@@ -269,12 +270,14 @@ public:
                     break;
                 const fp8_gemm_problem p = problem(q);
                 if (p.A_meta)
-                    rc = gemm_fp8_sparse24(p.M, p.N, p.K, p.A, p.A_meta, p.B, p.ldb, p.a_scale, p.a_mode,
-                                           p.b_scale, p.b_mode, p.alpha, p.C, p.ldc, p.out_dtype,
-                                           p.out_transposed, fst);
+                    rc = gemm_fp8_sparse24_fmt(p.M, p.N, p.K, p.A, p.A_meta, p.B, p.ldb, p.a_scale,
+                                               p.a_mode, p.b_scale, p.b_mode, p.alpha, p.C, p.ldc,
+                                               p.out_dtype, p.out_transposed, p.a_format, p.b_format,
+                                               fst);
                 else
-                    rc = gemm_fp8_dense(p.M, p.N, p.K, p.A, p.lda, p.B, p.ldb, p.a_scale, p.a_mode,
-                                        p.b_scale, p.b_mode, p.alpha, p.C, p.ldc, p.out_dtype, fst);
+                    rc = gemm_fp8_dense_fmt(p.M, p.N, p.K, p.A, p.lda, p.B, p.ldb, p.a_scale, p.a_mode,
+                                            p.b_scale, p.b_mode, p.alpha, p.C, p.ldc, p.out_dtype,
+                                            p.a_format, p.b_format, fst);
                 if (rc != FP8_OK)
                     break;
                 *launches += 2;
@@ -374,12 +377,14 @@ private:
             p.A = q->w.W, p.A_meta = q->w.meta, p.lda = q->w.K / 2;
             p.a_scale = q->w.scale, p.a_mode = q->w.mode;
             p.B = j.q, p.ldb = j.ldq, p.b_scale = j.dequant_scale, p.b_mode = 1;
+            p.a_format = q->w.format, p.b_format = FP8_E4M3;
             p.out_transposed = 1;
         } else {
             p.M = q->r.M, p.N = q->w.N;
             p.A = j.q, p.A_meta = nullptr, p.lda = j.ldq;
             p.a_scale = j.dequant_scale, p.a_mode = 1;
             p.B = q->w.W, p.ldb = q->w.ldw, p.b_scale = q->w.scale, p.b_mode = q->w.mode;
+            p.a_format = FP8_E4M3, p.b_format = q->w.format;
             p.out_transposed = 0;
         }
         return p;
@@ -662,7 +667,15 @@ extern "C" int fp8_server_register_weight(fp8_server* s, int64_t N, int64_t K, c
                                           int64_t ldw, const uint8_t* W_meta, const float* w_scale,
                                           int w_mode, uint64_t* handle)
 {
-    if (!s || !W || !w_scale || !handle || (w_mode != 0 && w_mode != 1))
+    return fp8_server_register_weight_fmt(s, N, K, W, ldw, W_meta, w_scale, w_mode, FP8_E4M3, handle);
+}
+
+extern "C" int fp8_server_register_weight_fmt(fp8_server* s, int64_t N, int64_t K, const uint8_t* W,
+                                              int64_t ldw, const uint8_t* W_meta, const float* w_scale,
+                                              int w_mode, int w_format, uint64_t* handle)
+{
+    if (!s || !W || !w_scale || !handle || (w_mode != 0 && w_mode != 1) ||
+        (w_format != FP8_E4M3 && w_format != FP8_E5M2))
         return FP8_ERR_INVALID;
     if (N <= 0 || K <= 0 || K % 16 != 0 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
         return FP8_ERR_SHAPE;
@@ -674,7 +687,7 @@ extern "C" int fp8_server_register_weight(fp8_server* s, int64_t N, int64_t K, c
     }
     Weight w;
     w.N = N, w.K = K, w.ldw = W_meta ? K / 2 : ldw, w.W = W, w.meta = W_meta, w.scale = w_scale,
-    w.mode = w_mode;
+    w.mode = w_mode, w.format = w_format;
     std::lock_guard<std::mutex> lk(s->mu);
     s->weights.push_back(w);
     *handle = s->weights.size();                 // 1-based

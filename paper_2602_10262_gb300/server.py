@@ -113,9 +113,9 @@ class Server:
             pass
 
     def register_weight(self, N: int, K: int, W, w_scale, w_mode: int, W_meta=None,
-                        ldw: Optional[int] = None) -> int:
+                        ldw: Optional[int] = None, w_format: int = 0) -> int:
         """W / W_meta / w_scale: CUDA tensors (kept alive by the server object)
-        or raw integer device addresses."""
+        or raw integer device addresses.  w_format: 0 = E4M3, 1 = E5M2 codes."""
         def ptr(t):
             if t is None:
                 return None
@@ -126,10 +126,11 @@ class Server:
         if ldw is None:
             ldw = W.stride(0) if isinstance(W, torch.Tensor) and W_meta is None else K
         hdl = ctypes.c_uint64()
-        rc = self.lib.fp8_server_register_weight(self.h, N, K, ptr(W), ldw, ptr(W_meta),
-                                                 ptr(w_scale), w_mode, ctypes.byref(hdl))
+        rc = self.lib.fp8_server_register_weight_fmt(self.h, N, K, ptr(W), ldw, ptr(W_meta),
+                                                     ptr(w_scale), w_mode, int(w_format),
+                                                     ctypes.byref(hdl))
         if rc != 0:
-            raise ServerError(rc, "fp8_server_register_weight")
+            raise ServerError(rc, "fp8_server_register_weight_fmt")
         return hdl.value
 
     def submit(self, tenant: int, weight: int, M: int, x, ldx: int, out, ldo: int,

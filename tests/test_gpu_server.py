@@ -117,3 +117,52 @@ def test_server_pool_from_free_memory(gb):
     with Server(num_tenants=1, latency_tenant=-1, reserve_bytes=reserve) as srv:
         st = srv.stats()
         assert 0 < st["pool_bytes"] <= free - reserve + (1 << 20)
+
+
+@pytest.fixture(scope="module")
+def setup_e5m2(gb, setup):
+    """The same requests against E5M2 weights (dense and 2:4)."""
+    K = setup["K"]
+    dev = torch.device("cuda")
+    w_dense = torch.from_numpy(workloads.randn_f32((1024, K), seed=61)).to(dev)
+    w_sparse = torch.from_numpy(workloads.randn_f32((768, K), seed=62)).to(dev)
+    Wd, dWd = gb.fp8_quantize_e5m2(w_dense, 1)
+    Ws, dWs = gb.fp8_quantize_e5m2(w_sparse, 1)
+    vals, meta = gb.prune24_compress(Ws)
+    torch.cuda.synchronize()
+    return dict(setup, Wd=Wd, dWd=dWd, vals=vals, meta=meta, dWs=dWs)
+
+
+@pytest.mark.parametrize("batching", [True, False])
+def test_e5m2_weights_equal_direct_calls_bitwise(gb, orc, setup_e5m2, batching):
+    """Requests against E5M2 weights (E4M3 activations x E5M2 weights, the
+    FP8 x BF8 pairing) equal direct format-aware calls bit for bit, and a
+    dense one matches the oracle."""
+    from paper_2602_10262_gb300.server import Server
+    S = setup_e5m2
+    outs, tickets = [], []
+    with Server(num_tenants=2, latency_tenant=0, batching=batching, pool_bytes=256 << 20) as srv:
+        hd = srv.register_weight(1024, S["K"], S["Wd"], S["dWd"], 1, w_format=1)
+        hs = srv.register_weight(768, S["K"], S["vals"], S["dWs"], 1, W_meta=S["meta"], w_format=1)
+        for i, (m, x) in enumerate(zip(S["Ms"], S["xs"])):
+            sparse = i % 2 == 1
+            N = 768 if sparse else 1024
+            out = torch.empty((m, N), dtype=torch.bfloat16, device="cuda")
+            outs.append(out)
+            tickets.append(srv.submit(i % 2, hs if sparse else hd, m, x, x.stride(0), out, N))
+        res = [srv.wait(t, 30) for t in tickets]
+    assert all(r is not None and r.status == 0 for r in res)
+    for i, out in enumerate(outs):
+        q, d = gb.fp8_quantize_e4m3(S["xs"][i], 1)
+        if i % 2:
+            ref = gb.gemm_fp8_sparse24_fmt(S["vals"], S["meta"], q, S["dWs"], 1, d, 1, 1.0, gb.OUT_BF16,
+                                           True, gb.E5M2, gb.E4M3)
+        else:
+            ref = gb.gemm_fp8_dense_fmt(q, S["Wd"], d, 1, S["dWd"], 1, 1.0, gb.OUT_BF16, gb.E4M3, gb.E5M2)
+        assert torch.equal(out, ref), f"request {i}"
+    x = S["xs"][4].cpu().numpy()
+    qo, do = orc.quantize(x, 1)
+    Wd, dWd = S["Wd"].cpu().numpy(), S["dWd"].cpu().numpy()
+    ref = orc.gemm(qo, Wd, do, 1, dWd, 1, a_fmt=0, b_fmt=1)
+    Sm = orc.gemm(parity.abs_codes(qo), parity.abs_codes(Wd), do, 1, dWd, 1, a_fmt=0, b_fmt=1)
+    parity.check_bf16(outs[4].float().cpu().numpy(), ref, Sm, S["K"])

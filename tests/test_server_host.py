@@ -133,6 +133,13 @@ def test_bad_arguments():
             s.register_weight(4096, 100, FAKE, FAKE, 1)        # K % 16 != 0
         with pytest.raises(ServerError):
             s.register_weight(4096, 4112, FAKE, FAKE, 1, W_meta=FAKE)   # sparse K % 128
+        for bad in (2, -1):
+            with pytest.raises(ServerError) as e:
+                s.register_weight(4096, 4096, FAKE, FAKE, 1, w_format=bad)   # not E4M3 / E5M2
+            assert e.value.status == ERR_INVALID
+        w5 = s.register_weight(4096, 4096, FAKE, FAKE, 1, w_format=1)        # E5M2 accepted
+        r = s.wait(s.submit(0, w5, 4, FAKE, 4096, FAKE, 4096), 5)
+        assert r.status == OK
     with pytest.raises(ServerError):
         Server(num_tenants=0, simulate=(1, 0, 0))
 
