@@ -175,10 +175,12 @@ def test_concurrent_submitters():
 
 
 def test_latency_tenant_not_blocked_by_bulk_queue():
-    # the bulk tenant's stream is busy for a long time; the latency tenant has
-    # its own stream and slots, so its request finishes first
+    # the bulk tenant's stream is busy for a long time (30 ms per launch plus
+    # 10 ms per GFLOP: >= 51 ms for a 2.1-GFLOP request, however the three
+    # are batched); the latency tenant has its own stream and slots, so its
+    # 0.03-GFLOP request finishes first
     with _server(num_tenants=2, latency_tenant=0, max_inflight=1,
-                 simulate=(30000.0, 0.0, 0)) as s:
+                 simulate=(30000.0, 10000.0, 0)) as s:
         w = _weight(s)
         bulk = [s.submit(1, w, 64, FAKE, 4096, FAKE, 4096) for _ in range(3)]
         lat = s.submit(0, w, 1, FAKE, 4096, FAKE, 4096)
