@@ -212,13 +212,15 @@ int gemm_fp8_dense_fmt(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_
  *
  * Limits and caveats:
  *   - a problem whose split-K scratch exceeds 4 MiB is rejected with
- *     FP8_ERR_SHAPE and nothing is launched.  The scratch is
- *     256 bytes of counters plus tiles x slices x 128 x (N-tile width)
- *     floats, with tiles x slices at most the SM count (only products with
- *     M <= 128 split): skinny products with M <= 32 always fit; wider ones
- *     fit while that total stays within 4 MiB (M = 64 with a long side of
- *     4864 rows and K = 8192, split in four, needs 4.98 MB and is
- *     rejected).  Problems that do not split need none and always run;
+ *     FP8_ERR_SHAPE and nothing is launched.  Only products with M <= 128
+ *     (or N <= 128) and K >= 4096 split; when the slices of each tile add
+ *     up within a thread-block cluster (the other slices' partial sums fit
+ *     in a CTA's shared-memory ring) they need no scratch.  Otherwise the
+ *     scratch is 256 bytes of counters plus tiles x slices x 128 x (N-tile
+ *     width) floats, tiles x slices at most the SM count: skinny products
+ *     with M <= 32 always fit; M = 64 with a long side of 2432 rows and
+ *     K = 8192, split in eight, needs 4.98 MB and is rejected.  Problems
+ *     that do not split need none and always run;
  *   - all calls on a device share the array, which keeps the previous call's
  *     contents; each call zeroes the counters it needs (cudaMemsetAsync, not
  *     an allocation).  Calls whose kernels overlap on the GPU (for example on

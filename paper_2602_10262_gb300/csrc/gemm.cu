@@ -1847,7 +1847,8 @@ extern "C" int gemm_fp8_dense_noalloc(int64_t M, int64_t N, int64_t K, const uin
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     Plan pl;
-    rc = build_plan(prm, &j, &bn, 1, 0, nullptr, &pl);
+    // slices that add up within a cluster need no scratch at all
+    rc = build_plan(prm, &j, &bn, 1, 0, nullptr, &pl, true);
     if (rc != FP8_OK)
         return rc;
     const size_t bytes = workspace_bytes(pl);

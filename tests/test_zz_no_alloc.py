@@ -32,10 +32,13 @@ def _args(A, B, sa, sb, C):
             sb.data_ptr(), 1, 1.0, C.data_ptr(), C.stride(0), 0, st)
 
 
-@pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (8, 8192, 4096), (512, 512, 1024)])
+@pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (8, 8192, 4096), (64, 1280, 8192),
+                                   (512, 512, 1024)])
 def test_noalloc_matches_dense_two_calls(lib, M, N, K):
-    # (16, 4096, 4096) and (8, 8192, 4096) split K through the scratch array;
-    # (512, 512, 1024) does not split and needs no scratch
+    # (16, 4096, 4096) and (8, 8192, 4096) split K and add the slices up
+    # within clusters (no scratch); (64, 1280, 8192) splits in eight, whose
+    # partial sums exceed a CTA's ring, so it goes through the scratch array
+    # (2.6 MB); (512, 512, 1024) does not split
     dev = torch.device("cuda")
     A = torch.from_numpy(workloads.random_codes((M, K), seed=M)).to(dev)
     B = torch.from_numpy(workloads.random_codes((N, K), seed=N)).to(dev)
@@ -52,10 +55,12 @@ def test_noalloc_matches_dense_two_calls(lib, M, N, K):
 
 
 def test_noalloc_rejects_scratch_beyond_the_array(lib):
-    # 38 tiles of 64-wide N split in four: 152 x 128 x 64 floats (4.98 MB)
-    # exceed the 4 MiB array -> a clear FP8_ERR_SHAPE, nothing launched
+    # 19 tiles of 64-wide N split in eight: seven slices' partial sums
+    # (224 KB) exceed a CTA's ring, so no cluster; 152 x 128 x 64 floats
+    # (4.98 MB) exceed the 4 MiB array -> a clear FP8_ERR_SHAPE, nothing
+    # launched
     dev = torch.device("cuda")
-    M, N, K = 64, 4864, 8192
+    M, N, K = 64, 2432, 8192
     A = torch.zeros((M, K), dtype=torch.uint8, device=dev)
     B = torch.zeros((N, K), dtype=torch.uint8, device=dev)
     s = torch.ones(max(M, N), device=dev)
