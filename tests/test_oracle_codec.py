@@ -118,6 +118,13 @@ def test_encode_exhaustive_positive_fp32(orc):
     assert bad == 0, hex(first)
 
 
+@pytest.mark.slow
+def test_encode_exhaustive_negative_fp32(orc):
+    # and every pattern with the sign bit set: with the positive half, all 2^32
+    bad, first = orc.check_encoder_range(1 << 31, 1 << 32)
+    assert bad == 0, hex(first)
+
+
 def test_encode_sampled_negative_fp32(orc):
     # the negative half on a fixed stride plus the symmetry encode(-x) = encode(x) ^ 0x80
     lo = 1 << 31

@@ -159,6 +159,12 @@ def test_encode_exhaustive_positive_fp32(orc):
     assert bad == 0, hex(first)
 
 
+@pytest.mark.slow
+def test_encode_exhaustive_negative_fp32(orc):
+    bad, first = orc.check_e5m2_encoder_range(1 << 31, 1 << 32)
+    assert bad == 0, hex(first)
+
+
 def test_encode_sampled_negative_fp32(orc):
     lo = 1 << 31
     for start in range(lo, 1 << 32, 1 << 27):
