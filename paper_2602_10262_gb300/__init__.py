@@ -65,6 +65,27 @@ def _dev(t: torch.Tensor, name: str, dtype: torch.dtype, dims: int):
         raise ValueError(f"{name} must have a contiguous last dimension")
 
 
+def _shape(t: torch.Tensor, name: str, shape) -> None:
+    """An output or companion array must have exactly the extent the call
+    writes or reads; a smaller one would be overrun on the device."""
+    if tuple(t.shape) != tuple(int(v) for v in shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _packed(t: torch.Tensor, name: str) -> None:
+    """Arrays the C ABI takes without a row stride must be contiguous."""
+    if t.numel() > 0 and not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _scale(t, name: str, n: int) -> None:
+    """A scale vector: float32 on the GPU, contiguous, at least n entries."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    if not t.is_contiguous() or t.numel() < n:
+        raise ValueError(f"{name} must be contiguous with at least {n} entries, got {t.numel()}")
+
+
 def _ld(t: torch.Tensor) -> int:
     return t.stride(0) if t.dim() == 2 else t.size(-1)
 
@@ -96,6 +117,8 @@ def _quantize(name: str, x, scale_mode, q, dequant_scale, stream):
     if dequant_scale is None:
         dequant_scale = torch.empty((1 if scale_mode == 0 else R,), dtype=torch.float32, device=x.device)
     _dev(q, "q", torch.uint8, 2)
+    _shape(q, "q", (R, C))
+    _scale(dequant_scale, "dequant_scale", 1 if scale_mode == 0 else R)
     rc = getattr(library(), name)(_p(x), R, C, _ld(x), int(scale_mode), _p(q), _ld(q),
                                   _p(dequant_scale), _stream(stream))
     _check(rc, name)
@@ -123,6 +146,10 @@ def prune24_compress(a: torch.Tensor, a_vals: Optional[torch.Tensor] = None,
         a_vals = torch.empty((M, K // 2), dtype=torch.uint8, device=a.device)
     if a_meta is None:
         a_meta = torch.empty((M, (K + 7) // 8), dtype=torch.uint8, device=a.device)
+    for t, nm, shp in ((a_vals, "a_vals", (M, K // 2)), (a_meta, "a_meta", (M, (K + 7) // 8))):
+        _dev(t, nm, torch.uint8, 2)
+        _shape(t, nm, shp)
+        _packed(t, nm)
     rc = library().prune24_compress(_p(a), M, K, _ld(a), _p(a_vals), _p(a_meta), _stream(stream))
     _check(rc, "prune24_compress")
     return a_vals, a_meta
@@ -130,9 +157,16 @@ def prune24_compress(a: torch.Tensor, a_vals: Optional[torch.Tensor] = None,
 
 def prune24_decompress(a_vals: torch.Tensor, a_meta: torch.Tensor, K: int,
                        out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    _dev(a_vals, "a_vals", torch.uint8, 2)
+    _dev(a_meta, "a_meta", torch.uint8, 2)
     M = a_vals.shape[0]
     if out is None:
         out = torch.empty((M, K), dtype=torch.uint8, device=a_vals.device)
+    for t, nm, shp in ((a_vals, "a_vals", (M, K // 2)), (a_meta, "a_meta", (M, (K + 7) // 8)),
+                       (out, "out", (M, K))):
+        _dev(t, nm, torch.uint8, 2)
+        _shape(t, nm, shp)
+        _packed(t, nm)
     rc = library().prune24_decompress(_p(a_vals), _p(a_meta), M, K, _p(out), _stream(stream))
     _check(rc, "prune24_decompress")
     return out
@@ -143,7 +177,19 @@ def _out(C, rows, cols, out_dtype, device):
     if C is None:
         C = torch.empty((rows, cols), dtype=dt, device=device)
     _dev(C, "C", dt, 2)
+    _shape(C, "C", (rows, cols))
     return C
+
+
+def _scales(a_scale, a_mode, M, b_scale, b_mode, N) -> None:
+    _scale(a_scale, "a_scale", M if a_mode else 1)
+    _scale(b_scale, "b_scale", N if b_mode else 1)
+
+
+def _sparse_a(a_vals, a_meta, M, K) -> None:
+    _shape(a_meta, "a_meta", (M, (K + 7) // 8))
+    _packed(a_vals, "a_vals")
+    _packed(a_meta, "a_meta")
 
 
 def gemm_fp8_dense(A: torch.Tensor, B: torch.Tensor, a_scale: torch.Tensor, a_mode: int,
@@ -158,6 +204,7 @@ def gemm_fp8_dense(A: torch.Tensor, B: torch.Tensor, a_scale: torch.Tensor, a_mo
     if B.shape[1] != K:
         raise ValueError("K mismatch")
     C = _out(C, M, N, out_dtype, A.device)
+    _scales(a_scale, a_mode, M, b_scale, b_mode, N)
     rc = library().gemm_fp8_dense(M, N, K, _p(A), _ld(A), _p(B), _ld(B), _p(a_scale), int(a_mode),
                                   _p(b_scale), int(b_mode), float(alpha), _p(C), _ld(C),
                                   int(out_dtype), _stream(stream))
@@ -177,6 +224,7 @@ def gemm_fp8_dense_fmt(A: torch.Tensor, B: torch.Tensor, a_scale: torch.Tensor, 
     if B.shape[1] != K:
         raise ValueError("K mismatch")
     C = _out(C, M, N, out_dtype, A.device)
+    _scales(a_scale, a_mode, M, b_scale, b_mode, N)
     rc = library().gemm_fp8_dense_fmt(M, N, K, _p(A), _ld(A), _p(B), _ld(B), _p(a_scale),
                                       int(a_mode), _p(b_scale), int(b_mode), float(alpha), _p(C),
                                       _ld(C), int(out_dtype), int(a_format), int(b_format),
@@ -199,6 +247,8 @@ def gemm_fp8_sparse24(a_vals: torch.Tensor, a_meta: torch.Tensor, B: torch.Tenso
     if B.shape[1] != K:
         raise ValueError("K mismatch")
     C = _out(C, N if out_transposed else M, M if out_transposed else N, out_dtype, B.device)
+    _scales(a_scale, a_mode, M, b_scale, b_mode, N)
+    _sparse_a(a_vals, a_meta, M, K)
     rc = library().gemm_fp8_sparse24(M, N, K, _p(a_vals), _p(a_meta), _p(B), _ld(B), _p(a_scale),
                                      int(a_mode), _p(b_scale), int(b_mode), float(alpha), _p(C),
                                      _ld(C), int(out_dtype), int(bool(out_transposed)),
@@ -223,6 +273,8 @@ def gemm_fp8_sparse24_fmt(a_vals: torch.Tensor, a_meta: torch.Tensor, B: torch.T
     if B.shape[1] != K:
         raise ValueError("K mismatch")
     C = _out(C, N if out_transposed else M, M if out_transposed else N, out_dtype, B.device)
+    _scales(a_scale, a_mode, M, b_scale, b_mode, N)
+    _sparse_a(a_vals, a_meta, M, K)
     rc = library().gemm_fp8_sparse24_fmt(M, N, K, _p(a_vals), _p(a_meta), _p(B), _ld(B),
                                          _p(a_scale), int(a_mode), _p(b_scale), int(b_mode),
                                          float(alpha), _p(C), _ld(C), int(out_dtype),
@@ -238,10 +290,20 @@ def make_problem(A: torch.Tensor, B: torch.Tensor, a_scale, a_mode, b_scale, b_m
                  b_format: int = E4M3) -> _lib.FP8Problem:
     """Build one ``fp8_gemm_problem`` entry (tensors must outlive the call)."""
     sparse = A_meta is not None
+    _dev(A, "A", torch.uint8, 2)
+    _dev(B, "B", torch.uint8, 2)
     M = A.shape[0]
+    N = B.shape[0]
     Kd = A.shape[1] * 2 if sparse else A.shape[1]
-    if K is not None and K != Kd:
+    if (K is not None and K != Kd) or B.shape[1] != Kd:
         raise ValueError("K mismatch")
+    if sparse:
+        _dev(A_meta, "A_meta", torch.uint8, 2)
+        _sparse_a(A, A_meta, M, Kd)
+    dt = torch.bfloat16 if out_dtype == OUT_BF16 else torch.float32
+    _dev(C, "C", dt, 2)
+    _shape(C, "C", (N, M) if out_transposed else (M, N))
+    _scales(a_scale, a_mode, M, b_scale, b_mode, N)
     return _lib.FP8Problem(M, B.shape[0], Kd, A.data_ptr(), 0 if A_meta is None else A_meta.data_ptr(),
                            _ld(A), B.data_ptr(), _ld(B), a_scale.data_ptr(), int(a_mode),
                            b_scale.data_ptr(), int(b_mode), float(alpha), C.data_ptr(), _ld(C),
