@@ -41,6 +41,31 @@ def _result(r: _lib.FP8Result) -> Result:
     return Result(r.status, r.batch_size, r.t_submit_us, r.t_launch_us, r.t_end_us, r.t_start_us)
 
 
+def _check_2d(t, name, dtype, rows, cols, ld) -> None:
+    """A tensor passed for a [rows, cols] array with row stride ld must be a
+    CUDA tensor of that dtype covering it; raw addresses are not checked."""
+    if not isinstance(t, torch.Tensor):
+        return
+    if not t.is_cuda or t.dtype != dtype or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D {dtype} CUDA tensor")
+    if t.shape[0] < rows or t.shape[1] < cols or (t.numel() > 0 and (t.stride(1) != 1 or t.stride(0) != ld)):
+        raise ValueError(f"{name} must cover [{rows}, {cols}] with row stride {ld}, got shape "
+                         f"{tuple(t.shape)} and strides {t.stride()}")
+
+
+def _check_weight(N, K, W, ldw, W_meta, w_scale, w_mode) -> None:
+    if W_meta is None:
+        _check_2d(W, "W", torch.uint8, N, K, ldw)
+    else:
+        _check_2d(W, "W", torch.uint8, N, K // 2, K // 2)
+        _check_2d(W_meta, "W_meta", torch.uint8, N, (K + 7) // 8, (K + 7) // 8)
+    if isinstance(w_scale, torch.Tensor):
+        n = N if w_mode else 1
+        if not w_scale.is_cuda or w_scale.dtype != torch.float32 or not w_scale.is_contiguous() \
+                or w_scale.numel() < n:
+            raise ValueError(f"w_scale must be a contiguous float32 CUDA tensor with >= {n} entries")
+
+
 def overlap_efficiency(results, one_per_interval: bool = True) -> float:
     """Fraction of the GPU's busy time during which two or more batches ran
     at once (the overlap-efficiency metric of the paper, section 3.2).
@@ -94,6 +119,7 @@ class Server:
             raise ServerError(rc, "fp8_server_create")
         self.h = h
         self._keep = []
+        self._shapes = {}           # handle -> (N, K) of registered weights
 
     def close(self):
         if self.h:
@@ -125,17 +151,24 @@ class Server:
             return int(t)
         if ldw is None:
             ldw = W.stride(0) if isinstance(W, torch.Tensor) and W_meta is None else K
+        _check_weight(N, K, W, ldw, W_meta, w_scale, w_mode)
         hdl = ctypes.c_uint64()
         rc = self.lib.fp8_server_register_weight_fmt(self.h, N, K, ptr(W), ldw, ptr(W_meta),
                                                      ptr(w_scale), w_mode, int(w_format),
                                                      ctypes.byref(hdl))
         if rc != 0:
             raise ServerError(rc, "fp8_server_register_weight_fmt")
+        self._shapes[hdl.value] = (int(N), int(K))
         return hdl.value
 
     def submit(self, tenant: int, weight: int, M: int, x, ldx: int, out, ldo: int,
                out_dtype: int = 1, alpha: float = 1.0) -> int:
-        """x / out: device addresses (int) or CUDA tensors."""
+        """x / out: device addresses (int) or CUDA tensors (checked against the
+        weight's N and K; the caller keeps them alive until the result)."""
+        if weight in self._shapes:
+            N, K = self._shapes[weight]
+            _check_2d(x, "x", torch.float32, M, K, ldx)
+            _check_2d(out, "out", torch.bfloat16 if out_dtype == 1 else torch.float32, M, N, ldo)
         xp = x.data_ptr() if isinstance(x, torch.Tensor) else int(x)
         op = out.data_ptr() if isinstance(out, torch.Tensor) else int(out)
         req = _lib.FP8Request(tenant, weight, M, xp, ldx, op, ldo, out_dtype, alpha)

@@ -39,3 +39,12 @@ def test_wrappers_refuse_host_tensors():
         gb.gemm_fp8_dense(a, a, torch.ones(1), 0, torch.ones(1), 0)
     with pytest.raises(TypeError, match="CUDA tensor"):
         gb.make_problem(a, a, torch.ones(1), 0, torch.ones(1), 0, torch.empty(4, 4))
+
+
+def test_server_argument_checks():
+    from paper_2602_10262_gb300 import server
+    server._check_2d(0x1000, "x", torch.float32, 4, 16, 16)       # raw addresses pass unchecked
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        server._check_2d(torch.ones(4, 16), "x", torch.float32, 4, 16, 16)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        server._check_weight(8, 16, torch.zeros(8, 16, dtype=torch.uint8), 16, None, 0x1000, 1)
