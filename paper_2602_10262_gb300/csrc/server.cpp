@@ -287,6 +287,9 @@ public:
         if (rc == FP8_OK && (!ev1 || cudaEventRecord(ev1, st) != cudaSuccess))
             rc = FP8_ERR_CUDA;
         if (rc != FP8_OK) {
+            // kernels of this batch already enqueued may still use the
+            // requests' workspace, which the caller releases on failure
+            cudaStreamSynchronize(st);
             events_.push_back(ev0);
             if (ev1)
                 events_.push_back(ev1);
