@@ -104,6 +104,11 @@ class Oracle:
                                          ctypes.c_double, i32, i32, i64, P, P, P]
         lib.orc_gemm_sparse24.argtypes = [i64, i64, i64, P, P, P, i64, P, i32, P, i32,
                                           ctypes.c_double, i32, i32, P]
+        lib.orc_e8m0_decode_array.argtypes = [P, i64, P]
+        lib.orc_mx_quantize.restype = i32
+        lib.orc_mx_quantize.argtypes = [P, i64, i64, i64, i32, P, i64, P]
+        lib.orc_gemm_mx.argtypes = [i64, i64, i64, P, i64, P, P, i64, P, ctypes.c_double, i32, i32,
+                                    P]
         lib.orc_max_threads.restype = i32
         lib.orc_set_threads.argtypes = [i32]
         self.lib = lib
@@ -271,6 +276,46 @@ class Oracle:
         self.lib.orc_gemm_sparse24(M, N, K, _ptr(v), _ptr(m), _ptr(B), K, _ptr(sa),
                                    int(a_mode), _ptr(sb), int(b_mode), float(alpha), int(a_fmt),
                                    int(b_fmt), _ptr(C))
+        return C
+
+    # --- block-scaled FP8 (OCP MX; not in the paper) --------------------------
+
+    def e8m0_decode(self, codes) -> np.ndarray:
+        """E8M0 scale codes -> 2^(code - 127) (0xFF: NaN)."""
+        c = _c(codes, np.uint8)
+        out = np.empty(c.shape, np.float64)
+        self.lib.orc_e8m0_decode_array(_ptr(c), c.size, _ptr(out))
+        return out
+
+    def mx_quantize(self, x, fmt: int = 0):
+        """fp32 [R, C] (C % 32 == 0) -> (codes uint8 [R, C], E8M0 scale codes
+        uint8 [R, C / 32]), one power-of-two scale per 32-element block."""
+        a = _c(x, np.float32)
+        if a.ndim != 2:
+            raise OracleError("mx_quantize expects a 2-D array")
+        R, C = a.shape
+        q = np.empty((R, C), np.uint8)
+        sc = np.empty((R, max(C // 32, 0)), np.uint8)
+        rc = self.lib.orc_mx_quantize(_ptr(a), R, C, C, int(fmt), _ptr(q), C, _ptr(sc))
+        if rc == -2:
+            raise OracleError("the row length must be a multiple of 32")
+        if rc == -4:
+            raise OracleError("non-finite input")
+        return q, sc
+
+    def gemm_mx(self, A, SA, B, SB, alpha=1.0, a_fmt=0, b_fmt=0) -> np.ndarray:
+        """C = alpha * sum_b SA[m,b] SB[n,b] sum_{k in b} decA decB (FP64)."""
+        A = _c(A, np.uint8)
+        B = _c(B, np.uint8)
+        SA = _c(SA, np.uint8)
+        SB = _c(SB, np.uint8)
+        M, K = A.shape
+        N = B.shape[0]
+        if B.shape[1] != K or K % 32 or SA.shape != (M, K // 32) or SB.shape != (N, K // 32):
+            raise OracleError("shape mismatch")
+        C = np.empty((M, N), np.float64)
+        self.lib.orc_gemm_mx(M, N, K, _ptr(A), K, _ptr(SA), _ptr(B), K, _ptr(SB), float(alpha),
+                             int(a_fmt), int(b_fmt), _ptr(C))
         return C
 
     def max_threads(self) -> int:

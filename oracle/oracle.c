@@ -24,6 +24,8 @@
  *   - 2:4 structured sparsity (section 2 "Structured Sparsity" and section 6):
  *     in every group of four consecutive elements along K two are zero; the
  *     pruning keeps the two largest magnitudes.
+ *   - Block-scaled FP8 (OCP MX, not in the paper): 32-element blocks along K
+ *     sharing an E8M0 power-of-two scale, and the GEMM over such operands.
  *   - GEMM: C = alpha * dA[m] * dB[n] * sum_k decA(A[m,k]) * decB(B[n,k]),
  *     FP8 x FP8 products accumulated (here in FP64), as the FP8 matrix-core
  *     operation of section 4 (FP8 x FP8 operands, wide accumulation).
@@ -598,6 +600,107 @@ void orc_gemm_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t *vals,
     orc_decompress24(vals, meta, M, K, a);
     orc_gemm(M, N, K, a, K, B, ldb, dA, a_mode, dB, b_mode, alpha, a_fmt, b_fmt, C);
     free(a);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Block-scaled FP8 (the OCP Microscaling formats MXFP8 E4M3 / E5M2): each  */
+/* block of 32 consecutive elements along K shares one power-of-two scale   */
+/* stored as E8M0.  Not in the paper; the next precision step after the     */
+/* per-row scaling it measures.                                             */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_MX_BLOCK 32
+
+/* E8M0 scale code e: 2^(e - 127) for e = 0..254; 0xFF is NaN.  No sign,
+ * no zero, no mantissa.                                                   */
+double orc_e8m0_decode(uint8_t e)
+{
+    if (e == 0xFF)
+        return NAN;
+    return ldexp(1.0, (int)e - 127);
+}
+
+void orc_e8m0_decode_array(const uint8_t *c, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = orc_e8m0_decode(c[i]);
+}
+
+/* x: fp32 [rows, cols], row stride ld; cols % 32 == 0.  For each row and
+ * each block of 32 columns:
+ *   amax = max |x| over the block;
+ *   amax == 0      -> scale code 0 (2^-127) and all codes 0 (reading: the
+ *                     spec leaves the exponent free for an all-zero block);
+ *   otherwise  e   = floor(log2(amax)) - emax, emax = 8 for E4M3 (448 =
+ *                    1.75 * 2^8) and 15 for E5M2 (57344 = 1.75 * 2^15),
+ *                    clamped to the E8M0 range [-127, 127];
+ *              code = e + 127;  q = enc(x * 2^-e) (round to nearest even,
+ *                    saturating; amax * 2^-e lies in [2^emax, 2^(emax+1)),
+ *                    so block maxima above the format's largest value
+ *                    saturate to it).
+ * The scaling by 2^-e is exact in fp32 wherever the result is at least
+ * 2^-126, and anything smaller encodes to zero in both formats.
+ * q has row stride ldq; scales are [rows, cols / 32] row-major.
+ * Returns 0, -2 if cols % 32 != 0, -4 on a non-finite input.             */
+int orc_mx_quantize(const float *x, int64_t rows, int64_t cols, int64_t ld,
+                    int fmt, uint8_t *q, int64_t ldq, uint8_t *scales)
+{
+    if (cols % ORC_MX_BLOCK != 0)
+        return -2;
+    const int emax = (fmt == 1) ? 15 : 8;
+    const int64_t nb = cols / ORC_MX_BLOCK;
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t b = 0; b < nb; ++b) {
+            const float *xb = x + r * ld + b * ORC_MX_BLOCK;
+            uint8_t *qb = q + r * ldq + b * ORC_MX_BLOCK;
+            double amax = 0.0;
+            for (int i = 0; i < ORC_MX_BLOCK; ++i) {
+                if (!isfinite(xb[i]))
+                    return -4;
+                if (fabs((double)xb[i]) > amax)
+                    amax = fabs((double)xb[i]);
+            }
+            if (amax == 0.0) {
+                scales[r * nb + b] = 0;
+                for (int i = 0; i < ORC_MX_BLOCK; ++i)
+                    qb[i] = orc_fp8_encode(fmt, xb[i]);       /* +-0 keep their sign */
+                continue;
+            }
+            int E;
+            frexp(amax, &E);                  /* amax = f * 2^E, f in [0.5, 1) */
+            int e = (E - 1) - emax;           /* floor(log2(amax)) - emax      */
+            if (e < -127)
+                e = -127;
+            if (e > 127)
+                e = 127;
+            scales[r * nb + b] = (uint8_t)(e + 127);
+            for (int i = 0; i < ORC_MX_BLOCK; ++i)
+                qb[i] = orc_fp8_encode(fmt, (float)ldexp((double)xb[i], -e));
+        }
+    return 0;
+}
+
+/* C[m,n] = alpha * sum over blocks b of SA[m,b] * SB[n,b] *
+ *          sum_{k in b} decA(A[m,k]) * decB(B[n,k])   (FP64), with SA, SB
+ * the decoded E8M0 scales ([M, K/32] and [N, K/32] row-major), A [M, K]
+ * and B [N, K] codes (row strides lda, ldb).  K % 32 == 0.               */
+void orc_gemm_mx(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
+                 const uint8_t *SA, const uint8_t *B, int64_t ldb, const uint8_t *SB,
+                 double alpha, int a_fmt, int b_fmt, double *C)
+{
+    const int64_t nb = K / ORC_MX_BLOCK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t m = 0; m < M; ++m)
+        for (int64_t n = 0; n < N; ++n) {
+            double acc = 0.0;
+            for (int64_t b = 0; b < nb; ++b) {
+                const double sb = orc_e8m0_decode(SA[m * nb + b]) * orc_e8m0_decode(SB[n * nb + b]);
+                const int64_t k0 = b * ORC_MX_BLOCK;
+                acc += sb * dot_codes(A + m * lda + k0, a_fmt, B + n * ldb + k0, b_fmt,
+                                      ORC_MX_BLOCK);
+            }
+            C[m * N + n] = alpha * acc;
+        }
 }
 
 int orc_max_threads(void)

@@ -14,6 +14,7 @@ import pytest
 import oracle
 from tests import test_oracle_codec as tc
 from tests import test_oracle_e5m2 as t5
+from tests import test_oracle_mx as tmx
 from tests import test_oracle_gemm as tg
 from tests import test_oracle_prune as tp
 from tests import test_oracle_quant as tq
@@ -72,6 +73,13 @@ MUTANTS = {
     "fp8_encode_dispatch": ("return fmt == 1 ? orc_e5m2_encode(x) : orc_e4m3_encode(x);",
                             "return orc_e4m3_encode(x);"),
     "quant_e5m2_target": ("                num = 57344.0f;", "                num = 65536.0f;"),
+    "mx_emax_e4m3": ("const int emax = (fmt == 1) ? 15 : 8;", "const int emax = (fmt == 1) ? 15 : 7;"),
+    "mx_ceil_not_floor": ("int e = (E - 1) - emax;", "int e = E - emax;"),
+    "mx_scale_code_bias": ("scales[r * nb + b] = (uint8_t)(e + 127);", "scales[r * nb + b] = (uint8_t)(e + 128);"),
+    "mx_scale_applied_inverted": ("qb[i] = orc_fp8_encode(fmt, (float)ldexp((double)xb[i], -e));",
+                                  "qb[i] = orc_fp8_encode(fmt, (float)ldexp((double)xb[i], e));"),
+    "e8m0_bias_128": ("return ldexp(1.0, (int)e - 127);", "return ldexp(1.0, (int)e - 128);"),
+    "gemm_mx_b_scale_block": ("orc_e8m0_decode(SB[n * nb + b])", "orc_e8m0_decode(SB[n * nb])"),
     "decompress_swapped": ("out[m * K + 4 * g + i0] = vals[m * ldv + 2 * g];",
                            "out[m * K + 4 * g + i1] = vals[m * ldv + 2 * g];"),
 }
@@ -111,6 +119,12 @@ def _pins(orc):
         lambda: t5.test_gemm_formats_vs_numpy(orc, 1, 0, 3, 5, 7, 0, 0),
         lambda: t5.test_gemm_small_integers_exact_every_pairing(orc),
         lambda: t5.test_gemm_format_is_per_operand(orc),
+        lambda: tmx.test_e8m0_decode_all_codes_vs_torch_and_ml_dtypes(orc),
+        lambda: tmx.test_hand_worked_blocks(orc),
+        lambda: tmx.test_zero_block_and_errors(orc),
+        lambda: tmx.test_scale_property_and_codes_vs_torch(orc, 0),
+        lambda: tmx.test_power_of_two_invariance(orc, 0),
+        lambda: tmx.test_gemm_mx_vs_numpy(orc, 0, 1),
     ]
 
 
