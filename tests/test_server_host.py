@@ -224,3 +224,22 @@ def test_batch_start_times_and_overlap_in_simulation():
         both = [s.submit(k % 2, w, 8, FAKE, 4096, FAKE, 4096) for k in range(4)]
         rs = [s.wait(t, 5) for t in both]
         assert overlap_efficiency(rs) > 0.5
+
+
+def test_pool_stress_random_sizes():
+    # a small pool and random request sizes: the first-fit pool fragments and
+    # refills, FIFO admission waits for space, and every request completes
+    # with the pool empty afterwards
+    import random
+    rng = random.Random(5)
+    pool = 24 << 20
+    with _server(num_tenants=2, latency_tenant=0, pool_bytes=pool, simulate=(20.0, 2.0, 0)) as s:
+        w = _weight(s, N=4096, K=4096)
+        tickets = [s.submit(rng.randrange(2), w, rng.randint(1, 1024), FAKE, 4096, FAKE, 4096)
+                   for _ in range(300)]
+        rs = [s.wait(t, 20) for t in tickets]
+        assert all(r is not None and r.status == OK for r in rs)
+        st = s.stats()
+        assert st["completed"] == 300 and st["failed"] == 0
+        assert st["pool_in_use"] == 0
+        assert 0 < st["pool_high_water"] <= pool
