@@ -9,13 +9,15 @@ output rows); this module compiles it with gcc on first use and wraps it with
 numpy arrays.  Each wrapper names the definition it follows (arXiv 2602.10262:
 section 2 "FP8 Matrix Cores" for the E4M3 and E5M2 formats and FP8 x FP8 ->
 wide accumulation, Table 3 for mixed-format operand pairs, section 2
-"Structured Sparsity" and section 6 for 2:4 sparsity).  Format numbers:
-``E4M3 = 0``, ``E5M2 = 1``.
+"Structured Sparsity" and section 6 for 2:4 sparsity; block-scaled FP8
+with E8M0 scales per 32 elements follows the OCP MX layout and is not in
+the paper).  Format numbers: ``E4M3 = 0``, ``E5M2 = 1``.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (exhaustive decode, brute-force encode, closed-form
 quantisation fixtures, hand-built 2:4 groups, numpy float64 matmul on decoded
-inputs, identity and permutation invariants); ``tests/test_oracle_mutants.py``
+inputs, identity and permutation invariants, the defining property of the
+block scales); ``tests/test_oracle_mutants.py``
 shows that planted mistakes in ``oracle.c`` fail those pins.
 """
 from __future__ import annotations
