@@ -32,3 +32,15 @@ def test_concurrency_stats_serial_and_identical():
     st = bench._concurrency_stats([(0.0, 2.0), (0.0, 2.0)], 2.0, [1.0, 1.0])
     assert st["overlap_efficiency"] == pytest.approx(1.0)
     assert st["fairness_1_minus_range_over_mean"] == 1.0 and st["cv"] == 0.0
+
+
+def test_recorded_traffic_follows_the_kernel_source(tmp_path):
+    """The DRAM traffic in the benchmark line comes from the committed ncu
+    summary only while the GEMM source is the one it was captured on."""
+    import bench
+    src = os.path.join(ROOT, "paper_2602_10262_gb300", "csrc", "gemm.cu")
+    assert bench.recorded_traffic(src, "dense_16384") > 1e9
+    changed = tmp_path / "gemm.cu"
+    changed.write_bytes(open(src, "rb").read() + b"\n// edited\n")
+    assert bench.recorded_traffic(str(changed), "dense_16384") is None
+    assert bench.recorded_traffic(src, "no_such_workload") is None
