@@ -114,3 +114,18 @@ def test_tune_cache_file_round_trip(lib, tmp_path):
         assert lib.gemm_fp8_tune_cache_load(str(f).encode()) == -1
     assert lib.gemm_fp8_tune_cache_load(str(tmp_path / "missing.txt").encode()) == -1
     assert lib.gemm_fp8_tune_cache_clear() == 0
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++11")])
+def test_header_is_plain_c(lang, std):
+    # the boundary is a C ABI: the header compiles on its own as C99 (and as
+    # C++), with no torch or CUDA headers needed
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    for h in HEADERS:
+        r = subprocess.run([cc, "-fsyntax-only", std, "-Wall", "-Wextra", "-pedantic", "-Werror",
+                            "-x", lang, h], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
