@@ -132,10 +132,10 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ traffic record
 
-def recorded_traffic(kernel_src: str, workload: str):
+def recorded_traffic(kernel_src: str, workload: str, profiles_dir: str = None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (sha256 of the file recorded with it)."""
-    path = os.path.join(ROOT, "profiles", f"gemm_fp8_kernel_{workload}.md")
+    path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), f"gemm_fp8_kernel_{workload}.md")
     if not os.path.exists(path):
         return None
     rec = {}
@@ -175,15 +175,50 @@ class OracleSample:
 
     def run(self, a=None, b=None):
         """Returns (FLOPs, seconds) of one dense + one sparse sub-block (the
-        first a rows of A and b rows of B; default: all of the sample)."""
+        first a rows of A and b rows of B; default: all of the sample).  The
+        full sub-block's results are kept for check()."""
         a = self.a if a is None else min(a, self.a)
         b = self.b if b is None else min(b, self.b)
         t0 = time.perf_counter()
-        self.orc.gemm(self.A[:a], self.B[:b], self.dA[:a], 1, self.dB[:b], 1)
-        self.orc.gemm_sparse24(self.vals[:a], self.meta[:a], self.B[:b], self.size, self.dA[:a], 1,
-                               self.dB[:b], 1)
+        Cd = self.orc.gemm(self.A[:a], self.B[:b], self.dA[:a], 1, self.dB[:b], 1)
+        Cs = self.orc.gemm_sparse24(self.vals[:a], self.meta[:a], self.B[:b], self.size, self.dA[:a], 1,
+                                    self.dB[:b], 1)
         dt = time.perf_counter() - t0
+        if a == self.a and b == self.b:
+            self.ref = (Cd, Cs)
         return 2.0 * 2.0 * a * b * self.size, dt
+
+    def _bf16_check(self, got, ref, A):
+        """The BF16 bound per element, |C - ref| <= 1e-2 |ref| + gamma S with
+        S = dA dB sum_k |a b| and gamma = (K + 2) 2^-24 (S from the oracle's
+        decoded codes)."""
+        dec = lambda c: self.orc.decode(c & np.uint8(0x7F), 0)
+        S = (dec(A) @ dec(self.B).T) * np.abs(self.dA.astype(np.float64))[:, None] \
+            * np.abs(self.dB.astype(np.float64))[None, :]
+        gamma = (self.size + 2) * 2.0 ** -24
+        diff = np.abs(got.astype(np.float64) - ref)
+        bound = 1e-2 * np.abs(ref) + gamma * S
+        return {"elements": int(ref.size), "failed": int(np.count_nonzero(diff > bound)),
+                "needed_gamma_term": int(np.count_nonzero(diff > 1e-2 * np.abs(ref))),
+                "max_err_over_bound": float(np.max(diff / bound)),
+                "normwise_rel_err": float(np.linalg.norm(got.astype(np.float64) - ref) / np.linalg.norm(ref))}
+
+    def check(self, gpu):
+        """The GPU step's codes, scales, compressed A and outputs on this
+        sub-block against the oracle's (gpu: host copies of the same rows)."""
+        Cd, Cs = self.ref
+        out = {"sub_block": f"rows [0,{self.a}) of A x rows [0,{self.b}) of B, K={self.size}",
+               "quantize_bitexact": bool(np.array_equal(gpu["A"], self.A) and np.array_equal(gpu["B"], self.B)
+                                         and np.array_equal(gpu["dA"], self.dA)
+                                         and np.array_equal(gpu["dB"], self.dB)),
+               "prune_bitexact": bool(np.array_equal(gpu["vals"], self.vals)
+                                      and np.array_equal(gpu["meta"], self.meta)),
+               "dense": self._bf16_check(gpu["Cd"], Cd, self.A),
+               "sparse": self._bf16_check(gpu["Cs"], Cs, self.orc.decompress24(self.vals, self.meta, self.size)),
+               "tolerance": "bf16: |C - ref| <= 1e-2 |ref| + (K+2) 2^-24 dA dB sum|a b| per element"}
+        out["pass"] = (out["quantize_bitexact"] and out["prune_bitexact"] and out["dense"]["failed"] == 0
+                       and out["sparse"]["failed"] == 0)
+        return out
 
     def describe(self):
         return (f"A rows [0,{self.a}) x B rows [0,{self.b}) at K={self.size}: "
@@ -999,6 +1034,13 @@ def main():
     ms = max_over_ranks(ms_local, ws)
     if gb.fp8_last_device_error() != 0:
         raise RuntimeError("device error during the timed region")
+    # the timed steps' own results on the oracle's sub-block, kept for the
+    # parity check of the CPU leg below
+    ca, cb = min(args.cpu_rows, M), min(args.cpu_cols, N)
+    gpu_block = {"A": A[:ca].cpu().numpy(), "dA": dA[:ca].cpu().numpy(), "B": B[:cb].cpu().numpy(),
+                 "dB": dB[:cb].cpu().numpy(), "vals": vals[:ca].cpu().numpy(), "meta": meta[:ca].cpu().numpy(),
+                 "Cd": Cd[:ca, :cb].float().cpu().numpy(),
+                 "Cs": Cs[:ca, :cb].float().cpu().numpy() if sparse_ok else None}
 
     flops_dense = 2.0 * M * N * K
     flops_step = flops_dense * (2 if sparse_ok else 1)
@@ -1120,12 +1162,15 @@ def main():
 
     # ---------------------------------------------------------------- CPU oracle
     cpu = None
+    parity = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cores = cpu_cores()
         smp = OracleSample(S, args.cpu_rows, args.cpu_cols, cores)
         f, t = smp.run()
         cpu = {"value": f / t / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": smp.describe() + f", {t:.1f} s"}
+        if sparse_ok:
+            parity = smp.check(gpu_block)
         # the same oracle on one host thread, on a smaller block
         a1, b1 = max(1, args.cpu_rows // 32), max(1, args.cpu_cols // 16)
         smp.orc.set_threads(1)
@@ -1143,7 +1188,8 @@ def main():
             "config": config(S, ws),
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "stages": stages, "sparse_path": sparse_ok,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks.summary(), "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu, "parity": parity, "clocks": clocks.summary(),
+            "serving": serving,
         }
         print(json.dumps(line))
     return 0

@@ -79,6 +79,20 @@ int fp8_last_device_error(fp8_stream_t stream);
 /* Number of SMs of the current device (persistent grids are sized from it). */
 int fp8_device_sm_count(void);
 
+/* Failure-path testing (the paper has no counterpart; this exercises the
+ * device error handling above without faulting the GPU).  The next
+ * `launches` eager GEMM kernel launches of the process (any entry point, any
+ * thread; CUDA-graph nodes made by gemm_fp8_grouped_graph_create are not
+ * affected) run with their TMA producer issuing no operand loads: the MMA
+ * warp's wait for the first stage then runs past the wait limit, the kernel
+ * records FP8_ERR_TIMEOUT, stops every role, waits for its own outstanding
+ * tensor-core work, frees its tensor memory and exits, leaving C unwritten
+ * (split-K counters untouched).  wait_limit_ms > 0 sets the limit of every
+ * bounded wait of eager GEMM launches from now on (the default is 2 s);
+ * 0 restores the default.  launches = 0 cancels pending stalls.
+ * FP8_ERR_INVALID for launches < 0 or a limit outside [0, 60000] ms. */
+int fp8_test_stall_gemm_loads(int launches, double wait_limit_ms);
+
 /* ---------------------------------------------------------------------------
  * Scale selection + E4M3 quantisation (rows a1, a2 of the path).
  * Paper: section 2 "FP8 Matrix Cores" (OCP E4M3 format).
@@ -226,7 +240,14 @@ int gemm_fp8_dense_fmt(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_
  *     an allocation).  Calls whose kernels overlap on the GPU (for example on
  *     two streams at once) race on the array: serialise them;
  *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress); make it before any stream capture.  A lookup
+ *     that fails is not remembered: the next call tries again.  Separately,
+ *     under CUDA's lazy module loading (the default) the driver loads a
+ *     kernel's code, and the array, on a device the first time they are
+ *     used there, which can take device memory once.  Callers for whom no
+ *     call may allocate set CUDA_MODULE_LOADING=EAGER (everything is loaded
+ *     with the library) or make a warm-up call per device and shape class
+ *     at start-up.
  * ------------------------------------------------------------------------- */
 int gemm_fp8_dense_noalloc(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
                            const uint8_t *B, int64_t ldb, const float *a_scale, int a_mode,

@@ -20,7 +20,7 @@ __all__ = [
     "Fp8Error", "library", "fp8_quantize_e4m3", "fp8_quantize_e5m2", "prune24_compress",
     "prune24_decompress", "gemm_fp8_dense", "gemm_fp8_dense_fmt", "gemm_fp8_sparse24",
     "gemm_fp8_sparse24_fmt", "gemm_fp8_grouped", "gemm_fp8_grouped_ex", "fp8_last_device_error",
-    "fp8_device_sm_count", "fp8_gemm_set_tile_config", "gemm_fp8_grouped_autotune",
+    "fp8_device_sm_count", "fp8_test_stall_gemm_loads", "fp8_gemm_set_tile_config", "gemm_fp8_grouped_autotune",
     "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
     "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2",
 ]
@@ -101,6 +101,14 @@ def fp8_last_device_error(stream=None) -> int:
 
 def fp8_device_sm_count() -> int:
     return int(library().fp8_device_sm_count())
+
+
+def fp8_test_stall_gemm_loads(launches: int, wait_limit_ms: float = 0.0) -> None:
+    """Failure-path testing: the next `launches` eager GEMM launches issue no
+    operand loads and end with FP8_ERR_TIMEOUT after `wait_limit_ms` (which
+    applies to every eager GEMM launch until reset with 0)."""
+    _check(library().fp8_test_stall_gemm_loads(int(launches), float(wait_limit_ms)),
+           "fp8_test_stall_gemm_loads")
 
 
 def fp8_gemm_set_tile_config(mt: int = 0, group_m: int = 0) -> None:

@@ -80,6 +80,7 @@ SIGNATURES = {
     "fp8_status_string": (ctypes.c_char_p, [I32]),
     "fp8_last_device_error": (I32, [P]),
     "fp8_device_sm_count": (I32, []),
+    "fp8_test_stall_gemm_loads": (I32, [I32, ctypes.c_double]),
     "fp8_quantize_e4m3": (I32, [P, I64, I64, I64, I32, P, I64, P, P]),
     "fp8_quantize_e5m2": (I32, [P, I64, I64, I64, I32, P, I64, P, P]),
     "prune24_compress": (I32, [P, I64, I64, I64, P, P, P]),

@@ -161,6 +161,9 @@ struct Params {
     float* ws;              // split-K partial sums (nullptr when no problem splits)
     unsigned* ctr;          // split-K arrival counters, zero between launches
     int cluster_split;      // > 0: one problem whose split tiles run as clusters of this many CTAs
+    unsigned long long wait_ns;   // limit of every bounded wait (kWaitLimitNs unless a test sets another)
+    int withhold_loads;     // failure-path test: the producer issues no loads, so the MMA warp's
+                            // first wait runs past wait_ns and the launch ends with FP8_ERR_TIMEOUT
 };
 
 struct TileCoord {
@@ -553,6 +556,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
     const int total_tiles = prm.total_tiles;
     const int cluster_split = prm.cluster_split;
     int* const err = prm.err;
+    const unsigned long long wlim = prm.wait_ns;
     float* const ws = prm.ws;
     unsigned* const ctr = prm.ctr;
     const TileCoord tc_first = tile_coord(prm, blockIdx.x);
@@ -601,7 +605,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             uint32_t phase = 0;
             uint32_t armed = 0;                 // bit s: slot s armed at least once
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+            const int producer_tiles = prm.withhold_loads ? 0 : total_tiles;
+            for (int tile = blockIdx.x; ok && tile < producer_tiles; tile += gridDim.x) {
                 const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
                 const bool first = tile == static_cast<int>(blockIdx.x);
                 const ProblemScalars P = first ? P_first : prm.prob[tc.p];
@@ -625,7 +630,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                 for (int kb = kb0; kb < kb1; kb += KC) {
                     const int nck = min(KC, kb1 - kb);          // k-blocks in this stage
                     // a slot never armed is free: no wait on its first use
-                    if (((armed >> stage) & 1u) && !mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
+                    if (((armed >> stage) & 1u) && !mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, wlim)) {
                         ok = false;
                         abort_pipeline(abort_flag, err);
                         break;
@@ -674,7 +679,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                     if (!(armed >> s & 1u))
                         continue;
                     const uint32_t last_parity = (s < stage) ? phase : (phase ^ 1u);
-                    mbar_wait(full_bar(s), last_parity, &never);
+                    mbar_wait(full_bar(s), last_parity, &never, wlim);
                 }
             }
         }
@@ -694,7 +699,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                 const int acc = local % C::kAcc;
                 const uint32_t acc_phase = (local / C::kAcc) & 1;
                 // an accumulator not used yet is free: no wait on its first use
-                if (local >= C::kAcc && !mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag)) {
+                if (local >= C::kAcc && !mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, wlim)) {
                     abort_pipeline(abort_flag, err);
                     break;
                 }
@@ -706,7 +711,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                 for (int kb = kb0; kb < kb1; kb += KC) {
                     const int nck = min(KC, kb1 - kb);          // k-blocks in this stage
                     const uint32_t first = kb == kb0 ? 0u : 1u;     // 0: overwrite the accumulator
-                    if (!mbar_wait(full_bar(stage), phase, abort_flag)) {
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag, wlim)) {
                         ok = false;
                         abort_pipeline(abort_flag, err);
                         break;
@@ -771,7 +776,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             // every MMA this thread issued has finished before TMEM is freed
             const volatile int never = 0;
             mma_commit(drain_bar);
-            mbar_wait(drain_bar, 0u, &never);
+            mbar_wait(drain_bar, 0u, &never, wlim);
         }
     } else {
         // ---------------------------------------------------- epilogue
@@ -794,7 +799,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
             ScaleWindows sw;
             sw.init(P, jbase, lane);
             // the whole warp takes the same branch (tcgen05.ld is warp-collective)
-            const bool got = mbar_wait(tfull_bar(acc), acc_phase, abort_flag);
+            const bool got = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, wlim);
             if (!__all_sync(0xFFFFFFFFu, got)) {
                 abort_pipeline(abort_flag, err);
                 break;
@@ -813,14 +818,14 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                     if (threadIdx.x == 64)
                         for (int r = 1; r < P.splits; ++r)
                             mbar_arrive_remote(cluster_map(split_verdict_bar, static_cast<uint32_t>(r)));
-                    const bool got = mbar_wait_cluster(split_written_bar, 0u, abort_flag);
+                    const bool got = mbar_wait_cluster(split_written_bar, 0u, abort_flag, wlim);
                     if (!__all_sync(0xFFFFFFFFu, got)) {
                         abort_pipeline(abort_flag, err);
                         break;
                     }
                     cluster_reduce_store(P, smem, BM * MT, row, taddr, i, row_ok, fi, jbase, sw, lane);
                 } else {
-                    const bool got = mbar_wait_cluster(split_verdict_bar, 0u, abort_flag);
+                    const bool got = mbar_wait_cluster(split_verdict_bar, 0u, abort_flag, wlim);
                     if (!__all_sync(0xFFFFFFFFu, got)) {
                         abort_pipeline(abort_flag, err);
                         break;
@@ -843,7 +848,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                 __threadfence();
                 mbar_arrive(split_written_bar);
                 if (threadIdx.x == 64) {
-                    if (mbar_wait(split_written_bar, split_phase, abort_flag)) {
+                    if (mbar_wait(split_written_bar, split_phase, abort_flag, wlim)) {
                         const unsigned prev = atomicAdd(ctr + P.ctr_off + tc.tile, 1u);
                         *split_flag = (prev == static_cast<unsigned>(P.splits - 1)) ? 1 : 0;
                     } else {
@@ -852,7 +857,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                     }
                     mbar_arrive(split_verdict_bar);
                 }
-                const bool got_verdict = mbar_wait(split_verdict_bar, split_phase, abort_flag);
+                const bool got_verdict = mbar_wait(split_verdict_bar, split_phase, abort_flag, wlim);
                 split_phase ^= 1u;
                 if (!__all_sync(0xFFFFFFFFu, got_verdict)) {
                     abort_pipeline(abort_flag, err);
@@ -1263,6 +1268,8 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     out->ws_floats = static_cast<size_t>(ws);
     out->ctr_count = static_cast<size_t>(ctrs);
     prm.err = device_error_word();
+    prm.wait_ns = kWaitLimitNs;
+    prm.withhold_loads = 0;
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
@@ -1274,11 +1281,23 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     return FP8_OK;
 }
 
+// Failure-path test switch (fp8_test_stall_gemm_loads): eager launches still
+// to be stalled, and the wait limit eager launches get.
+std::atomic<int> g_stall_launches{0};
+std::atomic<unsigned long long> g_test_wait_ns{0};
+
 template <int MAXP>
 int launch_plan(Params<MAXP>& prm, const Plan& pl, cudaStream_t st)
 {
     if (pl.grid == 0)
         return FP8_OK;
+    const unsigned long long test_wait = g_test_wait_ns.load(std::memory_order_relaxed);
+    if (test_wait)
+        prm.wait_ns = test_wait;
+    int n = g_stall_launches.load(std::memory_order_relaxed);
+    while (n > 0 && !g_stall_launches.compare_exchange_weak(n, n - 1)) {
+    }
+    prm.withhold_loads = n > 0 ? 1 : 0;
     void* args[] = {&prm};
     // programmatic stream serialization: the kernel's setup may overlap the
     // tail of the previous kernel on `st` (it waits for it before touching
@@ -1806,19 +1825,28 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device (host code only has a stand-in for the symbol).
+// Device address of g_noalloc_scratch on the current device (host code only
+// has a stand-in for the symbol).  A successful lookup is kept for the rest
+// of the process; a failed one (a transient error, or a first call made
+// while a stream is being captured in global mode) is not, so the next call
+// tries again instead of failing for good.
 int noalloc_scratch(void** out)
 {
-    static std::once_flag once[64];
+    static std::mutex mu;
     static void* addr[64];
-    static cudaError_t err[64];
     int dev = 0;
     GB_CUDA_OK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64)
         return FP8_ERR_UNSUPPORTED;
-    std::call_once(once[dev], [dev] { err[dev] = cudaGetSymbolAddress(&addr[dev], g_noalloc_scratch); });
-    GB_CUDA_OK(err[dev]);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();                 // leave no sticky error behind
+            return FP8_ERR_CUDA;
+        }
+        addr[dev] = p;
+    }
     *out = addr[dev];
     return FP8_OK;
 }
@@ -1854,13 +1882,13 @@ extern "C" int gemm_fp8_dense_noalloc(int64_t M, int64_t N, int64_t K, const uin
     const size_t bytes = workspace_bytes(pl);
     if (bytes > kNoAllocScratchBytes)
         return FP8_ERR_SHAPE;                    // needs more scratch than the fixed array holds
+    // resolved on every call (a cached pointer after the first), so any
+    // first call on a device does the lookup
     void* scratch = nullptr;
-    if (bytes) {
-        rc = noalloc_scratch(&scratch);
-        if (rc != FP8_OK)
-            return rc;
-    }
-    bind_workspace(prm, pl, scratch);
+    rc = noalloc_scratch(&scratch);
+    if (rc != FP8_OK)
+        return rc;
+    bind_workspace(prm, pl, bytes ? scratch : nullptr);
     if (bytes)
         GB_CUDA_OK(cudaMemsetAsync(prm.ctr, 0, pl.ctr_count * sizeof(unsigned), st));
     return launch_plan(prm, pl, st);
@@ -2317,5 +2345,14 @@ extern "C" int fp8_gemm_set_tile_config(int mt, int group_m)
         return FP8_ERR_INVALID;
     gb300::g_force_mt.store(mt);
     gb300::g_force_group_m.store(group_m);
+    return FP8_OK;
+}
+
+extern "C" int fp8_test_stall_gemm_loads(int launches, double wait_limit_ms)
+{
+    if (launches < 0 || !(wait_limit_ms >= 0.0) || wait_limit_ms > 60000.0)
+        return FP8_ERR_INVALID;
+    gb300::g_test_wait_ns.store(static_cast<unsigned long long>(wait_limit_ms * 1e6));
+    gb300::g_stall_launches.store(launches);
     return FP8_OK;
 }

@@ -1,9 +1,9 @@
 // Inline-PTX building blocks for sm_103a: mbarrier, TMA (cp.async.bulk.tensor),
 // tcgen05 (TMEM alloc / MMA / commit / ld / st / cp) and fences.
 //
-// Every wait here is bounded: it polls the barrier and gives up after
-// kWaitLimitNs of %globaltimer, so a broken pipeline reports an error status
-// instead of hanging the GPU.
+// Every wait here is bounded: it polls the barrier and gives up after a
+// limit (kWaitLimitNs unless the launch sets another) of %globaltimer, so a
+// broken pipeline reports an error status instead of hanging the GPU.
 #pragma once
 #include <cstdint>
 #include <cuda.h>
@@ -61,8 +61,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 }
 
 // Wait until the phase with the given parity has completed.  Returns false
-// after kWaitLimitNs, or early when *abort (shared memory) becomes non-zero.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort)
+// after limit_ns, or early when *abort (shared memory) becomes non-zero.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort,
+                                          unsigned long long limit_ns)
 {
     if (mbar_try_wait(bar, parity))
         return true;
@@ -74,7 +75,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const v
                 return true;
         if (*abort)
             return false;
-        if (globaltimer() - t0 > kWaitLimitNs)
+        if (globaltimer() - t0 > limit_ns)
             return false;
     }
 }
@@ -134,7 +135,8 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t par
 }
 
 // Bounded wait (as mbar_wait) with cluster-scope acquire.
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, const volatile int* abort)
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, const volatile int* abort,
+                                                  unsigned long long limit_ns)
 {
     if (mbar_try_wait_cluster(bar, parity))
         return true;
@@ -146,7 +148,7 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
                 return true;
         if (*abort)
             return false;
-        if (globaltimer() - t0 > kWaitLimitNs)
+        if (globaltimer() - t0 > limit_ns)
             return false;
     }
 }

@@ -78,6 +78,17 @@ def test_host_validation_without_gpu(lib):
     assert lib.fp8_quantize_e5m2(None, 0, 4, 4, 0, None, 4, None, None) == 0
 
 
+def test_stall_switch_validates_and_resets(lib):
+    # failure-path test switch: bad counts and limits are refused; 0, 0
+    # cancels pending stalls and restores the default limit (no CUDA call)
+    assert lib.fp8_test_stall_gemm_loads(-1, 0.0) == -1
+    assert lib.fp8_test_stall_gemm_loads(0, -1.0) == -1
+    assert lib.fp8_test_stall_gemm_loads(0, float("nan")) == -1
+    assert lib.fp8_test_stall_gemm_loads(0, 1e9) == -1
+    assert lib.fp8_test_stall_gemm_loads(3, 50.0) == 0
+    assert lib.fp8_test_stall_gemm_loads(0, 0.0) == 0
+
+
 def test_grouped_rejects_bad_format(lib):
     from paper_2602_10262_gb300 import _lib
     pr = _lib.FP8Problem(4, 4, 32, 16, 0, 32, 16, 32, 16, 0, 16, 0, 1.0, 16, 4, 0, 0, 0, 0)

@@ -37,10 +37,16 @@ def test_concurrency_stats_serial_and_identical():
 def test_recorded_traffic_follows_the_kernel_source(tmp_path):
     """The DRAM traffic in the benchmark line comes from the committed ncu
     summary only while the GEMM source is the one it was captured on."""
+    import hashlib
     import bench
-    src = os.path.join(ROOT, "paper_2602_10262_gb300", "csrc", "gemm.cu")
-    assert bench.recorded_traffic(src, "dense_16384") > 1e9
-    changed = tmp_path / "gemm.cu"
-    changed.write_bytes(open(src, "rb").read() + b"\n// edited\n")
-    assert bench.recorded_traffic(str(changed), "dense_16384") is None
-    assert bench.recorded_traffic(src, "no_such_workload") is None
+    src = tmp_path / "gemm.cu"
+    src.write_bytes(b"// a kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "gemm_fp8_kernel_dense_16384.md").write_text(
+        f"# record\n\n- source_sha256_16: `{sha}`\n- dram_bytes_per_launch: `3646000000`\n")
+    assert bench.recorded_traffic(str(src), "dense_16384", str(prof)) == 3646000000.0
+    src.write_bytes(src.read_bytes() + b"// edited\n")
+    assert bench.recorded_traffic(str(src), "dense_16384", str(prof)) is None
+    assert bench.recorded_traffic(str(src), "no_such_workload", str(prof)) is None

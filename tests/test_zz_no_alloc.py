@@ -3,6 +3,14 @@ allocate device memory (fixed memory budgets planned up front; code running
 inside an allocator's callbacks).  Its split-K scratch is a fixed array in
 the library's device memory instead of a per-call allocation.
 
+Checked here: the result equals gemm_fp8_dense bit for bit and the oracle
+within the FP32 tolerance, on two calls in a row (the second call finds the
+first one's leftovers in the array); the call leaves the device's default
+memory pool (where cudaMallocAsync draws from) untouched while
+gemm_fp8_dense on the same shape grows it, so the shape really needs scratch
+and the array served it; a problem whose scratch exceeds the array is
+refused with FP8_ERR_SHAPE.
+
 Collected last on purpose (file name), so that a run stopping at the first
 failure has run every other test first.  Passes alone in a fresh process and
 after the other tests."""
@@ -17,6 +25,10 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
+SCRATCH_BYTES = 4 << 20              # the array's size, as the header states
+RESERVED_MEM_CURRENT = 5             # CUmemPool_attribute values (cuda.h)
+USED_MEM_CURRENT = 7
+
 
 @pytest.fixture(scope="module")
 def lib():
@@ -24,48 +36,120 @@ def lib():
     return _lib.load()
 
 
-def _args(A, B, sa, sb, C):
+class DefaultPool:
+    """Reserved and used bytes of the current device's default memory pool,
+    read through the driver API (the pool cudaMallocAsync allocates from;
+    PyTorch's caching allocator does not use it)."""
+
+    def __init__(self):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def _attr(self, a):
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, a, ctypes.byref(v)) == 0
+        return v.value
+
+    def snapshot(self):
+        return self._attr(RESERVED_MEM_CURRENT), self._attr(USED_MEM_CURRENT)
+
+
+def _args(A, B, sa, sb, C, stream):
     M, K = A.shape
     N = B.shape[0]
-    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = ctypes.c_void_p(stream.cuda_stream)
     return (M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), sa.data_ptr(), 1,
             sb.data_ptr(), 1, 1.0, C.data_ptr(), C.stride(0), 0, st)
 
 
-@pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (8, 8192, 4096), (64, 1280, 8192),
-                                   (512, 512, 1024)])
-def test_noalloc_matches_dense_two_calls(lib, M, N, K):
-    # (16, 4096, 4096) and (8, 8192, 4096) split K and add the slices up
-    # within clusters (no scratch); (64, 1280, 8192) splits in eight, whose
-    # partial sums exceed a CTA's ring, so it goes through the scratch array
-    # (2.6 MB); (512, 512, 1024) does not split
+def _operands(M, N, K):
     dev = torch.device("cuda")
-    A = torch.from_numpy(workloads.random_codes((M, K), seed=M)).to(dev)
-    B = torch.from_numpy(workloads.random_codes((N, K), seed=N)).to(dev)
-    sa = torch.from_numpy(np.abs(workloads.randn_f32((M,), seed=3)) + 0.5).to(dev)
-    sb = torch.from_numpy(np.abs(workloads.randn_f32((N,), seed=4)) + 0.5).to(dev)
-    ref = torch.empty((M, N), dtype=torch.float32, device=dev)
-    assert lib.gemm_fp8_dense(*_args(A, B, sa, sb, ref)) == 0
-    for _ in range(2):                        # the second call reuses the array's old contents
-        out = torch.full((M, N), float("nan"), dtype=torch.float32, device=dev)
-        assert lib.gemm_fp8_dense_noalloc(*_args(A, B, sa, sb, out)) == 0
+    A = workloads.random_codes((M, K), seed=M)
+    B = workloads.random_codes((N, K), seed=N)
+    sa = (np.abs(workloads.randn_f32((M,), seed=3)) + 0.5).astype(np.float32)
+    sb = (np.abs(workloads.randn_f32((N,), seed=4)) + 0.5).astype(np.float32)
+    host = (A, B, sa, sb)
+    return host, tuple(torch.from_numpy(v).to(dev) for v in host)
+
+
+def _scratch_shape(t):
+    """A product that splits along K and whose slices do not fit a cluster:
+    M = 64 rows on the MMA N side (64-wide tiles), K = 8192, and N = 128 t
+    rows, i.e. t tiles; with t <= SMs / 8 each tile splits in eight, and
+    seven slices' partial sums (7 x 128 x 64 floats, 224 KiB) exceed a CTA's
+    ring.  Its scratch: t x 8 x 128 x 64 floats plus 256 bytes of counters."""
+    return 64, 128 * t, 8192, t * 8 * 128 * 64 * 4 + 256
+
+
+def test_noalloc_equals_dense_and_oracle_two_calls(lib, orc):
+    sms = lib.fp8_device_sm_count()
+    M, N, K, need = _scratch_shape(min(sms // 8, 15))   # 15 tiles: 3.9 MB of the 4 MiB
+    assert need <= SCRATCH_BYTES
+    host, (A, B, sa, sb) = _operands(M, N, K)
+    pool = DefaultPool()
+    ref = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    s1 = torch.cuda.Stream()
+    before = pool.snapshot()
+    for i in range(2):                       # the second call reuses the array's old contents
+        out = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
-        parity.check_fp32(out.double().cpu().numpy(), ref.double().cpu().numpy())
-    assert lib.fp8_last_device_error(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+        assert lib.gemm_fp8_dense_noalloc(*_args(A, B, sa, sb, out, s1)) == 0
+        s1.synchronize()
+        assert pool.snapshot() == before, "the no-allocation call drew from the default pool"
+        if i == 0:
+            first = out.clone()
+        else:
+            assert torch.equal(out, first)
+    assert lib.fp8_last_device_error(ctypes.c_void_p(s1.cuda_stream)) == 0
+
+    # control: the regular call on a fresh stream takes its split-K scratch
+    # from the default pool, so this shape does need scratch
+    s2 = torch.cuda.Stream()
+    assert lib.gemm_fp8_dense(*_args(A, B, sa, sb, ref, s2)) == 0
+    s2.synchronize()
+    after = pool.snapshot()
+    assert after[1] >= before[1] + need - 256, (before, after, need)
+    assert torch.equal(first, ref), "gemm_fp8_dense_noalloc differs from gemm_fp8_dense"
+
+    Ah, Bh, sah, sbh = host
+    parity.check_fp32(first.double().cpu().numpy(), orc.gemm(Ah, Bh, sah, 1, sbh, 1))
+
+
+@pytest.mark.parametrize("M,N,K", [(16, 4096, 4096), (8, 8192, 4096), (512, 512, 1024)])
+def test_noalloc_without_scratch_equals_dense(lib, orc, M, N, K):
+    # slices added up within clusters (the first two) or no split at all:
+    # no scratch, and the same bits as gemm_fp8_dense
+    host, (A, B, sa, sb) = _operands(M, N, K)
+    st = torch.cuda.current_stream()
+    ref = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    assert lib.gemm_fp8_dense(*_args(A, B, sa, sb, ref, st)) == 0
+    for _ in range(2):
+        out = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+        assert lib.gemm_fp8_dense_noalloc(*_args(A, B, sa, sb, out, st)) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    Ah, Bh, sah, sbh = host
+    parity.check_fp32(ref.double().cpu().numpy(), orc.gemm(Ah, Bh, sah, 1, sbh, 1))
+    assert lib.fp8_last_device_error(ctypes.c_void_p(st.cuda_stream)) == 0
 
 
 def test_noalloc_rejects_scratch_beyond_the_array(lib):
-    # 19 tiles of 64-wide N split in eight: seven slices' partial sums
-    # (224 KB) exceed a CTA's ring, so no cluster; 152 x 128 x 64 floats
-    # (4.98 MB) exceed the 4 MiB array -> a clear FP8_ERR_SHAPE, nothing
-    # launched
+    sms = lib.fp8_device_sm_count()
+    M, N, K, need = _scratch_shape(sms // 8)             # GB300: 19 tiles, 4.98 MB
+    if need <= SCRATCH_BYTES:
+        pytest.skip(f"{sms} SMs: the largest eight-slice split needs only {need} bytes")
     dev = torch.device("cuda")
-    M, N, K = 64, 2432, 8192
     A = torch.zeros((M, K), dtype=torch.uint8, device=dev)
     B = torch.zeros((N, K), dtype=torch.uint8, device=dev)
     s = torch.ones(max(M, N), device=dev)
     C = torch.empty((M, N), dtype=torch.float32, device=dev)
-    assert lib.gemm_fp8_dense_noalloc(*_args(A, B, s, s, C)) == -2
+    st = torch.cuda.current_stream()
+    assert lib.gemm_fp8_dense_noalloc(*_args(A, B, s, s, C, st)) == -2
     # the regular entry point takes the same problem from the allocator
-    assert lib.gemm_fp8_dense(*_args(A, B, s, s, C)) == 0
+    assert lib.gemm_fp8_dense(*_args(A, B, s, s, C, st)) == 0
     torch.cuda.synchronize()
