@@ -76,17 +76,63 @@ def max_over_ranks(v: float, ws: int) -> float:
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """SM clock and clock-event (throttle) reasons sampled during a region:
+    every 5 ms through NVML (the driver's libnvidia-ml.so.1, read only),
+    else every 100 ms from nvidia-smi."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReason bits (nvml.h)
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
+    PERIOD_S = 0.005
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, uuid: str = None):
         self.index = index
+        self.uuid = uuid           # CUDA and NVML may number GPUs differently
         self.proc = None
         self.lines = []
+        self.samples = []          # (sm_mhz, reason bits) from NVML
+        self.max_mhz = None
+        self.nvml = None
+        self.stop = threading.Event()
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            if self.uuid:
+                rc = lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(self.uuid.encode()), ctypes.byref(h))
+            else:
+                rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h))
+            if rc != 0:
+                return None
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:      # NVML_CLOCK_SM
+                self.max_mhz = float(mx.value)
+            return lib, h
+        except OSError:
+            return None
+
+    def _nvml_loop(self):
+        import ctypes
+        lib, h = self.nvml
+        clk, why = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and \
+                    lib.nvmlDeviceGetCurrentClocksEventReasons(h, ctypes.byref(why)) == 0:
+                self.samples.append((float(clk.value), int(why.value)))
+            self.stop.wait(self.PERIOD_S)
 
     def __enter__(self):
+        self.nvml = self._nvml_open()
+        if self.nvml is not None:
+            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.thread.start()
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
@@ -103,6 +149,13 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        if self.nvml is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
+            try:
+                self.nvml[0].nvmlShutdown()
+            except Exception:
+                pass
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -112,6 +165,11 @@ class ClockSampler:
             self.thread.join(timeout=5)
 
     def summary(self):
+        if self.nvml is not None:
+            sm = [c for c, _ in self.samples]
+            reasons = sorted(n for n, bit in self.REASON_BITS.items() if any(w & bit for _, w in self.samples))
+            return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(sm), "source": "nvml, 5 ms"}
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
@@ -127,7 +185,16 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 100 ms"}
+
+
+def gpu_uuid(dev):
+    """NVML's UUID string of a CUDA device ("GPU-..."), or None."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return None
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 # ------------------------------------------------------------------ traffic record
@@ -270,17 +337,24 @@ def config(size, ws):
 
 class ServingBench:
     """Poisson stream of FP8 GEMM requests from two tenants against resident
-    weights, served by the library's request server in three modes: per call
-    (one quantise + one GEMM launch per request), continuous batching, and
-    continuous batching with co-scheduling (the bulk tenant's GEMMs capped
-    at SMs - 24 CTAs so the latency tenant always finds free SMs).
+    weights, served by the library's request server.  Modes: per call (one
+    quantise + one GEMM launch per request: the baseline), continuous
+    batching with the latency tenant's requests launched as they arrive and
+    the bulk tenant's GEMMs leaving `reserve` SMs free for them (the
+    server's policy, "batched"), and continuous batching without a reserve.
 
     Tenant 0 (latency): M log-uniform in [1, 64]; tenant 1 (throughput): M
     log-uniform in [64, 4096]; (N, K) uniform over {4096, 8192, 14336}^2;
     half the requests use the 2:4-sparse copy of the weight.  Inputs are
-    seeded synthetic fp32 (seed 2 for the trace)."""
+    seeded synthetic fp32 (seed 2 for the trace); each request reads its
+    activations from a random row offset of a 16384-row buffer.  Every
+    request in flight has an output slot of its own (no two in-flight
+    requests write the same bytes); a slot is reused once its request's
+    result has been collected."""
 
     SIZES = (4096, 8192, 14336)
+    RESERVE = 24                   # SMs the batched mode keeps free for the latency tenant
+    SLOTS = 128                    # output slots (requests in flight at most)
 
     def __init__(self, dev, gb):
         self.gb, self.dev = gb, dev
@@ -293,9 +367,9 @@ class ServingBench:
                 vals, meta = gb.prune24_compress(Wd)
                 self.weights[(N, K)] = (Wd, dW, vals, meta)
                 del w
-        self.X = torch.randn((4096, max(self.SIZES)), generator=g, device=dev, dtype=torch.float32)
-        self.arena = torch.empty((1 << 30,), dtype=torch.bfloat16, device=dev)
-        self.arena_pos = 0
+        self.X = torch.randn((16384, max(self.SIZES)), generator=g, device=dev, dtype=torch.float32)
+        self.slot_elems = 4096 * max(self.SIZES)
+        self.outs = torch.empty((self.SLOTS, self.slot_elems), dtype=torch.bfloat16, device=dev)
         torch.cuda.synchronize()
 
     def trace(self, n, seed):
@@ -307,53 +381,80 @@ class ServingBench:
         K = rng.choice(self.SIZES, n)
         sparse = rng.random(n) < 0.5
         gap = rng.exponential(1.0, n)           # unit-rate Poisson arrivals, scaled later
-        return [dict(tenant=int(t), M=int(m), N=int(nn), K=int(k), sparse=bool(sp), gap=float(gp))
-                for t, m, nn, k, sp, gp in zip(tenant, M, N, K, sparse, gap)]
+        row = rng.integers(0, 16384 - 4096, n)  # activation rows [row, row + M)
+        return [dict(tenant=int(t), M=int(m), N=int(nn), K=int(k), sparse=bool(sp), gap=float(gp), row=int(r0))
+                for t, m, nn, k, sp, gp, r0 in zip(tenant, M, N, K, sparse, gap, row)]
 
-    def _out(self, M, N):
-        n = M * N
-        if self.arena_pos + n > self.arena.numel():
-            self.arena_pos = 0
-        o = self.arena[self.arena_pos:self.arena_pos + n]
-        self.arena_pos += (n + 127) // 128 * 128
-        return o.data_ptr()
-
-    MODES = {"per_call": (False, False), "batched": (True, False), "batched_coscheduled": (True, True)}
-
-    def _server(self, mode):
-        from paper_2602_10262_gb300.server import Server
+    def modes(self):
         sms = self.gb.fp8_device_sm_count()
-        batching, cosched = self.MODES[mode]
-        srv = Server(num_tenants=2, latency_tenant=0, batching=batching,
-                     bulk_max_ctas=max(sms - 24, 1) if cosched else 0, pool_bytes=4 << 30)
+        return {"per_call": dict(batching=False),
+                "batched": dict(batching=True, bulk_max_ctas=max(sms - self.RESERVE, 1)),
+                "batched_no_reserve": dict(batching=True)}
+
+    def _server(self, mode_cfg):
+        from paper_2602_10262_gb300.server import Server
+        srv = Server(num_tenants=2, latency_tenant=0, pool_bytes=8 << 30, **mode_cfg)
         handles = {}
         for (N, K), (Wd, dW, vals, meta) in self.weights.items():
             handles[(N, K, False)] = srv.register_weight(N, K, Wd, dW, 1)
             handles[(N, K, True)] = srv.register_weight(N, K, vals, dW, 1, W_meta=meta)
         return srv, handles
 
-    def run(self, reqs, mode, rate=None):
-        """Submit `reqs` (all at once when rate is None, else Poisson at
-        `rate` requests/s) to a server in `mode`; returns per-request
-        latencies, the makespan in microseconds, the server's stats and the
-        results."""
-        srv, handles = self._server(mode)
+    def run(self, reqs, mode_cfg, rate=None, window=96):
+        """Serve `reqs`: Poisson arrivals at `rate` requests/s, or (rate None)
+        a closed loop keeping `window` requests in flight.  Returns latencies
+        (us), the makespan (us), the server's stats and the results."""
+        from collections import deque
+        srv, handles = self._server(mode_cfg)
         ld = self.X.stride(0)
+        xb, ob = self.X.data_ptr(), self.outs.data_ptr()
+        free = list(range(self.SLOTS))
+        pend = (deque(), deque())                # per tenant: (ticket, slot, index), in order
+        res = [None] * len(reqs)
+        inflight = 0
+
+        def collect(block):
+            nonlocal inflight
+            got = False
+            for q in pend:
+                while q:
+                    t, slot, i = q[0]
+                    r = srv.wait(t, 60) if block and not got else srv.poll(t)
+                    if r is None:
+                        break
+                    q.popleft()
+                    res[i] = r
+                    free.append(slot)
+                    inflight -= 1
+                    got = True
+            return got
+
         try:
             times = None
             if rate is not None:
                 times = np.cumsum([r["gap"] for r in reqs]) / rate * 1e6
             t0 = srv.now_us() + 1000.0
-            tickets = []
             for i, r in enumerate(reqs):
                 if times is not None:
                     target = t0 + times[i]
                     while srv.now_us() < target:
-                        pass
-                out = self._out(r["M"], r["N"])
-                tickets.append(srv.submit(r["tenant"], handles[(r["N"], r["K"], r["sparse"])],
-                                          r["M"], self.X.data_ptr(), ld, out, r["N"]))
-            res = [srv.wait(t, 60) for t in tickets]
+                        collect(False)
+                while not free or (rate is None and inflight >= window):
+                    if not collect(False):
+                        oldest = min((q for q in pend if q), key=lambda q: q[0][2])
+                        r0 = srv.wait(oldest[0][0], 60)
+                        t_, slot, j = oldest.popleft()
+                        res[j] = r0
+                        free.append(slot)
+                        inflight -= 1
+                slot = free.pop()
+                x = xb + 4 * r["row"] * ld
+                tk = srv.submit(r["tenant"], handles[(r["N"], r["K"], r["sparse"])], r["M"], x, ld,
+                                ob + 2 * slot * self.slot_elems, r["N"])
+                pend[r["tenant"]].append((tk, slot, i))
+                inflight += 1
+            while inflight:
+                collect(True)
             stats = srv.stats()
         finally:
             srv.close()
@@ -370,13 +471,13 @@ class ServingBench:
 
     def isolated(self, reqs):
         """Latency of each request run alone (per-call server, one at a time)."""
-        srv, handles = self._server("per_call")
+        srv, handles = self._server(dict(batching=False))
         ld = self.X.stride(0)
         out = []
         try:
             for r in reqs:
                 t = srv.submit(r["tenant"], handles[(r["N"], r["K"], r["sparse"])], r["M"],
-                               self.X.data_ptr(), ld, self._out(r["M"], r["N"]), r["N"])
+                               self.X.data_ptr() + 4 * r["row"] * ld, ld, self.outs.data_ptr(), r["N"])
                 x = srv.wait(t, 60)
                 out.append(x.t_end_us - x.t_submit_us)
         finally:
@@ -384,44 +485,52 @@ class ServingBench:
         return np.array(out)
 
 
-def serving_report(gb, dev, n_cap=1500, n_load=1500, loads=(0.8,)):
-    """Capacity of each serving mode, then the same seeded Poisson trace
-    offered at each fraction of the per-call capacity in `loads`.  The first
-    load's results sit at the top level; further loads under "other_loads"."""
+def serving_report(gb, dev, n_cap=20000, n_load=20000, loads=(0.8,), n_iso=2000):
+    """Capacity of each serving mode (closed loop, 96 requests in flight),
+    then the same seeded Poisson trace of n_load requests offered at each
+    fraction of the lowest capacity in `loads`.  Slowdown = latency / the
+    request's latency alone, measured for the first n_iso requests; Jain's
+    index and the paper's fairness 1 - (max - min) / mean and min / max are
+    taken over the tenants' mean slowdowns (tenants of very different sizes
+    are compared by how much the mix slows each down).  The first load's
+    results sit at the top level; further loads under "other_loads"."""
     from paper_2602_10262_gb300.server import overlap_efficiency
     sb = ServingBench(dev, gb)
+    modes = sb.modes()
     cap_reqs = sb.trace(n_cap, workloads.SEED_REQUESTS + 1)
     cap = {}
-    for mode in ServingBench.MODES:
-        sb.run(cap_reqs[:64], mode)                          # warm-up
-        _, span, stats, _ = sb.run(cap_reqs, mode)
+    for mode, cfg in modes.items():
+        sb.run(cap_reqs[:256], cfg)                          # warm-up
+        _, span, stats, _ = sb.run(cap_reqs, cfg)
         cap[mode] = {"tflops": sb.flops(cap_reqs) / (span * 1e-6) / 1e12,
                      "req_per_s": n_cap / (span * 1e-6),
                      "kernel_launches": stats["kernel_launches"], "batches": stats["batches"]}
     reqs = sb.trace(n_load, workloads.SEED_REQUESTS)
-    iso = sb.isolated(reqs)
+    iso = sb.isolated(reqs[:n_iso])
     tenant = np.array([r["tenant"] for r in reqs])
     out = {"workload": "Poisson two-tenant GEMM stream, M log-uniform [1,4096], "
                        "(N,K) in {4096,8192,14336}^2, 50% 2:4-sparse weights",
+           "requests_per_point": n_load, "modes": {m: {k: v for k, v in c.items()} for m, c in modes.items()},
            "capacity": cap}
     for i, load in enumerate(loads):
         base = min(cap, key=lambda m: cap[m]["req_per_s"])
         rate = load * cap[base]["req_per_s"]
         block = {"offered_load": f"{load} x {base} capacity = {rate:.0f} req/s"}
-        for mode in ServingBench.MODES:
-            lat, span, stats, res = sb.run(reqs, mode, rate)
-            slow = iso / lat
-            x = [float(np.mean(slow[tenant == t])) for t in (0, 1)]
-            mean_lat = [float(np.mean(lat[tenant == t])) for t in (0, 1)]
+        for mode, cfg in modes.items():
+            lat, span, stats, res = sb.run(reqs, cfg, rate)
+            slow = lat[:n_iso] / iso
+            t_iso = tenant[:n_iso]
+            x = [float(np.mean(slow[t_iso == t])) for t in (0, 1)]              # mean slowdown
+            y = [float(np.mean(1.0 / slow[t_iso == t])) for t in (0, 1)]        # isolated / observed
             block[mode] = {
                 "p50_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 50)) for t in (0, 1)},
                 "p99_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 99)) for t in (0, 1)},
                 "p99_all_us": float(np.percentile(lat, 99)),
+                "mean_slowdown": {f"tenant{t}": x[t] for t in (0, 1)},
                 "tflops": sb.flops(reqs) / (span * 1e-6) / 1e12,
-                "jain": (sum(x) ** 2) / (2 * sum(v * v for v in x)),
-                "fairness_1_minus_range_over_mean":
-                    1.0 - (max(mean_lat) - min(mean_lat)) / np.mean(mean_lat),
-                "fairness_min_over_max": min(mean_lat) / max(mean_lat),
+                "jain": (sum(y) ** 2) / (2 * sum(v * v for v in y)),
+                "fairness_1_minus_range_over_mean": 1.0 - (max(x) - min(x)) / np.mean(x),
+                "fairness_min_over_max": min(x) / max(x),
                 "overlap_efficiency": overlap_efficiency(res),
                 "mean_batch": float(np.mean([r.batch_size for r in res])),
                 "kernel_launches": stats["kernel_launches"],
@@ -432,8 +541,6 @@ def serving_report(gb, dev, n_cap=1500, n_load=1500, loads=(0.8,)):
             out.setdefault("other_loads", {})[str(load)] = block
     return out
 
-
-# ------------------------------------------------------------------ shape sweep
 
 def _l2_copies(dev, set_bytes):
     """Operand sets to rotate through so that one pass streams at least twice
@@ -776,7 +883,66 @@ def format_sweep(gb, dev):
     return {"dense": rows, "quantize": quant}
 
 
-SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency")
+def mx_sweep(gb, dev):
+    """Block-scaled (MX, one E8M0 scale per 32 elements of K) against per-row
+    scaled E4M3 on the same shapes: device time per call with L2-cold
+    operand rotation, bf16 out."""
+    rows = []
+    for M, N, K in ((4096, 4096, 4096), (8192, 8192, 8192), (16384, 16384, 16384), (16, 8192, 8192),
+                    (128, 8192, 8192), (2048, 2048, 2048)):
+        n = _l2_copies(dev, M * K + N * K)
+        mx_fns, row_fns, keep = [], [], []
+        for i in range(n):
+            g = torch.Generator(device=dev).manual_seed(100 + i)
+            x = torch.randn((M, K), generator=g, device=dev)
+            w = torch.randn((N, K), generator=g, device=dev)
+            A, SA = gb.fp8_quantize_mx(x, gb.E4M3, scale_layout=1)
+            B, SB = gb.fp8_quantize_mx(w, gb.E4M3, scale_layout=1)
+            Ar, dA = gb.fp8_quantize_e4m3(x, 1)
+            Br, dB = gb.fp8_quantize_e4m3(w, 1)
+            del x, w
+            C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+            keep += [A, SA, B, SB, Ar, dA, Br, dB, C]
+            mx_fns.append(lambda A=A, SA=SA, B=B, SB=SB, C=C: gb.gemm_fp8_mx(A, SA, B, SB, 1.0, gb.OUT_BF16, C=C))
+            row_fns.append(lambda A=Ar, dA=dA, B=Br, dB=dB, C=C: gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 1.0,
+                                                                                    gb.OUT_BF16, C=C))
+        ms_mx, ms_row = _time_ms(mx_fns), _time_ms(row_fns)
+        f = 2.0 * M * N * K
+        rows.append({"M": M, "N": N, "K": K, "mx_us": ms_mx * 1e3, "per_row_us": ms_row * 1e3,
+                     "mx_tflops": f / ms_mx / 1e9, "per_row_tflops": f / ms_row / 1e9,
+                     "mx_over_per_row": ms_row / ms_mx, "operand_copies": n})
+        del keep, mx_fns, row_fns
+    return rows
+
+
+def serving_policy_sweep(gb, dev, n=20000, load=0.8):
+    """The batched server with the bulk tenant leaving R SMs free for the
+    latency tenant, R in {0, 8, 16, 24, 32}, against per-call serving, on
+    one seeded Poisson trace at `load` x the per-call capacity."""
+    sb = ServingBench(dev, gb)
+    sms = gb.fp8_device_sm_count()
+    reqs = sb.trace(n, workloads.SEED_REQUESTS)
+    tenant = np.array([r["tenant"] for r in reqs])
+    sb.run(reqs[:256], dict(batching=False))
+    _, span, _, _ = sb.run(reqs, dict(batching=False))
+    rate = load * n / (span * 1e-6)
+    out = {"offered_req_per_s": rate, "requests": n, "rows": []}
+    cfgs = [("per_call", dict(batching=False))] + \
+        [(f"batched_reserve_{r}", dict(batching=True, bulk_max_ctas=(sms - r) if r else 0))
+         for r in (0, 8, 16, 24, 32)]
+    for name, cfg in cfgs:
+        lat, span, _, _ = sb.run(reqs, cfg, rate)
+        _, cspan, _, _ = sb.run(reqs[:8000], cfg)
+        out["rows"].append({"mode": name,
+                            "p99_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 99)) for t in (0, 1)},
+                            "p50_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 50)) for t in (0, 1)},
+                            "p99_all_us": float(np.percentile(lat, 99)),
+                            "capacity_req_per_s": 8000 / (cspan * 1e-6)})
+    return out
+
+
+SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency", "mx",
+                  "serving_policy")
 
 
 def sweep(gb, dev, sections=SWEEP_SECTIONS):
@@ -796,6 +962,10 @@ def sweep(gb, dev, sections=SWEEP_SECTIONS):
         out["serving"] = serving_report(gb, dev, loads=(0.8, 0.5, 0.95))
     if "concurrency" in sections:
         out["concurrency"] = concurrency_sweep(gb, dev)
+    if "mx" in sections:
+        out["mx"] = mx_sweep(gb, dev)
+    if "serving_policy" in sections:
+        out["serving_policy"] = serving_policy_sweep(gb, dev)
     return out
 
 
@@ -1023,7 +1193,7 @@ def main():
     stop = torch.cuda.Event(enable_timing=True)
     barrier(ws)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local, gpu_uuid(dev)) as clocks:
         start.record(stream)
         for i in range(args.steps):
             step(recs[i])

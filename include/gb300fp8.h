@@ -137,6 +137,56 @@ typedef struct {
 int fp8_quantize_e4m3_rows_grouped(const fp8_quant_job *jobs, int num_jobs, fp8_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Block-scaled FP8 (the OCP Microscaling "MX" formats MXFP8 E4M3 / E5M2).
+ * The paper measures FP8 with one scale per tensor or channel; this is the
+ * next precision step on the same tensor cores (tcgen05 kind::mxf8f6f4),
+ * with one power-of-two scale per 32 consecutive elements along K.
+ *
+ * fp8_quantize_mx: x device fp32 [rows, cols], row stride ldx, cols % 32 == 0
+ * (FP8_ERR_SHAPE otherwise).  For each row and block b of 32 columns:
+ * amax = max|x| over the block; amax == 0 gives scale code 0 and the codes
+ * of the block's signed zeros; otherwise e = floor(log2 amax) - emax (emax 8
+ * for E4M3, 15 for E5M2) clamped to [-127, 127], scale code e + 127 (E8M0:
+ * the scale 2^(code - 127)), and codes = the format's round-to-nearest-even,
+ * saturating encoding of fl32(x * 2^-e).  So amax * 2^-e lies in
+ * [2^emax, 2^(emax+1)) and a block maximum above the format's largest value
+ * saturates to it.  format: an fp8_format.  q: device [rows, cols], row
+ * stride ldq.  scales: device bytes, in one of two layouts:
+ *   scale_layout 0, row-major: [rows, cols / 32], scale of (r, b) at
+ *     r * (cols / 32) + b;
+ *   scale_layout 1, tiled (what gemm_fp8_mx reads; 16-byte aligned,
+ *     fp8_mx_scale_tiled_bytes(rows, cols) bytes): 512-byte chunks, one per
+ *     128 rows x 128 columns, chunk (r / 128) * ceil(cols / 128) + b / 4;
+ *     within it the scale of (r, b) at 16 * (r % 32) + 4 * ((r % 128) / 32)
+ *     + b % 4 (the order in which the tensor core takes a 128 x 4 block of
+ *     scales).  Entries of rows >= rows or blocks >= cols / 32 hold 127 (1.0).
+ * NaN/Inf in x: FP8_ERR_NONFINITE in the device error word.
+ *
+ * fp8_mx_scales_to_tiled: row-major scales [rows, cols / 32] (contiguous)
+ * -> the tiled layout above (for scales produced elsewhere).
+ *
+ * gemm_fp8_mx: C[m,n] = alpha * sum over blocks b of 2^(SA[m,b] - 127) *
+ * 2^(SB[n,b] - 127) * sum_{k in b} decA(A[m,k]) decB(B[n,k]), accumulated in
+ * FP32 on the tensor cores, which apply the block scales.  A [M, K] (lda),
+ * B [N, K] (ldb) codes as in gemm_fp8_dense (16-byte aligned, strides
+ * multiples of 16); a_scales / b_scales: the tiled layout of A's and B's
+ * scales (16-byte aligned).  K % 32 == 0 (FP8_ERR_SHAPE otherwise).  C, ldc,
+ * out_dtype, formats and stream as gemm_fp8_dense_fmt.  Needs no workspace.
+ * ------------------------------------------------------------------------- */
+size_t fp8_mx_scale_tiled_bytes(int64_t rows, int64_t cols);
+
+int fp8_quantize_mx(const float *x, int64_t rows, int64_t cols, int64_t ldx, int format,
+                    uint8_t *q, int64_t ldq, uint8_t *scales, int scale_layout, fp8_stream_t stream);
+
+int fp8_mx_scales_to_tiled(const uint8_t *scales, int64_t rows, int64_t cols, uint8_t *tiled,
+                           fp8_stream_t stream);
+
+int gemm_fp8_mx(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
+                const uint8_t *a_scales, const uint8_t *B, int64_t ldb, const uint8_t *b_scales,
+                float alpha, void *C, int64_t ldc, int out_dtype, int a_format, int b_format,
+                fp8_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * 2:4 prune + compress (row a3).  Paper: section 2 "Structured Sparsity",
  * section 6 (2 of every 4 consecutive elements along K are zero; the paper
  * blames a fixed conversion + allocation + dispatch cost in section 6.1.1 —
@@ -387,11 +437,16 @@ int gemm_fp8_grouped_graph_destroy(fp8_grouped_graph *graph);
  *
  * A scheduler thread owns the GPU work.  Each tenant has its own CUDA stream;
  * the latency tenant's stream has the highest priority.  Whenever one of a
- * tenant's in-flight slots frees, the requests that arrived meanwhile (FIFO,
- * up to max_batch) are admitted if their workspace (M x K codes + M scales)
- * fits in the server's device pool, quantised by one grouped launch and
- * multiplied by one grouped persistent GEMM launch.  Bulk tenants' GEMMs may
- * be capped at bulk_max_ctas CTAs so latency work runs beside them.  With
+ * bulk tenant's in-flight slots frees, the requests that arrived meanwhile
+ * (FIFO, up to max_batch) are admitted if their workspace (M x K codes + M
+ * scales) fits in the server's device pool, quantised by one grouped launch
+ * and multiplied by one grouped persistent GEMM launch.  The latency tenant
+ * is not held to an in-flight limit: its requests go out as soon as they are
+ * admitted, in batches of at most latency_max_batch.  Bulk tenants' GEMMs may
+ * be capped at bulk_max_ctas CTAs so latency work finds free SMs beside
+ * them (a persistent GEMM keeps its SMs until its last tile).  The
+ * scheduler builds each batch under the server's lock and enqueues it
+ * without holding it, so submit, poll and wait never wait on a launch.  With
  * batching = 0 every request is launched on its own as soon as it is
  * admitted (one quantise + one GEMM launch per request: the per-call
  * baseline).  A request's result does not depend on what it was batched
@@ -409,10 +464,13 @@ typedef struct {
     int latency_tenant;       /* tenant given the high-priority stream (-1: none) */
     int batching;             /* 1: continuous batching; 0: one launch per request */
     int max_batch;            /* requests per batch, 1..FP8_GROUPED_MAX_PROBLEMS (0: max) */
-    int max_inflight;         /* in-flight batches per tenant (0: 4) */
+    int max_inflight;         /* in-flight batches per bulk tenant (0: 4) */
     int bulk_max_ctas;        /* CTA cap for non-latency tenants' GEMMs (0: all SMs) */
     size_t pool_bytes;        /* workspace pool; 0: free HBM minus reserve_bytes */
     size_t reserve_bytes;     /* HBM left untouched when sizing the pool (0: 1 GiB) */
+    int latency_max_batch;    /* with batching: requests per batch of the latency
+                                 tenant (0: 1, i.e. each of its requests is
+                                 launched on its own as soon as it is admitted) */
 } fp8_server_config;
 
 typedef struct fp8_server fp8_server;

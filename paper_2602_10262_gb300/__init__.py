@@ -22,7 +22,8 @@ __all__ = [
     "gemm_fp8_sparse24_fmt", "gemm_fp8_grouped", "gemm_fp8_grouped_ex", "fp8_last_device_error",
     "fp8_device_sm_count", "fp8_test_stall_gemm_loads", "fp8_gemm_set_tile_config", "gemm_fp8_grouped_autotune",
     "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
-    "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2",
+    "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2", "fp8_quantize_mx", "fp8_mx_scales_to_tiled",
+    "fp8_mx_scale_tiled_bytes", "gemm_fp8_mx",
 ]
 
 OUT_F32 = 0
@@ -143,6 +144,77 @@ def fp8_quantize_e5m2(x: torch.Tensor, scale_mode: int, q: Optional[torch.Tensor
                       dequant_scale: Optional[torch.Tensor] = None, stream=None):
     """fp32 [R, C] -> (E5M2 codes uint8 [R, C], dequant scales fp32 [1] or [R])."""
     return _quantize("fp8_quantize_e5m2", x, scale_mode, q, dequant_scale, stream)
+
+
+def fp8_mx_scale_tiled_bytes(rows: int, cols: int) -> int:
+    """Bytes of the tiled E8M0 scale layout of a [rows, cols] operand."""
+    return int(library().fp8_mx_scale_tiled_bytes(int(rows), int(cols)))
+
+
+def fp8_quantize_mx(x: torch.Tensor, fmt: int = E4M3, scale_layout: int = 1,
+                    q: Optional[torch.Tensor] = None, scales: Optional[torch.Tensor] = None,
+                    stream=None):
+    """Block-scaled quantisation: fp32 [R, C] (C % 32 == 0) -> (codes uint8
+    [R, C], E8M0 scale codes: uint8 [R, C / 32] for scale_layout 0, the tiled
+    bytes gemm_fp8_mx reads for scale_layout 1)."""
+    _dev(x, "x", torch.float32, 2)
+    R, C = x.shape
+    if q is None:
+        q = torch.empty((R, C), dtype=torch.uint8, device=x.device)
+    _dev(q, "q", torch.uint8, 2)
+    _shape(q, "q", (R, C))
+    if scale_layout == 0:
+        shape = (R, C // 32)
+    else:
+        shape = (fp8_mx_scale_tiled_bytes(R, C),)
+    if scales is None:
+        scales = torch.empty(shape, dtype=torch.uint8, device=x.device)
+    _shape(scales, "scales", shape)
+    _packed(scales, "scales")
+    rc = library().fp8_quantize_mx(_p(x), R, C, _ld(x), int(fmt), _p(q), _ld(q), _p(scales),
+                                   int(scale_layout), _stream(stream))
+    _check(rc, "fp8_quantize_mx")
+    return q, scales
+
+
+def fp8_mx_scales_to_tiled(scales: torch.Tensor, rows: int, cols: int,
+                           tiled: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Row-major E8M0 scales [rows, cols / 32] -> the tiled layout."""
+    _dev(scales, "scales", torch.uint8, 2)
+    _shape(scales, "scales", (rows, cols // 32))
+    _packed(scales, "scales")
+    n = fp8_mx_scale_tiled_bytes(rows, cols)
+    if tiled is None:
+        tiled = torch.empty((n,), dtype=torch.uint8, device=scales.device)
+    _shape(tiled, "tiled", (n,))
+    rc = library().fp8_mx_scales_to_tiled(_p(scales), int(rows), int(cols), _p(tiled), _stream(stream))
+    _check(rc, "fp8_mx_scales_to_tiled")
+    return tiled
+
+
+def gemm_fp8_mx(A: torch.Tensor, a_scales: torch.Tensor, B: torch.Tensor, b_scales: torch.Tensor,
+                alpha: float = 1.0, out_dtype: int = OUT_BF16, a_format: int = E4M3,
+                b_format: int = E4M3, C: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Block-scaled GEMM: C[M, N] = alpha * sum_b 2^sa 2^sb dec(A) dec(B)^T over
+    32-element blocks; a_scales / b_scales in the tiled layout."""
+    _dev(A, "A", torch.uint8, 2)
+    _dev(B, "B", torch.uint8, 2)
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("K mismatch")
+    for t, nm, rows in ((a_scales, "a_scales", M), (b_scales, "b_scales", N)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8:
+            raise TypeError(f"{nm} must be a uint8 CUDA tensor")
+        _packed(t, nm)
+        if t.numel() < fp8_mx_scale_tiled_bytes(rows, K):
+            raise ValueError(f"{nm} must hold {fp8_mx_scale_tiled_bytes(rows, K)} bytes")
+    C = _out(C, M, N, out_dtype, A.device)
+    rc = library().gemm_fp8_mx(M, N, K, _p(A), _ld(A), _p(a_scales), _p(B), _ld(B), _p(b_scales),
+                               float(alpha), _p(C), _ld(C), int(out_dtype), int(a_format), int(b_format),
+                               _stream(stream))
+    _check(rc, "gemm_fp8_mx")
+    return C
 
 
 def prune24_compress(a: torch.Tensor, a_vals: Optional[torch.Tensor] = None,

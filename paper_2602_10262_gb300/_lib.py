@@ -51,7 +51,8 @@ class FP8ServerConfig(ctypes.Structure):
     """Mirror of ``fp8_server_config``."""
     _fields_ = [("num_tenants", I32), ("latency_tenant", I32), ("batching", I32),
                 ("max_batch", I32), ("max_inflight", I32), ("bulk_max_ctas", I32),
-                ("pool_bytes", ctypes.c_size_t), ("reserve_bytes", ctypes.c_size_t)]
+                ("pool_bytes", ctypes.c_size_t), ("reserve_bytes", ctypes.c_size_t),
+                ("latency_max_batch", I32)]
 
 
 class FP8Request(ctypes.Structure):
@@ -83,6 +84,10 @@ SIGNATURES = {
     "fp8_test_stall_gemm_loads": (I32, [I32, ctypes.c_double]),
     "fp8_quantize_e4m3": (I32, [P, I64, I64, I64, I32, P, I64, P, P]),
     "fp8_quantize_e5m2": (I32, [P, I64, I64, I64, I32, P, I64, P, P]),
+    "fp8_mx_scale_tiled_bytes": (ctypes.c_size_t, [I64, I64]),
+    "fp8_quantize_mx": (I32, [P, I64, I64, I64, I32, P, I64, P, I32, P]),
+    "fp8_mx_scales_to_tiled": (I32, [P, I64, I64, P, P]),
+    "gemm_fp8_mx": (I32, [I64, I64, I64, P, I64, P, P, I64, P, F32, P, I64, I32, I32, I32, P]),
     "prune24_compress": (I32, [P, I64, I64, I64, P, P, P]),
     "prune24_decompress": (I32, [P, P, I64, I64, P, P]),
     "gemm_fp8_dense": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32, P]),

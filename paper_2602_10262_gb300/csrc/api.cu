@@ -9,10 +9,12 @@ namespace {
 constexpr int kMaxDevices = 64;
 
 __device__ int g_error_word;
+__device__ float g_one = 1.0f;
 
 struct DeviceInfo {
     std::once_flag once;
     int* err = nullptr;
+    float* one = nullptr;
     int sms = 0;
     int major = 0, minor = 0;
 };
@@ -28,6 +30,8 @@ DeviceInfo* info()
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_error_word) == cudaSuccess)
             d->err = static_cast<int*>(p);
+        if (cudaGetSymbolAddress(&p, g_one) == cudaSuccess)
+            d->one = static_cast<float*>(p);
         cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&d->major, cudaDevAttrComputeCapabilityMajor, dev);
         cudaDeviceGetAttribute(&d->minor, cudaDevAttrComputeCapabilityMinor, dev);
@@ -40,6 +44,12 @@ int* device_error_word()
 {
     DeviceInfo* d = info();
     return d ? d->err : nullptr;
+}
+
+const float* device_one()
+{
+    DeviceInfo* d = info();
+    return d ? d->one : nullptr;
 }
 
 int sm_count()

@@ -21,6 +21,11 @@ __device__ __forceinline__ void report_device_error(int* err_word, int code)
 // the lookup failed.
 int* device_error_word();
 
+// Address of a device float holding 1.0 on the current device (scale
+// operand of products that carry no per-row scales); nullptr if the lookup
+// failed.
+const float* device_one();
+
 // SM count of the current device (cached per device).
 int sm_count();
 

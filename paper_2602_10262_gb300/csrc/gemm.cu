@@ -83,7 +83,11 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 // (2 KB each), then the B chunks: 4 / 5 / 7 / 8 stages for BNC = 128 / 64 /
 // 32 / 16, each k-block's metadata in its own 4 TMEM columns.  Launches
 // mixing dense and sparse problems, BNC = 256 and MT = 2 keep KC = 1.
-template <int MT, bool SP = false, int BNC = BN_MAX, int KC = 1>
+// MX: block-scaled launches (kind::mxf8f6f4): 128 x 128 tiles, dense codes
+// as above, and per k-block two 512-byte chunks of E8M0 scales after the B
+// chunks (A's 128 rows, then B's), copied into a ring of TMEM columns
+// 128..255 (8 per k-block: A's 4 then B's 4) beside the first accumulator.
+template <int MT, bool SP = false, int BNC = BN_MAX, int KC = 1, bool MX = false>
 struct Cfg {
     static constexpr bool kSparse2 = MT == 2 && SP;
     static constexpr int kStages =
@@ -99,7 +103,10 @@ struct Cfg {
     static constexpr int kBChunk = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : BNC * BK;
     static constexpr int kABytes = KC * kAChunk;
     static constexpr int kBBytes = KC * kBChunk;
-    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kSfChunk = 512;                        // scales of 128 rows x one k-block
+    static constexpr int kSfBytes = MX ? KC * 2 * kSfChunk : 0;
+    static constexpr int kSfCol0 = BNC;                         // MX: scale ring in TMEM columns
+    static constexpr int kStageBytes = kABytes + kBBytes + kSfBytes;
     static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : (BNC == 256 ? SPARSE_BN_MAX : BNC);
     static constexpr int kAcc = MT == 2 ? 1 : 2;                  // accumulator buffers
     static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
@@ -115,6 +122,8 @@ struct Cfg {
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
     static_assert(KC == 1 || (KC == 2 && MT == 1 && BNC <= 128), "two-chunk stages: 128-row tiles");
     static_assert(kBChunk % 1024 == 0, "B chunks stay swizzle-atom aligned");
+    static_assert(!MX || (MT == 1 && !SP && BNC == 128), "block-scaled launches: 128 x 128 dense tiles");
+    static_assert(!MX || kSfCol0 + 8 * kStages * KC <= BN_MAX, "scale ring fits beside the first accumulator");
 };
 
 // Everything of a problem but its tensor maps.  Each role thread copies this
@@ -142,6 +151,9 @@ struct ProblemScalars {
     int ctr_off;            // split-K: first tile counter of this problem
     int tile_start;         // first work unit (tile x slice) of this problem
     uint32_t idesc;
+    const uint8_t* sfp;     // block-scaled only: tiled E8M0 scales of P and Q (512-byte
+    const uint8_t* sfq;     // chunks, sf_kb per 128-row tile)
+    int sf_kb;
 };
 
 struct Problem : ProblemScalars {
@@ -517,11 +529,11 @@ __device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P,
 
 // ---------------------------------------------------------------- kernel
 
-template <int MAXP, int MT, bool SP, int BNC, int KC>
-__global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
+template <int MAXP, int MT, bool SP, int BNC, int KC, bool MX = false>
+__global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
     gemm_fp8_kernel(const __grid_constant__ Params<MAXP> prm)
 {
-    using C = Cfg<MT, SP, BNC, KC>;
+    using C = Cfg<MT, SP, BNC, KC, MX>;
     constexpr int S = C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -635,9 +647,11 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                         abort_pipeline(abort_flag, err);
                         break;
                     }
-                    // a 3-D box always lands all KC chunks (those past K as zeros)
+                    // a 3-D box always lands all KC chunks (those past K as zeros);
+                    // block scales come for the nck k-blocks of the stage only
                     mbar_arrive_expect_tx(full_bar(stage),
-                                          chunk_bytes * static_cast<uint32_t>(KC > 1 && P.tma3d ? KC : nck));
+                                          chunk_bytes * static_cast<uint32_t>(KC > 1 && P.tma3d ? KC : nck) +
+                                              (MX ? 2u * C::kSfChunk * static_cast<uint32_t>(nck) : 0u));
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
                     if (sparse && KC > 1) {
                         // kept codes then metadata of all KC k-blocks (3-D chunk boxes)
@@ -662,6 +676,15 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                             if (c < nck)
                                 tma_load_2d(sa + C::kABytes + c * b_chunk, map_q, full_bar(stage), (kb + c) * BK,
                                             col0);
+                    }
+                    if constexpr (MX) {
+                        // the k-blocks of one 128-row tile are consecutive chunks
+                        const uint32_t sf = sa + C::kABytes + C::kBBytes;
+                        const size_t chunk_p = static_cast<size_t>(tc.m_blk) * P.sf_kb + kb;
+                        const size_t chunk_q = static_cast<size_t>(tc.n_blk) * P.sf_kb + kb;
+                        bulk_load(sf, P.sfp + chunk_p * C::kSfChunk, C::kSfChunk * nck, full_bar(stage));
+                        bulk_load(sf + KC * C::kSfChunk, P.sfq + chunk_q * C::kSfChunk, C::kSfChunk * nck,
+                                  full_bar(stage));
                     }
                     armed |= 1u << stage;
                     if (++stage == S) {
@@ -718,8 +741,27 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC>::kThreads, 1)
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
-                    const uint64_t bdesc = sdesc_kmajor_sw128(sa + C::kABytes);
-                    if (sparse) {
+                    if constexpr (MX) {
+#pragma unroll
+                        for (int c = 0; c < KC; ++c) {
+                            if (c >= nck)
+                                break;
+                            // scales of k-block c (A's 128 rows, B's 128 rows) -> their
+                            // ring columns, each 32-row group to every lane quarter
+                            const uint32_t sf_col = static_cast<uint32_t>(C::kSfCol0 + 8 * (stage * KC + c));
+                            const uint32_t sm_sf = sa + C::kABytes + C::kBBytes + c * C::kSfChunk;
+                            tmem_cp_32x128b_warpx4(tmem_base + sf_col, sdesc_rows16_noswizzle(sm_sf));
+                            tmem_cp_32x128b_warpx4(tmem_base + sf_col + 4u,
+                                                   sdesc_rows16_noswizzle(sm_sf + KC * C::kSfChunk));
+                            const uint64_t adesc = sdesc_kmajor_sw128(sa + c * C::kAChunk);
+                            const uint64_t bdesc_c = sdesc_kmajor_sw128(sa + C::kABytes + c * b_chunk);
+#pragma unroll
+                            for (int k = 0; k < BK / 32; ++k)
+                                mma_mx_f8f6f4(d_tmem, adesc + 2u * k, bdesc_c + 2u * k,
+                                              mx_sf_ids(idesc, static_cast<uint32_t>(k)), tmem_base + sf_col,
+                                              tmem_base + sf_col + 4u, (first | c | k) != 0 ? 1u : 0u);
+                        }
+                    } else if (sparse) {
 #pragma unroll
                         for (int c = 0; c < KC; ++c) {
                             if (c >= nck)
@@ -1047,6 +1089,8 @@ struct Job {
     int out_bf16;
     int trans_out;
     int fmt_p, fmt_q;       // fp8_format of P and Q (instruction-descriptor A / B format)
+    const uint8_t* sfp;     // block-scaled problems: tiled E8M0 scales of P and Q
+    const uint8_t* sfq;     // (nullptr otherwise)
 };
 
 bool valid_format(int f)
@@ -1118,7 +1162,7 @@ int slice_kblocks(int k_blocks, int s)
 int split_count(const Job& j)
 {
     const int sms = sm_count();
-    if (!splits_k(j.rows_p, j.rows_q, j.K))
+    if (j.sfp != nullptr || !splits_k(j.rows_p, j.rows_q, j.K))
         return 1;
     const int64_t tiles = problem_tiles(j.rows_p, j.rows_q, j.K);
     const int k_blocks = static_cast<int>((j.K + BK - 1) / BK);
@@ -1183,6 +1227,12 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
     pr.kb_per_split = pr.splits > 1 ? slice_kblocks(pr.k_blocks, pr.splits) : pr.k_blocks;
     pr.splits = (pr.k_blocks + pr.kb_per_split - 1) / pr.kb_per_split;     // no empty slice
     pr.idesc = idesc_f8_f32(BM, bn, pr.sparse != 0, 0, mma_format(j.fmt_p), mma_format(j.fmt_q));
+    if (j.sfp) {
+        pr.idesc = idesc_mx_f8(BM, bn, mma_format(j.fmt_p), mma_format(j.fmt_q));
+        pr.sfp = j.sfp;
+        pr.sfq = j.sfq;
+        pr.sf_kb = pr.k_blocks;
+    }
     return FP8_OK;
 }
 
@@ -1235,10 +1285,10 @@ void bind_workspace(Params<MAXP>& prm, const Plan& pl, void* base)
     bind_workspace(prm, base, pl.ctr_count);
 }
 
-template <int MAXP, int MT, bool SP, int BNC = BN_MAX, int KC = 1>
+template <int MAXP, int MT, bool SP, int BNC = BN_MAX, int KC = 1, bool MX = false>
 int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
 {
-    using C = Cfg<MT, SP, BNC, KC>;
+    using C = Cfg<MT, SP, BNC, KC, MX>;
     static std::once_flag attr_once[64];
     int dev = 0;
     GB_CUDA_OK(cudaGetDevice(&dev));
@@ -1246,7 +1296,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
         return FP8_ERR_UNSUPPORTED;
     cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once[dev], [&] {
-        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC>,
+        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC, MX>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     });
     GB_CUDA_OK(attr_err);
@@ -1273,7 +1323,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
-    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC>);
+    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC, MX>);
     out->ring_bytes = static_cast<size_t>(C::kStages) * C::kStageBytes;
     out->grid = grid;
     out->threads = C::kThreads;
@@ -1433,7 +1483,7 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
             c.mt = ok2 && 2 * tiles2 >= sm_count() ? 2 : 1;
         }
     }
-    if (mixed_kinds(jobs, n))
+    if (mixed_kinds(jobs, n) || (n > 0 && jobs[0].sfp != nullptr))
         c.mt = 1;
     if (c.group_m <= 0)
         c.group_m = GROUP_M_DEFAULT;
@@ -1467,6 +1517,13 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
     }
     prm.num_problems = n;
     prm.group_m = c.group_m;
+    if (n > 0 && jobs[0].sfp != nullptr) {
+        // block-scaled launches (single problems): 128 x 128 tiles
+        if constexpr (MAXP == 1)
+            return kc == 2 ? plan<MAXP, 1, false, 128, 2, true>(prm, max_ctas, pl)
+                           : plan<MAXP, 1, false, 128, 1, true>(prm, max_ctas, pl);
+        return FP8_ERR_UNSUPPORTED;
+    }
     if (c.mt == 1) {
         if (kc == 2 && all_sparse) {
             if (max_bn <= 16)
@@ -1892,6 +1949,50 @@ extern "C" int gemm_fp8_dense_noalloc(int64_t M, int64_t N, int64_t K, const uin
     if (bytes)
         GB_CUDA_OK(cudaMemsetAsync(prm.ctr, 0, pl.ctr_count * sizeof(unsigned), st));
     return launch_plan(prm, pl, st);
+}
+
+extern "C" int gemm_fp8_mx(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda,
+                           const uint8_t* a_scales, const uint8_t* B, int64_t ldb, const uint8_t* b_scales,
+                           float alpha, void* C, int64_t ldc, int out_dtype, int a_format, int b_format,
+                           fp8_stream_t stream)
+{
+    using namespace gb300;
+    if (!valid_format(a_format) || !valid_format(b_format))
+        return FP8_ERR_INVALID;
+    if (M < 0 || N < 0 || K < 0 || (out_dtype != 0 && out_dtype != 1))
+        return FP8_ERR_INVALID;
+    if (M == 0 || N == 0)
+        return FP8_OK;
+    if (!C)
+        return FP8_ERR_INVALID;
+    if (ldc < N || K % 32 != 0 || M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
+        return FP8_ERR_SHAPE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (K == 0) {
+        if (!device_supported())
+            return FP8_ERR_UNSUPPORTED;
+        return write_zeros(C, ldc, M, N, out_dtype, st);
+    }
+    if (!A || !B || !a_scales || !b_scales)
+        return FP8_ERR_INVALID;
+    if (lda < K || ldb < K)
+        return FP8_ERR_SHAPE;
+    if (!aligned16(A) || !aligned16(B) || lda % 16 || ldb % 16 || !aligned16(a_scales) || !aligned16(b_scales))
+        return FP8_ERR_ALIGN;
+    if (!device_supported() || !device_one())
+        return FP8_ERR_UNSUPPORTED;
+    // no per-row scales: both scale operands read a device 1.0, so the
+    // epilogue stores alpha * acc
+    const float* one = device_one();
+    Job j = make_job(M, N, K, A, lda, nullptr, B, ldb, one, 0, one, 0, alpha, C, ldc, out_dtype, 0, a_format,
+                     b_format);
+    const bool swapped = M <= 128 && N > M;          // make_job's rule for small-M dense products
+    j.sfp = swapped ? b_scales : a_scales;
+    j.sfq = swapped ? a_scales : b_scales;
+    const int bn = 128;
+    Params<1> prm;
+    memset(&prm, 0, sizeof(prm));
+    return run_jobs(prm, &j, &bn, 1, 0, st);
 }
 
 extern "C" int gemm_fp8_sparse24(int64_t M, int64_t N, int64_t K, const uint8_t* a_vals,

@@ -183,6 +183,17 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// Plain bulk copy global -> shared (no tensor map): `bytes` (a multiple of
+// 16) from a 16-byte aligned global address to a 16-byte aligned shared
+// address; completion as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // 2-D tiled store of one box from shared memory (bulk-group completion).
 // x = innermost coordinate; elements outside the tensor are not written.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int32_t x, int32_t y)
@@ -271,6 +282,22 @@ __device__ __forceinline__ void mma_sp_f8f6f4(uint32_t d_tmem, uint64_t adesc, u
         "setp.ne.b32 p, %5, 0;\n\t"
         "tcgen05.mma.sp.cta_group::1.kind::f8f6f4 [%0], %1, %2, [%3], %4, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(meta_tmem), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Block-scaled variant (kind::mxf8f6f4, one E8M0 scale per 32 elements of K
+// per row of A and of B): the scales of this MMA's K = 32 step are read from
+// tensor memory at sfa_tmem / sfb_tmem, the byte within each 32-bit column
+// chosen by the scale-factor ids of the instruction descriptor.
+__device__ __forceinline__ void mma_mx_f8f6f4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t sfa_tmem, uint32_t sfb_tmem, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa_tmem), "r"(sfb_tmem), "r"(accumulate)
         : "memory");
 }
 
@@ -375,6 +402,15 @@ __device__ __forceinline__ void tmem_cp_128x128b(uint32_t taddr, uint64_t sdesc)
     asm volatile("tcgen05.cp.cta_group::1.128x128b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
 }
 
+// Shared memory -> tensor memory: 32 rows x 128 bits, copied to each of the
+// four 32-lane quarters (row i to lanes i, 32 + i, 64 + i, 96 + i), four
+// consecutive 32-bit columns from taddr.  Ordered with the tcgen05.mma
+// instructions this thread issues afterwards.
+__device__ __forceinline__ void tmem_cp_32x128b_warpx4(uint32_t taddr, uint64_t sdesc)
+{
+    asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
 // Instruction descriptor, kind::f8f6f4: FP8 A and B, both K-major, F32
 // accumulator, M x N tile.
 //   bits 0-1 sparsity selector, bit 2 sparse flag, bits 4-5 D format (1 = F32),
@@ -389,6 +425,24 @@ __host__ __device__ constexpr uint32_t idesc_f8_f32(int M, int N, bool sparse, i
     return (static_cast<uint32_t>(selector) & 3u) | (sparse ? (1u << 2) : 0u) | (1u << 4) |
            ((a_fmt & 7u) << 7) | ((b_fmt & 7u) << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
            (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::mxf8f6f4 with block scaling: FP8 A and B,
+// both K-major, F32 accumulator (implied), E8M0 scale factors.
+//   bits 4-5 B scale-factor id, bits 7-9 A format, bits 10-12 B format,
+//   bit 15/16 A/B major (0 = K), bits 17-22 N >> 3, bit 23 scale format
+//   (1 = E8M0), bits 24-28 M >> 4, bits 29-30 A scale-factor id.
+// The ids pick the byte of each 32-bit scale column: the K = 32 step k of a
+// 128-wide k-block uses byte k (mx_sf_ids).
+__host__ __device__ constexpr uint32_t idesc_mx_f8(int M, int N, uint32_t a_fmt, uint32_t b_fmt)
+{
+    return ((a_fmt & 7u) << 7) | ((b_fmt & 7u) << 10) | (static_cast<uint32_t>(N >> 3) << 17) | (1u << 23) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__host__ __device__ constexpr uint32_t mx_sf_ids(uint32_t idesc, uint32_t k)
+{
+    return idesc | ((k & 3u) << 4) | ((k & 3u) << 29);
 }
 
 }  // namespace gb300

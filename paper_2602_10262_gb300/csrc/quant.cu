@@ -268,8 +268,222 @@ int quantize(const float* x, int64_t rows, int64_t cols, int64_t ldx, int scale_
     return FP8_OK;
 }
 
+// ---------------------------------------------------------------- block-scaled (MX)
+
+// Byte offset of the scale of row r, 32-element block b, in the tiled layout
+// (include/gb300fp8.h): 512-byte chunks per 128 rows x 128 columns, chunk
+// (r / 128, b / 4) at (r / 128) * kb + b / 4, and within a chunk row r % 32
+// at 16-byte row r % 32, 4-byte word (r % 128) / 32, byte b % 4.
+__device__ __forceinline__ int64_t mx_tiled_offset(int64_t r, int64_t b, int64_t kb)
+{
+    return 512 * ((r >> 7) * kb + (b >> 2)) + 16 * (r & 31) + 4 * ((r & 127) >> 5) + (b & 3);
+}
+
+// One warp quantises a 128-column window of one row at a time: lane l
+// holds columns 4l .. 4l + 3, so the 32-element block j (of four) is lanes
+// 8j .. 8j + 7, and its amax is an 8-lane max reduction.  For a non-zero
+// block, e = floor(log2 amax) - emax (emax 8 for E4M3, 15 for E5M2) read
+// from amax's exponent field (a subnormal amax gives the floor -127), so
+// amax * 2^-e lies in [2^emax, 2^(emax+1)); the scale code is e + 127 and the
+// codes are the format's round-to-nearest-even, saturating encoding of the
+// IEEE product x * 2^-e (exact unless it falls below 2^-126).  An all-zero
+// block gets scale code 0 and the codes of its (signed) zeros.  Two windows
+// per iteration keep two 16-byte loads in flight per lane.
+template <int FMT, int TILED>
+__global__ void __launch_bounds__(kThreads) quant_mx_kernel(const float* __restrict__ x, int64_t rows,
+                                                            int64_t cols, int64_t ldx, uint8_t* __restrict__ q,
+                                                            int64_t ldq, uint8_t* __restrict__ sc, int vec,
+                                                            int qvec, int* err)
+{
+    grid_launch_dependents();
+    constexpr int kEmax = FMT == 1 ? 15 : 8;
+    constexpr int kU = 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t kb = (cols + 127) / 128;
+    const int64_t windows = rows * kb;
+    const int64_t warps = (static_cast<int64_t>(gridDim.x) * kThreads) >> 5;
+    const int64_t first = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
+    for (int64_t w0 = first; w0 < windows; w0 += kU * warps) {
+        float4 v[kU];
+        int64_t r[kU], c0[kU];
+        bool in[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t w = w0 + u * warps;
+            r[u] = w / kb;
+            c0[u] = (w - r[u] * kb) * 128 + 4 * lane;
+            in[u] = w < windows && c0[u] < cols;          // cols % 32 == 0: whole blocks in or out
+            v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (in[u]) {
+                const float* xr = x + r[u] * ldx + c0[u];
+                if (vec)
+                    v[u] = __ldg(reinterpret_cast<const float4*>(xr));
+                else
+                    v[u] = make_float4(xr[0], xr[1], xr[2], xr[3]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (w0 + u * warps >= windows)
+                break;                                    // the whole warp leaves together
+            uint32_t m = max(max(abs_bits(v[u].x), abs_bits(v[u].y)), max(abs_bits(v[u].z), abs_bits(v[u].w)));
+            m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, 1));
+            m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, 2));
+            m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, 4));
+            if (m >= kInfBits && (lane & 7) == 0)
+                report_device_error(err, FP8_ERR_NONFINITE);
+            uint32_t code = 0;
+            float s = 1.0f;
+            if (m != 0u && m < kInfBits) {
+                const int E = static_cast<int>(m >> 23);  // biased exponent of amax
+                const int e = E == 0 ? -127 : max(E - 127 - kEmax, -127);
+                code = static_cast<uint32_t>(e + 127);
+                s = __uint_as_float(static_cast<uint32_t>(127 - e) << 23);     // 2^-e, normal
+            }
+            if (in[u]) {
+                const uint32_t word = enc4<FMT>(v[u], s);
+                uint8_t* qd = q + r[u] * ldq + c0[u];
+                if (qvec) {
+                    *reinterpret_cast<uint32_t*>(qd) = word;
+                } else {
+                    qd[0] = word & 0xFFu;
+                    qd[1] = (word >> 8) & 0xFFu;
+                    qd[2] = (word >> 16) & 0xFFu;
+                    qd[3] = word >> 24;
+                }
+            }
+            // the four blocks' scale codes, from lanes 0, 8, 16, 24
+            const uint32_t s0 = __shfl_sync(0xFFFFFFFFu, code, 0), s1 = __shfl_sync(0xFFFFFFFFu, code, 8);
+            const uint32_t s2 = __shfl_sync(0xFFFFFFFFu, code, 16), s3 = __shfl_sync(0xFFFFFFFFu, code, 24);
+            if (lane == 0) {
+                const int64_t b0 = (c0[u] - 4 * lane) / 32;          // first block of the window
+                const int nb = static_cast<int>(min(static_cast<int64_t>(4), cols / 32 - b0));
+                const uint32_t sj[4] = {s0, s1, s2, s3};
+                if (TILED) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        word |= (j < nb ? sj[j] : 127u) << (8 * j);     // blocks past cols: scale 1
+                    *reinterpret_cast<uint32_t*>(sc + mx_tiled_offset(r[u], b0, kb)) = word;
+                } else {
+                    uint8_t* sr = sc + r[u] * (cols / 32) + b0;
+                    for (int j = 0; j < nb; ++j)
+                        sr[j] = static_cast<uint8_t>(sj[j]);
+                }
+            }
+        }
+    }
+}
+
+// Row-major scales [rows, cols / 32] -> the tiled layout (one 4-byte word,
+// four blocks of one row, per thread; padding rows and blocks get 127).
+__global__ void __launch_bounds__(kThreads) mx_scales_tile_kernel(const uint8_t* __restrict__ src, int64_t rows,
+                                                                  int64_t cols, uint8_t* __restrict__ dst)
+{
+    grid_launch_dependents();
+    const int64_t kb = (cols + 127) / 128;
+    const int64_t nbr = cols / 32;
+    const int64_t total = (rows + 127) / 128 * 128 * kb;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < total; i += stride) {
+        const int64_t r = i / kb, k = i - r * kb;
+        uint32_t word = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t b = 4 * k + j;
+            const uint32_t v = (r < rows && b < nbr) ? src[r * nbr + b] : 127u;
+            word |= v << (8 * j);
+        }
+        *reinterpret_cast<uint32_t*>(dst + mx_tiled_offset(r, 4 * k, kb)) = word;
+    }
+}
+
+int grid_for_items(int64_t items)
+{
+    const int64_t blocks = (items + kThreads - 1) / kThreads;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    return static_cast<int>(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+}
+
+template <int FMT>
+int quantize_mx(const float* x, int64_t rows, int64_t cols, int64_t ldx, uint8_t* q, int64_t ldq,
+                uint8_t* scales, int layout, cudaStream_t st)
+{
+    if (rows < 0 || cols < 0 || (layout != 0 && layout != 1))
+        return FP8_ERR_INVALID;
+    if (cols % 32 != 0)
+        return FP8_ERR_SHAPE;
+    if (rows == 0 || cols == 0)
+        return FP8_OK;
+    if (!x || !q || !scales)
+        return FP8_ERR_INVALID;
+    if (ldx < cols || ldq < cols)
+        return FP8_ERR_SHAPE;
+    if ((reinterpret_cast<uintptr_t>(x) & 3u) || (layout == 1 && !aligned16(scales)))
+        return FP8_ERR_ALIGN;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    const int vec = aligned16(x) && (ldx % 4 == 0);
+    const int qvec = (reinterpret_cast<uintptr_t>(q) % 4 == 0) && (ldq % 4 == 0);
+    const int64_t windows = rows * ((cols + 127) / 128);
+    const int grid = grid_for_items(windows * 32);
+    if (layout == 1) {
+        if (rows % 128 != 0)                     // padding rows of the last tile: scale 1
+            GB_CUDA_OK(cudaMemsetAsync(scales, 127, fp8_mx_scale_tiled_bytes(rows, cols), st));
+        quant_mx_kernel<FMT, 1><<<grid, kThreads, 0, st>>>(x, rows, cols, ldx, q, ldq, scales, vec, qvec,
+                                                          device_error_word());
+    } else {
+        quant_mx_kernel<FMT, 0><<<grid, kThreads, 0, st>>>(x, rows, cols, ldx, q, ldq, scales, vec, qvec,
+                                                          device_error_word());
+    }
+    GB_CUDA_OK(cudaGetLastError());
+    return FP8_OK;
+}
+
 }  // namespace
 }  // namespace gb300
+
+extern "C" size_t fp8_mx_scale_tiled_bytes(int64_t rows, int64_t cols)
+{
+    if (rows <= 0 || cols <= 0)
+        return 0;
+    return static_cast<size_t>((rows + 127) / 128) * static_cast<size_t>((cols + 127) / 128) * 512;
+}
+
+extern "C" int fp8_quantize_mx(const float* x, int64_t rows, int64_t cols, int64_t ldx, int format,
+                               uint8_t* q, int64_t ldq, uint8_t* scales, int scale_layout,
+                               fp8_stream_t stream)
+{
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (format == FP8_E4M3)
+        return gb300::quantize_mx<0>(x, rows, cols, ldx, q, ldq, scales, scale_layout, st);
+    if (format == FP8_E5M2)
+        return gb300::quantize_mx<1>(x, rows, cols, ldx, q, ldq, scales, scale_layout, st);
+    return FP8_ERR_INVALID;
+}
+
+extern "C" int fp8_mx_scales_to_tiled(const uint8_t* scales, int64_t rows, int64_t cols, uint8_t* tiled,
+                                      fp8_stream_t stream)
+{
+    using namespace gb300;
+    if (rows < 0 || cols < 0)
+        return FP8_ERR_INVALID;
+    if (cols % 32 != 0)
+        return FP8_ERR_SHAPE;
+    if (rows == 0 || cols == 0)
+        return FP8_OK;
+    if (!scales || !tiled)
+        return FP8_ERR_INVALID;
+    if (!aligned16(tiled))
+        return FP8_ERR_ALIGN;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    const int64_t words = (rows + 127) / 128 * 128 * ((cols + 127) / 128);
+    mx_scales_tile_kernel<<<grid_for_items(words), kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        scales, rows, cols, tiled);
+    GB_CUDA_OK(cudaGetLastError());
+    return FP8_OK;
+}
 
 extern "C" int fp8_quantize_e4m3(const float* x, int64_t rows, int64_t cols, int64_t ldx,
                                  int scale_mode, uint8_t* q, int64_t ldq, float* dequant_scale,

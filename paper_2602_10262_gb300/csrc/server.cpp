@@ -449,22 +449,46 @@ struct fp8_server {
         return std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
     }
 
-    // Scheduler thread: retire finished batches, launch new ones.  It spins
-    // (yielding) while work is around and backs off to short sleeps after
-    // ~2 ms without any.
+    // A batch formed under the lock and enqueued on the GPU without it.
+    struct Formed {
+        int tenant;
+        int max_ctas;
+        std::vector<Req*> reqs;
+        void* handle = nullptr;
+        int launches = 0;
+        int rc = FP8_OK;
+        double t_launch = 0;
+    };
+
+    // Scheduler thread: retire finished batches, form new ones under the
+    // lock, enqueue them with the lock released (so submit, poll and wait
+    // never wait on a launch), then record them.  It spins (yielding) while
+    // work is around and backs off to short sleeps after ~2 ms without any.
     void run()
     {
         exec->thread_init();
         double last_progress = now_us();
+        std::vector<Formed> todo;
         for (;;) {
             bool progress = false;
+            todo.clear();
             {
                 std::unique_lock<std::mutex> lk(mu);
                 progress |= retire_locked();
                 if (stopping && idle_locked())
                     break;
                 if (!stopping)
-                    progress |= launch_locked();
+                    form_locked(&todo);
+            }
+            for (Formed& b : todo) {
+                b.t_launch = now_us();
+                b.rc = exec->launch(b.tenant, b.reqs, cfg.batching != 0, b.max_ctas, b.t_launch, &b.handle,
+                                    &b.launches);
+            }
+            if (!todo.empty()) {
+                std::unique_lock<std::mutex> lk(mu);
+                record_locked(&todo);
+                progress = true;
             }
             const double now = now_us();
             if (progress)
@@ -515,56 +539,65 @@ struct fp8_server {
         return any;
     }
 
-    bool launch_locked()
+    // Take queued requests into batches (FIFO per tenant, admitted while
+    // their workspace fits the pool).  The latency tenant first, with no
+    // in-flight limit and batches of at most latency_max_batch; the bulk
+    // tenants in index order, each while it has an in-flight slot.
+    void form_locked(std::vector<Formed>* out)
     {
-        bool any = false;
-        const int max_batch = cfg.batching ? cfg.max_batch : 1;
-        // latency tenant first, then the others in index order
+        int formed[FP8_SERVER_MAX_TENANTS] = {};
         for (int k = -1; k < cfg.num_tenants; ++k) {
             const int t = (k < 0) ? cfg.latency_tenant : k;
             if (t < 0 || (k >= 0 && t == cfg.latency_tenant))
                 continue;
+            const bool latency = t == cfg.latency_tenant;
+            const int cap = !cfg.batching ? 1 : (latency ? cfg.latency_max_batch : cfg.max_batch);
             while (!queue[t].empty() &&
-                   (!cfg.batching || static_cast<int>(inflight[t].size()) < cfg.max_inflight)) {
-                std::vector<Req*> batch;
-                while (!queue[t].empty() && static_cast<int>(batch.size()) < max_batch) {
+                   (!cfg.batching || latency ||
+                    static_cast<int>(inflight[t].size()) + formed[t] < cfg.max_inflight)) {
+                Formed b;
+                b.tenant = t;
+                b.max_ctas = latency ? 0 : cfg.bulk_max_ctas;
+                while (!queue[t].empty() && static_cast<int>(b.reqs.size()) < cap) {
                     Req* q = queue[t].front();
                     if (!pool.alloc(q->ws_bytes, &q->ws_off))
                         break;                      // FIFO: wait for space
-                    batch.push_back(q);
+                    b.reqs.push_back(q);
                     queue[t].pop_front();
                 }
-                if (batch.empty())
+                if (b.reqs.empty())
                     break;
-                const int max_ctas = (t == cfg.latency_tenant) ? 0 : cfg.bulk_max_ctas;
-                void* handle = nullptr;
-                int launches = 0;
-                const double now = now_us();
-                const int rc = exec->launch(t, batch, cfg.batching != 0, max_ctas, now, &handle,
-                                            &launches);
-                stats.kernel_launches += launches;
-                if (rc != FP8_OK) {
-                    for (Req* q : batch) {
-                        q->status = rc;
-                        q->t_launch = q->t_start = q->t_end = now;
-                        pool.release(q->ws_off, q->ws_bytes);
-                        ++stats.failed;
-                    }
-                    done_cv.notify_all();
-                    any = true;
-                    continue;
-                }
-                for (Req* q : batch) {
-                    q->t_launch = now;
-                    q->batch_size = static_cast<int>(batch.size());
-                }
-                ++stats.batches;
-                stats.max_batch_seen = std::max<uint64_t>(stats.max_batch_seen, batch.size());
-                inflight[t].push_back(Batch{handle, std::move(batch)});
-                any = true;
+                ++formed[t];
+                out->push_back(std::move(b));
             }
         }
-        return any;
+    }
+
+    void record_locked(std::vector<Formed>* todo)
+    {
+        bool failed = false;
+        for (Formed& b : *todo) {
+            stats.kernel_launches += b.launches;
+            if (b.rc != FP8_OK) {
+                for (Req* q : b.reqs) {
+                    q->status = b.rc;
+                    q->t_launch = q->t_start = q->t_end = b.t_launch;
+                    pool.release(q->ws_off, q->ws_bytes);
+                    ++stats.failed;
+                }
+                failed = true;
+                continue;
+            }
+            for (Req* q : b.reqs) {
+                q->t_launch = b.t_launch;
+                q->batch_size = static_cast<int>(b.reqs.size());
+            }
+            ++stats.batches;
+            stats.max_batch_seen = std::max<uint64_t>(stats.max_batch_seen, b.reqs.size());
+            inflight[b.tenant].push_back(Batch{b.handle, std::move(b.reqs)});
+        }
+        if (failed)
+            done_cv.notify_all();
     }
 };
 
@@ -585,6 +618,10 @@ int normalise(const fp8_server_config* in, fp8_server_config* out)
         c.max_batch = FP8_QUANT_GROUPED_MAX;
     if (c.max_inflight <= 0)
         c.max_inflight = 4;
+    if (c.latency_max_batch <= 0)
+        c.latency_max_batch = 1;
+    if (c.latency_max_batch > c.max_batch)
+        c.latency_max_batch = c.max_batch;
     if (c.bulk_max_ctas < 0)
         c.bulk_max_ctas = 0;
     *out = c;

@@ -89,6 +89,26 @@ def test_stall_switch_validates_and_resets(lib):
     assert lib.fp8_test_stall_gemm_loads(0, 0.0) == 0
 
 
+def test_mx_host_checks(lib):
+    P = ctypes.c_void_p
+    # tiled scale bytes: 512 per 128 rows x 128 columns, partial tiles rounded up
+    assert lib.fp8_mx_scale_tiled_bytes(128, 128) == 512
+    assert lib.fp8_mx_scale_tiled_bytes(129, 160) == 2 * 2 * 512
+    assert lib.fp8_mx_scale_tiled_bytes(0, 128) == 0
+    # the row length must hold whole 32-element blocks; formats and layouts checked
+    assert lib.fp8_quantize_mx(P(16), 4, 48, 48, 0, P(16), 48, P(16), 0, None) == -2
+    assert lib.fp8_quantize_mx(P(16), 4, 64, 64, 2, P(16), 64, P(16), 0, None) == -1
+    assert lib.fp8_quantize_mx(P(16), 4, 64, 64, 0, P(16), 64, P(16), 2, None) == -1
+    assert lib.fp8_quantize_mx(P(16), 4, 64, 64, 0, P(16), 64, P(8), 1, None) == -3
+    assert lib.fp8_mx_scales_to_tiled(P(16), 4, 40, P(16), None) == -2
+    ok = (P(16), 64, P(16), P(16), 64, P(16), 1.0, P(16), 4, 0)
+    assert lib.gemm_fp8_mx(4, 4, 48, *ok, 0, 0, None) == -2        # K % 32
+    assert lib.gemm_fp8_mx(4, 4, 64, *ok, 0, 3, None) == -1        # format
+    assert lib.gemm_fp8_mx(4, 4, 64, P(16), 64, P(8), P(16), 64, P(16), 1.0, P(16), 4, 0, 0, 0,
+                           None) == -3                              # scales 16-byte aligned
+    assert lib.gemm_fp8_mx(0, 4, 64, *ok, 0, 0, None) == 0
+
+
 def test_grouped_rejects_bad_format(lib):
     from paper_2602_10262_gb300 import _lib
     pr = _lib.FP8Problem(4, 4, 32, 16, 0, 32, 16, 32, 16, 0, 16, 0, 1.0, 16, 4, 0, 0, 0, 0)

@@ -64,6 +64,35 @@ def test_max_batch_respected():
         assert s.stats()["completed"] == 13
 
 
+def test_latency_tenant_is_not_held_to_the_inflight_limit():
+    # one in-flight slot, 20 ms per batch: the bulk tenant's requests wait for
+    # the slot, the latency tenant's are all enqueued at once, one per batch
+    with _server(num_tenants=2, latency_tenant=0, max_inflight=1, simulate=(20000.0, 0.0, 0)) as s:
+        w = _weight(s)
+        lat = [s.submit(0, w, 8, FAKE, 4096, FAKE, 4096) for _ in range(6)]
+        bulk = [s.submit(1, w, 8, FAKE, 4096, FAKE, 4096) for _ in range(3)]
+        rl = [s.wait(t, 5) for t in lat]
+        rb = [s.wait(t, 5) for t in bulk]
+        assert all(r.status == OK and r.batch_size == 1 for r in rl)
+        assert max(r.t_launch_us for r in rl) - min(r.t_submit_us for r in rl) < 15000.0
+        # the bulk tenant's requests went out as one batch, or the later ones
+        # waited for its single slot
+        assert len({r.t_launch_us for r in rb}) == 1 or \
+            max(r.t_launch_us for r in rb) >= min(r.t_end_us for r in rb) - 1.0
+
+
+def test_latency_batches_capped():
+    with _server(num_tenants=2, latency_tenant=0, latency_max_batch=4, simulate=(20000.0, 0.0, 0)) as s:
+        w = _weight(s)
+        first = s.submit(0, w, 8, FAKE, 4096, FAKE, 4096)
+        time.sleep(0.005)
+        ts = [s.submit(0, w, 8, FAKE, 4096, FAKE, 4096) for _ in range(11)]
+        rs = [s.wait(t, 5) for t in [first] + ts]
+        assert all(r.status == OK for r in rs)
+        assert max(r.batch_size for r in rs) <= 4
+        assert s.stats()["completed"] == 12
+
+
 def test_per_call_mode_launches_every_request_alone():
     with _server(num_tenants=2, latency_tenant=0, batching=False) as s:
         w = _weight(s)
