@@ -353,7 +353,7 @@ class ServingBench:
     result has been collected."""
 
     SIZES = (4096, 8192, 14336)
-    RESERVE = 24                   # SMs the batched mode keeps free for the latency tenant
+    RESERVE = 16                   # SMs the batched mode keeps free for the latency tenant
     SLOTS = 128                    # output slots (requests in flight at most)
 
     def __init__(self, dev, gb):
@@ -815,6 +815,136 @@ def concurrency_sweep(gb, dev, iters=100, trials=5):
     return out
 
 
+def served_concurrency_sweep(gb, dev, iters=100, trials=3):
+    """The paper's concurrency experiments (sections 5.1, 5.3, 6.2, 7.2)
+    replayed as tenants of the request server (fp8_server_*): each tenant
+    submits its `iters` requests at once (fp32 activations quantised per row
+    by the server, resident E4M3 weights, BF16 out) and the server runs them
+    one launch per request on the tenant's stream, as the paper's streams
+    issue one GEMM after another; medians over `trials`.
+      - tenants: 1, 2, 4, 8 tenants of 512^3 requests, dense, 2:4 and
+        alternating dense / 2:4 (sections 5.1, 6.2); the dense sweep also
+        with continuous batching;
+      - fragmentation (section 5.3): a 512^3 tenant beside a 512^3, 1024^3
+        or 2048^3 tenant, sharing every SM, or with the 512^3 tenant as the
+        server's latency tenant (high-priority stream) and the larger one's
+        GEMMs capped at SMs - 24 CTAs (bulk_max_ctas);
+      - two transformer-layer instances (section 7.2): two tenants each
+        submitting the four layer GEMMs 10 times.
+    A tenant's time runs from its first submission to its last completion;
+    its isolated time is the same requests alone on the same server
+    configuration; overlap efficiency is over the tenants' spans."""
+    from paper_2602_10262_gb300.server import Server
+    sms = gb.fp8_device_sm_count()
+    g = torch.Generator(device=dev).manual_seed(4000)
+    weights = {}
+
+    def weight(N, K, sparse):
+        key = (N, K, sparse)
+        if key not in weights:
+            w = torch.randn((N, K), generator=g, device=dev)
+            Wd, dW = gb.fp8_quantize_e4m3(w, 1)
+            if sparse:
+                vals, meta = gb.prune24_compress(Wd)
+                weights[key] = (vals, dW, meta)
+            else:
+                weights[key] = (Wd, dW, None)
+            del w
+        return weights[key]
+
+    X = torch.randn((16384, 14336), generator=g, device=dev)
+    ld = X.stride(0)
+
+    def serve(tenants, cfg, reuse_outputs=False):
+        """tenants: per tenant a list of (M, N, K, sparse); all requests are
+        submitted at once, interleaved over the tenants.  Returns per-tenant
+        (start, end) spans and the makespan, in ms."""
+        srv = Server(num_tenants=len(tenants), pool_bytes=16 << 30, **cfg)
+        outs, tickets = [], [[] for _ in tenants]
+        try:
+            handles = {}
+            for reqs in tenants:
+                for (M, N, K, sp) in reqs:
+                    if (N, K, sp) not in handles:
+                        W, dW, meta = weight(N, K, sp)
+                        handles[(N, K, sp)] = srv.register_weight(N, K, W, dW, 1, W_meta=meta)
+            bufs = {}
+            for t, reqs in enumerate(tenants):
+                for i, (M, N, K, sp) in enumerate(reqs):
+                    key = (t, M, N) if reuse_outputs else (t, i)
+                    if key not in bufs:
+                        bufs[key] = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+            torch.cuda.synchronize()
+            n = max(len(r) for r in tenants)
+            for i in range(n):
+                for t, reqs in enumerate(tenants):
+                    if i < len(reqs):
+                        M, N, K, sp = reqs[i]
+                        out = bufs[(t, M, N) if reuse_outputs else (t, i)]
+                        tickets[t].append(srv.submit(t, handles[(N, K, sp)], M, X.data_ptr(), ld,
+                                                     out.data_ptr(), N))
+            res = [[srv.wait(tk, 120) for tk in tks] for tks in tickets]
+        finally:
+            srv.close()
+        if any(r is None or r.status != 0 for rs in res for r in rs):
+            raise RuntimeError("served concurrency request failed")
+        spans = [(min(r.t_submit_us for r in rs) * 1e-3, max(r.t_end_us for r in rs) * 1e-3) for rs in res]
+        make = max(b for _, b in spans) - min(a for a, _ in spans)
+        return spans, make
+
+    def measure(tenants, cfg, iso_cfgs=None, reuse_outputs=False):
+        serve(tenants, cfg, reuse_outputs)                           # warm-up
+        iso = []
+        for t, reqs in enumerate(tenants):
+            c = (iso_cfgs or [cfg] * len(tenants))[t]
+            one = [float(np.median([(lambda s: s[1])(serve([reqs], c, reuse_outputs))
+                                    for _ in range(trials)]))]
+            iso += one
+        runs = [_concurrency_stats(*serve(tenants, cfg, reuse_outputs), iso) for _ in range(trials)]
+        med = {}
+        for k, v in runs[0].items():
+            if isinstance(v, float):
+                med[k] = float(np.median([r[k] for r in runs]))
+            elif isinstance(v, list):
+                med[k] = [float(np.median([r[k][i] for r in runs])) for i in range(len(v))]
+            else:
+                med[k] = v
+        med["isolated_ms"] = iso
+        return med
+
+    out = {"iters_per_tenant": iters, "trials": trials, "tenants": [], "fragmentation": []}
+    n = 512
+    kinds = {"fp8_dense": lambda i: False, "fp8_sparse": lambda i: True, "fp8_mixed": lambda i: i % 2 == 1}
+    for kind, sp_of in kinds.items():
+        for nt in (1, 2, 4, 8):
+            if kind == "fp8_mixed" and nt > 4:
+                continue
+            tenants = [[(n, n, n, sp_of(t))] * iters for t in range(nt)]
+            for batching in ((False, True) if kind == "fp8_dense" else (False,)):
+                med = measure(tenants, dict(latency_tenant=-1, batching=batching))
+                med.update({"kind": kind, "n": n, "batching": batching,
+                            "gflops_aggregate": 2.0 * n ** 3 * iters * nt / med["makespan_ms"] / 1e6})
+                out["tenants"].append(med)
+    reserve = min(24, sms // 2)
+    for big in (512, 1024, 2048):
+        tenants = [[(big, big, big, False)] * iters, [(n, n, n, False)] * iters]
+        for mode, cfg in (("shared", dict(latency_tenant=-1)),
+                          ("reserved", dict(latency_tenant=1, bulk_max_ctas=sms - reserve))):
+            med = measure(tenants, cfg, iso_cfgs=[dict(latency_tenant=-1)] * 2)
+            med.update({"pair": [big, n], "ratio": f"{big // n}:1", "mode": mode})
+            out["fragmentation"].append(med)
+    layer = [(M, N, K, False) for _, M, N, K in workloads.TRANSFORMER_LAYER]
+    flops = sum(2.0 * M * N * K for M, N, K, _ in layer)
+    tf_iters = 10
+    med = measure([layer * tf_iters, layer * tf_iters], dict(latency_tenant=-1), reuse_outputs=True)
+    med.update({"gflop_per_layer": flops / 1e9, "layers_per_instance": tf_iters,
+                "aggregate_tflops": 2 * flops * tf_iters / med["makespan_ms"] / 1e9})
+    out["transformer_two_instances"] = med
+    del X, weights
+    torch.cuda.empty_cache()
+    return out
+
+
 def aspect_sweep(gb, dev):
     """Throughput against the aspect ratio M/N at fixed work (M * N = 8192^2
     outputs, K = 4096): the analogue of the paper's shape sweep at fixed
@@ -929,7 +1059,9 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
     out = {"offered_req_per_s": rate, "requests": n, "rows": []}
     cfgs = [("per_call", dict(batching=False))] + \
         [(f"batched_reserve_{r}", dict(batching=True, bulk_max_ctas=(sms - r) if r else 0))
-         for r in (0, 8, 16, 24, 32)]
+         for r in (0, 8, 16, 24, 32)] + \
+        [(f"batched_reserve_{r}_latency_capped", dict(batching=True, bulk_max_ctas=sms - r, latency_max_ctas=r))
+         for r in (8, 16, 24, 32, 48)]
     for name, cfg in cfgs:
         lat, span, _, _ = sb.run(reqs, cfg, rate)
         _, cspan, _, _ = sb.run(reqs[:8000], cfg)
@@ -942,7 +1074,7 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
 
 
 SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency", "mx",
-                  "serving_policy")
+                  "serving_policy", "served_concurrency")
 
 
 def sweep(gb, dev, sections=SWEEP_SECTIONS):
@@ -966,6 +1098,8 @@ def sweep(gb, dev, sections=SWEEP_SECTIONS):
         out["mx"] = mx_sweep(gb, dev)
     if "serving_policy" in sections:
         out["serving_policy"] = serving_policy_sweep(gb, dev)
+    if "served_concurrency" in sections:
+        out["served_concurrency"] = served_concurrency_sweep(gb, dev)
     return out
 
 
@@ -1092,7 +1226,7 @@ def main():
     ap.add_argument("--sections", default=",".join(SWEEP_SECTIONS),
                     help="comma list of sweep tables: " + ", ".join(SWEEP_SECTIONS))
     ap.add_argument("--gemm", default=None,
-                    help="M,N,K[,sparse][,e4m3|e5m2,e4m3|e5m2]: run only this GEMM (warmup + "
+                    help="M,N,K[,sparse|mx][,e4m3|e5m2,e4m3|e5m2]: run only this GEMM (warmup + "
                          "steps launches; for profilers); the two formats are A's and B's")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -1109,11 +1243,16 @@ def main():
         f = args.gemm.split(",")
         M, N, K = (int(v) for v in f[:3])
         sparse = "sparse" in f[3:]
-        fmts = [{"e4m3": 0, "e5m2": 1}[t] for t in f[3:] if t != "sparse"] or [0, 0]
+        mx = "mx" in f[3:]
+        fmts = [{"e4m3": 0, "e5m2": 1}[t] for t in f[3:] if t not in ("sparse", "mx")] or [0, 0]
         af, bf = fmts[0], fmts[-1]
         x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 1, af, bf)
         C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
-        if sparse:
+        if mx:
+            A, SA = gb.fp8_quantize_mx(x, af, scale_layout=1)
+            B, SB = gb.fp8_quantize_mx(w, bf, scale_layout=1)
+            fn = lambda: gb.gemm_fp8_mx(A, SA, B, SB, 1.0, gb.OUT_BF16, af, bf, C=C)
+        elif sparse:
             vals, meta = gb.prune24_compress(A)
             fn = lambda: gb.gemm_fp8_sparse24_fmt(vals, meta, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16,
                                                   False, af, bf, C=C)

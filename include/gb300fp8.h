@@ -471,6 +471,9 @@ typedef struct {
     int latency_max_batch;    /* with batching: requests per batch of the latency
                                  tenant (0: 1, i.e. each of its requests is
                                  launched on its own as soon as it is admitted) */
+    int latency_max_ctas;     /* CTA cap for the latency tenant's GEMMs (0: all
+                                 SMs); set to the SMs bulk_max_ctas leaves free,
+                                 its work never waits for SMs held by bulk GEMMs */
 } fp8_server_config;
 
 typedef struct fp8_server fp8_server;

@@ -557,7 +557,7 @@ struct fp8_server {
                     static_cast<int>(inflight[t].size()) + formed[t] < cfg.max_inflight)) {
                 Formed b;
                 b.tenant = t;
-                b.max_ctas = latency ? 0 : cfg.bulk_max_ctas;
+                b.max_ctas = latency ? cfg.latency_max_ctas : cfg.bulk_max_ctas;
                 while (!queue[t].empty() && static_cast<int>(b.reqs.size()) < cap) {
                     Req* q = queue[t].front();
                     if (!pool.alloc(q->ws_bytes, &q->ws_off))
@@ -624,6 +624,8 @@ int normalise(const fp8_server_config* in, fp8_server_config* out)
         c.latency_max_batch = c.max_batch;
     if (c.bulk_max_ctas < 0)
         c.bulk_max_ctas = 0;
+    if (c.latency_max_ctas < 0)
+        c.latency_max_ctas = 0;
     *out = c;
     return FP8_OK;
 }
