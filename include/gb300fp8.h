@@ -375,14 +375,33 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
                         fp8_stream_t stream);
 
 /* Process-wide tile configuration of the GEMM kernels, for tuning and tests.
- * mt: 128-row MMA halves per CTA tile: 1 (128 x N tiles, double-buffered
- * accumulators), 2 (256 x N tiles: two MMAs share each B tile, a third fewer
- * operand bytes per FLOP), 0 = chosen per launch (2 when every problem fills
+ * mt: 1 (128 x N tiles of one CTA, double-buffered accumulators), 2 (256 x N
+ * tiles of one CTA: two MMAs share each B tile, a third fewer operand bytes
+ * per FLOP), 3 (256 x 256 tiles of a CTA pair, tcgen05 cta_group::2: each
+ * CTA of a two-CTA cluster loads 128 rows of A and 128 rows of B and holds
+ * its half of the accumulator; dense launches whose N tiles are 256 wide,
+ * otherwise as 0), 0 = chosen per launch (2 when every problem fills
  * 256-row tiles with N tiles >= 128 wide and those tiles number at least
  * half the SMs; a launch mixing dense and sparse problems always uses 1).
  * group_m: M-blocks per raster band (0 = 16).  Results do not depend on
  * either.  Affects launches enqueued after the call, from any thread. */
 int fp8_gemm_set_tile_config(int mt, int group_m);
+
+/* How gemm_fp8_dense would run a problem now (tile shape, split, grid),
+ * without launching anything; for tuning, tests and callers of
+ * gemm_fp8_dense_noalloc that size their problems against its scratch. */
+typedef struct {
+    int mt;                 /* tile kind as in fp8_gemm_set_tile_config (1, 2 or 3) */
+    int bn;                 /* N width of a tile */
+    int k_blocks_per_stage; /* 128-wide K chunks per pipeline stage */
+    int splits;             /* K slices per tile (1: no split) */
+    int cluster;            /* CTAs per thread-block cluster (0: no clusters) */
+    int grid;               /* CTAs launched */
+    int swapped;            /* 1: run as C^T = B A^T (small M on the MMA N side) */
+    size_t workspace_bytes; /* split-K scratch the launch needs (0: none) */
+} fp8_gemm_plan_info;
+
+int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info *info);
 
 /* Autotuner: times every candidate tile configuration (mt in {1, 2}, raster
  * band group_m in {2, 4, 8, 16, 32}) of this exact problem list on `stream`

@@ -23,7 +23,7 @@ __all__ = [
     "fp8_device_sm_count", "fp8_test_stall_gemm_loads", "fp8_gemm_set_tile_config", "gemm_fp8_grouped_autotune",
     "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
     "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2", "fp8_quantize_mx", "fp8_mx_scales_to_tiled",
-    "fp8_mx_scale_tiled_bytes", "gemm_fp8_mx",
+    "fp8_mx_scale_tiled_bytes", "gemm_fp8_mx", "gemm_fp8_dense_plan",
 ]
 
 OUT_F32 = 0
@@ -110,6 +110,16 @@ def fp8_test_stall_gemm_loads(launches: int, wait_limit_ms: float = 0.0) -> None
     applies to every eager GEMM launch until reset with 0)."""
     _check(library().fp8_test_stall_gemm_loads(int(launches), float(wait_limit_ms)),
            "fp8_test_stall_gemm_loads")
+
+
+def gemm_fp8_dense_plan(M: int, N: int, K: int, out_dtype: int = OUT_BF16) -> dict:
+    """How gemm_fp8_dense would run [M, K] x [N, K]^T now (tile kind, N width,
+    k-blocks per stage, K slices, cluster size, grid, operand swap, split-K
+    scratch bytes), without launching."""
+    info = _lib.FP8PlanInfo()
+    _check(library().gemm_fp8_dense_plan(int(M), int(N), int(K), int(out_dtype), ctypes.byref(info)),
+           "gemm_fp8_dense_plan")
+    return {name: getattr(info, name) for name, _ in info._fields_}
 
 
 def fp8_gemm_set_tile_config(mt: int = 0, group_m: int = 0) -> None:

@@ -87,10 +87,18 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 // as above, and per k-block two 512-byte chunks of E8M0 scales after the B
 // chunks (A's 128 rows, then B's), copied into a ring of TMEM columns
 // 128..255 (8 per k-block: A's 4 then B's 4) beside the first accumulator.
-template <int MT, bool SP = false, int BNC = BN_MAX, int KC = 1, bool MX = false>
+// PAIR: CTA-pair launches (cta_group::2, clusters of two): a 256 x 256 tile
+// per pair, each CTA loading its 128 rows of A and 128 rows of B (two
+// k-blocks per stage, three 64 KB stages) and holding its 128 x 256 half of
+// the accumulator; the even CTA issues the MMAs.  Per SM that is MT = 2's
+// bytes per FLOP with half of MT = 2's tensor memory per accumulator.
+constexpr int PAIR_TMEM_COLS = 256;       // columns per CTA (one accumulator)
+
+template <int MT, bool SP = false, int BNC = BN_MAX, int KC = 1, bool MX = false, bool PAIR = false>
 struct Cfg {
     static constexpr bool kSparse2 = MT == 2 && SP;
     static constexpr int kStages =
+        PAIR ? 3 :
         KC == 2 ? (SP ? (BNC == 128 ? 4 : (BNC == 64 ? 5 : (BNC == 32 ? 7 : 8)))
                       : (BNC == 128 ? 3 : (BNC == 64 ? 4 : 5)))
                 : MT == 2 ? (SP ? 4 : 3)
@@ -100,7 +108,7 @@ struct Cfg {
     // A bytes of one k-block: dense codes, or (SP launches) kept codes +
     // metadata; 128-row dense-capable tiles also hold a sparse k-block there
     static constexpr int kAChunk = SP ? kSpChunk + kMetaChunk : MT * BM * BK;
-    static constexpr int kBChunk = kSparse2 ? SPARSE_BN_MAX_MT2 * BK : BNC * BK;
+    static constexpr int kBChunk = PAIR ? (BNC / 2) * BK : kSparse2 ? SPARSE_BN_MAX_MT2 * BK : BNC * BK;
     static constexpr int kABytes = KC * kAChunk;
     static constexpr int kBBytes = KC * kBChunk;
     static constexpr int kSfChunk = 512;                        // scales of 128 rows x one k-block
@@ -108,19 +116,21 @@ struct Cfg {
     static constexpr int kSfCol0 = BNC;                         // MX: scale ring in TMEM columns
     static constexpr int kStageBytes = kABytes + kBBytes + kSfBytes;
     static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : (BNC == 256 ? SPARSE_BN_MAX : BNC);
-    static constexpr int kAcc = MT == 2 ? 1 : 2;                  // accumulator buffers
+    static constexpr int kTmemCols = PAIR ? PAIR_TMEM_COLS : TMEM_COLS;
+    static constexpr int kAcc = PAIR ? PAIR_TMEM_COLS / BN_MAX : (MT == 2 ? 1 : 2);   // accumulator buffers
     static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
     static constexpr int kEpiWarps = 4 * MT;
     static constexpr int kEpiBytes = kEpiWarps * 32 * 128;       // 32 rows x 128 B per warp
     static constexpr int kSmem = 1024 + kStages * kStageBytes + 256 + kEpiBytes;
-    static_assert(kMetaCol0 + 4 * kStages * KC <= BN_MAX, "metadata ring must fit beside the accumulator");
+    static_assert(PAIR || kMetaCol0 + 4 * kStages * KC <= BN_MAX, "metadata ring must fit beside the accumulator");
     static_assert(KC * (kSpChunk + kMetaChunk) <= kABytes || (MT == 2 && !SP),
                   "sparse A + metadata fit the A region");
     static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "swizzle atoms stay aligned");
     static_assert(kSmem <= 232448, "shared memory per CTA");
     static_assert((2 * kStages + 2 * kAcc + 3) * 8 + 12 <= 256, "barriers and flags fit their 256-byte region");
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
-    static_assert(KC == 1 || (KC == 2 && MT == 1 && BNC <= 128), "two-chunk stages: 128-row tiles");
+    static_assert(KC == 1 || (KC == 2 && MT == 1 && (BNC <= 128 || PAIR)), "two-chunk stages: 128-row tiles");
+    static_assert(!PAIR || (MT == 1 && !SP && !MX && BNC == BN_MAX && KC == 2), "CTA pairs: dense 256 x 256 tiles");
     static_assert(kBChunk % 1024 == 0, "B chunks stay swizzle-atom aligned");
     static_assert(!MX || (MT == 1 && !SP && BNC == 128), "block-scaled launches: 128 x 128 dense tiles");
     static_assert(!MX || kSfCol0 + 8 * kStages * KC <= BN_MAX, "scale ring fits beside the first accumulator");
@@ -529,11 +539,11 @@ __device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P,
 
 // ---------------------------------------------------------------- kernel
 
-template <int MAXP, int MT, bool SP, int BNC, int KC, bool MX = false>
-__global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
+template <int MAXP, int MT, bool SP, int BNC, int KC, bool MX = false, bool PAIR = false>
+__global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     gemm_fp8_kernel(const __grid_constant__ Params<MAXP> prm)
 {
-    using C = Cfg<MT, SP, BNC, KC, MX>;
+    using C = Cfg<MT, SP, BNC, KC, MX, PAIR>;
     constexpr int S = C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -571,7 +581,12 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
     const unsigned long long wlim = prm.wait_ns;
     float* const ws = prm.ws;
     unsigned* const ctr = prm.ctr;
-    const TileCoord tc_first = tile_coord(prm, blockIdx.x);
+    // CTA pairs walk the tiles pair by pair (both CTAs of a pair take the
+    // same tiles); other launches CTA by CTA
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const int tile0 = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+    const int tile_step = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
+    const TileCoord tc_first = tile_coord(prm, tile0);
     const ProblemScalars P_first = prm.prob[tc_first.p];
     if (threadIdx.x == 0) {
         tma_prefetch_desc(&prm.prob[tc_first.p].tmP);
@@ -585,7 +600,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
         }
         for (int b = 0; b < C::kAcc; ++b) {
             mbar_init(tfull_bar(b), 1);
-            mbar_init(tempty_bar(b), 128 * MT);
+            // pairs: the even CTA's barrier counts both CTAs' epilogue threads
+            mbar_init(tempty_bar(b), PAIR ? 2 * 128 : 128 * MT);
         }
         mbar_init(drain_bar, 1);
         // cluster split-K: "written" counts the other slices' epilogue
@@ -597,13 +613,31 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
     }
     __syncwarp();
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
-        tmem_relinquish();
+        if constexpr (PAIR) {
+            tmem_alloc_pair(smem_u32(tmem_slot), C::kTmemCols);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(smem_u32(tmem_slot), C::kTmemCols);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    int my_tiles = total_tiles;                 // tiles this CTA walks (0: it takes none)
+    if constexpr (PAIR) {
+        // both CTAs' barriers and tensor memory exist before either touches
+        // the other's; a collective allocation gives both the same columns
+        // (checked: a pair that disagrees does no work and reports an error)
+        cluster_sync();
+        const uint32_t peer_base = ld_shared_cluster_u32(cluster_map(smem_u32(tmem_slot), rank ^ 1u));
+        if (peer_base != tmem_base) {
+            my_tiles = 0;
+            if (threadIdx.x == 0)
+                report_device_error(err, FP8_ERR_UNSUPPORTED);
+        }
+    }
     // Everything above reads only the kernel parameters and shared memory;
     // from here on the previous kernel's outputs (operands, scales, the
     // split-K workspace) are read and written.
@@ -617,10 +651,13 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
             uint32_t phase = 0;
             uint32_t armed = 0;                 // bit s: slot s armed at least once
             bool ok = true;
-            const int producer_tiles = prm.withhold_loads ? 0 : total_tiles;
-            for (int tile = blockIdx.x; ok && tile < producer_tiles; tile += gridDim.x) {
-                const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
-                const bool first = tile == static_cast<int>(blockIdx.x);
+            const int producer_tiles = prm.withhold_loads ? 0 : my_tiles;
+            // pairs: the even CTA arms its "full" barrier for both CTAs' bytes
+            // and both CTAs' loads complete on it
+            const uint32_t full_rank = PAIR ? 0u : rank;
+            for (int tile = tile0; ok && tile < producer_tiles; tile += tile_step) {
+                const TileCoord tc = tile == tile0 ? tc_first : tile_coord(prm, tile);
+                const bool first = tile == tile0;
                 const ProblemScalars P = first ? P_first : prm.prob[tc.p];
                 if (!first || P.sparse) {
                     tma_prefetch_desc(&prm.prob[tc.p].tmP);
@@ -647,12 +684,41 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
                         abort_pipeline(abort_flag, err);
                         break;
                     }
+                    const uint32_t sa = smem_base + stage * C::kStageBytes;
+                    if constexpr (PAIR) {
+                        // this CTA's 128 rows of A and 128 rows of B; both CTAs'
+                        // copies complete on the even CTA's barrier
+                        const uint32_t fb = rank == 0 ? full_bar(stage) : cluster_map(full_bar(stage), 0u);
+                        const int prow0 = tc.m_blk * 2 * BM + BM * static_cast<int>(rank);
+                        const int pcol0 = tc.n_blk * P.bn + (BN_MAX / 2) * static_cast<int>(rank);
+                        if (rank == 0)
+                            mbar_arrive_expect_tx(fb, 2u * static_cast<uint32_t>(C::kAChunk + C::kBChunk) *
+                                                          static_cast<uint32_t>(P.tma3d ? KC : nck));
+                        if (P.tma3d) {
+                            tma_load_3d_pair(sa, map_p, fb, 0, prow0, kb);
+                            tma_load_3d_pair(sa + C::kABytes, map_q, fb, 0, pcol0, kb);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < KC; ++c) {
+                                if (c < nck) {
+                                    tma_load_2d_pair(sa + c * C::kAChunk, map_p, fb, (kb + c) * BK, prow0);
+                                    tma_load_2d_pair(sa + C::kABytes + c * C::kBChunk, map_q, fb, (kb + c) * BK,
+                                                     pcol0);
+                                }
+                            }
+                        }
+                        armed |= 1u << stage;
+                        if (++stage == S) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                        continue;
+                    }
                     // a 3-D box always lands all KC chunks (those past K as zeros);
                     // block scales come for the nck k-blocks of the stage only
                     mbar_arrive_expect_tx(full_bar(stage),
                                           chunk_bytes * static_cast<uint32_t>(KC > 1 && P.tma3d ? KC : nck) +
                                               (MX ? 2u * C::kSfChunk * static_cast<uint32_t>(nck) : 0u));
-                    const uint32_t sa = smem_base + stage * C::kStageBytes;
                     if (sparse && KC > 1) {
                         // kept codes then metadata of all KC k-blocks (3-D chunk boxes)
                         tma_load_3d(sa, map_p, full_bar(stage), 0, row0, kb);
@@ -693,7 +759,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
                     }
                 }
             }
-            if (!ok) {
+            if (!ok && full_rank == rank) {
                 // let the copies already in flight land before the CTA exits:
                 // the latest arming of slot s has parity `phase` if s < stage
                 // (armed in the current round), else `phase ^ 1`
@@ -713,16 +779,22 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
             uint32_t phase = 0;
             int local = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x, ++local) {
-                const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
-                const ProblemScalars P = tile == static_cast<int>(blockIdx.x) ? P_first : prm.prob[tc.p];
+            // pairs: the even CTA issues the pair's MMAs
+            const int mma_tiles = (PAIR && rank != 0) ? 0 : my_tiles;
+            for (int tile = tile0; ok && tile < mma_tiles; tile += tile_step, ++local) {
+                const TileCoord tc = tile == tile0 ? tc_first : tile_coord(prm, tile);
+                const ProblemScalars P = tile == tile0 ? P_first : prm.prob[tc.p];
                 const bool sparse = P.sparse != 0;
                 const uint32_t idesc = P.idesc;
-                const uint32_t b_chunk = static_cast<uint32_t>(P.bn) * BK;      // B chunks bn x 128 B apart
+                const uint32_t b_chunk = PAIR ? static_cast<uint32_t>(C::kBChunk)
+                                              : static_cast<uint32_t>(P.bn) * BK;   // B chunks bn x 128 B apart
                 const int acc = local % C::kAcc;
                 const uint32_t acc_phase = (local / C::kAcc) & 1;
                 // an accumulator not used yet is free: no wait on its first use
-                if (local >= C::kAcc && !mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, wlim)) {
+                // (pairs: both CTAs' epilogues release it, the odd one remotely)
+                if (local >= C::kAcc &&
+                    !(PAIR ? mbar_wait_cluster(tempty_bar(acc), acc_phase ^ 1u, abort_flag, wlim)
+                           : mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, wlim))) {
                     abort_pipeline(abort_flag, err);
                     break;
                 }
@@ -734,13 +806,35 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
                 for (int kb = kb0; kb < kb1; kb += KC) {
                     const int nck = min(KC, kb1 - kb);          // k-blocks in this stage
                     const uint32_t first = kb == kb0 ? 0u : 1u;     // 0: overwrite the accumulator
-                    if (!mbar_wait(full_bar(stage), phase, abort_flag, wlim)) {
+                    if (!(PAIR ? mbar_wait_cluster(full_bar(stage), phase, abort_flag, wlim)
+                               : mbar_wait(full_bar(stage), phase, abort_flag, wlim))) {
                         ok = false;
                         abort_pipeline(abort_flag, err);
                         break;
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
+                    if constexpr (PAIR) {
+#pragma unroll
+                        for (int c = 0; c < KC; ++c) {
+                            if (c >= nck)
+                                break;
+                            // each CTA's 128 rows of A and of B sit at these offsets
+                            const uint64_t adesc = sdesc_kmajor_sw128(sa + c * C::kAChunk);
+                            const uint64_t bdesc_c = sdesc_kmajor_sw128(sa + C::kABytes + c * b_chunk);
+#pragma unroll
+                            for (int k = 0; k < BK / 32; ++k)
+                                mma_f8f6f4_pair(d_tmem, adesc + 2u * k, bdesc_c + 2u * k, idesc,
+                                                (first | c | k) != 0 ? 1u : 0u);
+                        }
+                        // the stage is free in both CTAs once these MMAs are done
+                        mma_commit_pair_multicast(empty_bar(stage), 0x3);
+                        if (++stage == S) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                        continue;
+                    }
                     if constexpr (MX) {
 #pragma unroll
                         for (int c = 0; c < KC; ++c) {
@@ -812,13 +906,24 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
                         phase ^= 1u;
                     }
                 }
-                if (ok)
-                    mma_commit(tfull_bar(acc));
+                if (ok) {
+                    if constexpr (PAIR)
+                        mma_commit_pair_multicast(tfull_bar(acc), 0x3);     // both CTAs' epilogues
+                    else
+                        mma_commit(tfull_bar(acc));
+                }
             }
             // every MMA this thread issued has finished before TMEM is freed
             const volatile int never = 0;
-            mma_commit(drain_bar);
-            mbar_wait(drain_bar, 0u, &never, wlim);
+            if constexpr (PAIR) {
+                if (rank == 0) {
+                    mma_commit_pair_multicast(drain_bar, 0x1);
+                    mbar_wait(drain_bar, 0u, &never, wlim);
+                }
+            } else {
+                mma_commit(drain_bar);
+                mbar_wait(drain_bar, 0u, &never, wlim);
+            }
         }
     } else {
         // ---------------------------------------------------- epilogue
@@ -828,13 +933,14 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
         const int row = half * BM + quarter * 32 + lane;
         int local = 0;
         uint32_t split_phase = 0;
-        for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++local) {
-            const TileCoord tc = tile == static_cast<int>(blockIdx.x) ? tc_first : tile_coord(prm, tile);
-            const ProblemScalars P = tile == static_cast<int>(blockIdx.x) ? P_first : prm.prob[tc.p];
+        for (int tile = tile0; tile < my_tiles; tile += tile_step, ++local) {
+            const TileCoord tc = tile == tile0 ? tc_first : tile_coord(prm, tile);
+            const ProblemScalars P = tile == tile0 ? P_first : prm.prob[tc.p];
             const int acc = local % C::kAcc;
             const uint32_t acc_phase = (local / C::kAcc) & 1;
             // the scales do not depend on the accumulator: load them first
-            const int i = tc.m_blk * BM * MT + row;
+            // (pairs: CTA r holds rows 128 r .. of the 256-row tile)
+            const int i = PAIR ? tc.m_blk * 2 * BM + BM * static_cast<int>(rank) + row : tc.m_blk * BM * MT + row;
             const bool row_ok = i < P.rows_p;
             const float fi = row_ok ? __fmul_rn(P.alpha, __ldg(P.sp + (P.sp_mode ? i : 0))) : 0.0f;
             const int jbase = tc.n_blk * P.bn;
@@ -850,12 +956,12 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>((acc + half) * BN_MAX);
             if (P.splits > 1 && cluster_split) {
-                const int rank = static_cast<int>(cluster_ctarank());
-                if (rank != tc.slice) {                 // launch shape broken: never expected
+                const int crank = static_cast<int>(cluster_ctarank());
+                if (crank != tc.slice) {                // launch shape broken: never expected
                     abort_pipeline(abort_flag, err);
                     break;
                 }
-                if (rank == 0) {
+                if (crank == 0) {
                     // every MMA of this unit has completed: the ring is free
                     if (threadIdx.x == 64)
                         for (int r = 1; r < P.splits; ++r)
@@ -872,7 +978,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
                         abort_pipeline(abort_flag, err);
                         break;
                     }
-                    cluster_send_partial(P, cluster_map(smem_base, 0u), BM * MT, rank, row, taddr);
+                    cluster_send_partial(P, cluster_map(smem_base, 0u), BM * MT, crank, row, taddr);
                     mbar_arrive_remote(cluster_map(split_written_bar, 0u));
                 }
                 tc_fence_before();
@@ -934,7 +1040,10 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
                 }
             }
             tc_fence_before();
-            mbar_arrive(tempty_bar(acc));
+            if (PAIR && rank != 0)
+                mbar_arrive_remote(cluster_map(tempty_bar(acc), 0u));     // the even CTA's barrier
+            else
+                mbar_arrive(tempty_bar(acc));
         }
         // TMA stores issued by this warp are complete before the CTA ends
         if (lane == 0)
@@ -947,12 +1056,17 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX>::kThreads, 1)
     tc_fence_before();
     __syncthreads();
     // cluster split-K: no CTA leaves while a peer may still write to its
-    // shared memory (every wait above is bounded, so all threads get here)
-    if (cluster_split)
+    // shared memory; pairs: neither CTA frees the pair's tensor memory (or
+    // its barriers) while the other may still use them (every wait above is
+    // bounded, so all threads get here)
+    if (PAIR || cluster_split)
         cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, TMEM_COLS);
+        if constexpr (PAIR)
+            tmem_dealloc_pair(tmem_base, C::kTmemCols);
+        else
+            tmem_dealloc(tmem_base, C::kTmemCols);
     }
 }
 
@@ -1179,7 +1293,12 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
 {
     memset(&pr, 0, sizeof(pr));
     pr.sparse = j.E != nullptr;
-    const int box_p = BM * mt;
+    // mt 3: a CTA pair per 256-row tile; each CTA's boxes are 128 rows of P
+    // and bn / 2 rows of Q
+    const bool pair = mt == 3;
+    const int box_p = pair ? BM : BM * mt;
+    const int box_q = pair ? bn / 2 : bn;
+    const int tile_p = pair ? 2 * BM : box_p;
     if (kc > 1 && pr.sparse) {
         // sparse K is a multiple of 128: kept codes in 64-byte chunks,
         // metadata in 16-byte chunks, B in 128-byte chunks
@@ -1191,7 +1310,7 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
     } else {
         pr.tma3d = kc > 1 && j.K % BK == 0 &&
                    make_map3(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BK, box_p, kc, CU_TENSOR_MAP_SWIZZLE_128B) &&
-                   make_map3(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, kc, CU_TENSOR_MAP_SWIZZLE_128B);
+                   make_map3(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, box_q, kc, CU_TENSOR_MAP_SWIZZLE_128B);
     }
     if (pr.tma3d) {
         // maps made above
@@ -1202,7 +1321,7 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
     } else if (!make_map(&pr.tmP, j.P, j.rows_p, j.K, j.ldp, BK, box_p, CU_TENSOR_MAP_SWIZZLE_128B)) {
         return FP8_ERR_CUDA;
     }
-    if (!pr.tma3d && !make_map(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, CU_TENSOR_MAP_SWIZZLE_128B))
+    if (!pr.tma3d && !make_map(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, box_q, CU_TENSOR_MAP_SWIZZLE_128B))
         return FP8_ERR_CUDA;
     pr.sp = j.sp;
     pr.sq = j.sq;
@@ -1220,13 +1339,13 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
     pr.vec_store = aligned16(j.C) && ((j.ldc * esz) % 16 == 0);
     pr.tma_store = pr.vec_store && !pr.trans_out && make_out_map(&pr.tmC, j.C, j.rows_p, j.rows_q, j.ldc, esz);
     pr.bn = bn;
-    pr.m_blocks = static_cast<int>((j.rows_p + box_p - 1) / box_p);
+    pr.m_blocks = static_cast<int>((j.rows_p + tile_p - 1) / tile_p);
     pr.n_blocks = static_cast<int>((j.rows_q + bn - 1) / bn);
     pr.k_blocks = static_cast<int>((j.K + BK - 1) / BK);
     pr.splits = split_count(j);
     pr.kb_per_split = pr.splits > 1 ? slice_kblocks(pr.k_blocks, pr.splits) : pr.k_blocks;
     pr.splits = (pr.k_blocks + pr.kb_per_split - 1) / pr.kb_per_split;     // no empty slice
-    pr.idesc = idesc_f8_f32(BM, bn, pr.sparse != 0, 0, mma_format(j.fmt_p), mma_format(j.fmt_q));
+    pr.idesc = idesc_f8_f32(pair ? 2 * BM : BM, bn, pr.sparse != 0, 0, mma_format(j.fmt_p), mma_format(j.fmt_q));
     if (j.sfp) {
         pr.idesc = idesc_mx_f8(BM, bn, mma_format(j.fmt_p), mma_format(j.fmt_q));
         pr.sfp = j.sfp;
@@ -1248,7 +1367,9 @@ int write_zeros(void* C, int64_t ldc, int64_t rows, int64_t cols, int out_bf16, 
 struct Plan {
     const void* func = nullptr;
     int grid = 0, threads = 0, smem = 0;
-    int cluster = 0;            // > 1: launched as clusters of this many CTAs (split-K in the cluster)
+    int cluster = 0;            // > 1: launched as clusters of this many CTAs (split-K in the
+                                // cluster, or 2: CTA pairs)
+    int kc = 1;                 // k-blocks per pipeline stage
     size_t ring_bytes = 0;      // bytes of the kernel's TMA ring
     size_t ws_floats = 0;       // split-K partials
     size_t ctr_count = 0;       // split-K tile counters
@@ -1285,10 +1406,10 @@ void bind_workspace(Params<MAXP>& prm, const Plan& pl, void* base)
     bind_workspace(prm, base, pl.ctr_count);
 }
 
-template <int MAXP, int MT, bool SP, int BNC = BN_MAX, int KC = 1, bool MX = false>
+template <int MAXP, int MT, bool SP, int BNC = BN_MAX, int KC = 1, bool MX = false, bool PAIR = false>
 int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
 {
-    using C = Cfg<MT, SP, BNC, KC, MX>;
+    using C = Cfg<MT, SP, BNC, KC, MX, PAIR>;
     static std::once_flag attr_once[64];
     int dev = 0;
     GB_CUDA_OK(cudaGetDevice(&dev));
@@ -1296,7 +1417,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
         return FP8_ERR_UNSUPPORTED;
     cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once[dev], [&] {
-        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC, MX>,
+        attr_err = cudaFuncSetAttribute(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC, MX, PAIR>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     });
     GB_CUDA_OK(attr_err);
@@ -1323,7 +1444,17 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     int grid = std::min(tiles, sm_count());
     if (max_ctas > 0)
         grid = std::min(grid, max_ctas);
-    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC, MX>);
+    if (PAIR) {
+        // one pair of CTAs per tile at most, SMs / 2 pairs (build_plan trims
+        // this to the pairs that can be resident at once)
+        int pairs = std::min(tiles, sm_count() / 2);
+        if (max_ctas > 0)
+            pairs = std::min(pairs, std::max(1, max_ctas / 2));
+        grid = 2 * pairs;
+    }
+    out->cluster = PAIR ? 2 : 0;
+    out->kc = KC;
+    out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC, MX, PAIR>);
     out->ring_bytes = static_cast<size_t>(C::kStages) * C::kStageBytes;
     out->grid = grid;
     out->threads = C::kThreads;
@@ -1370,16 +1501,16 @@ int launch_plan(Params<MAXP>& prm, const Plan& pl, cudaStream_t st)
     return FP8_OK;
 }
 
-// True when `clusters` clusters of `size` CTAs of the plan's kernel can all
-// be resident at once (each CTA needs an SM to itself; clusters must fit in
-// one GPC).  Cached per kernel variant and size.
-bool clusters_fit(const Plan& pl, int size, int clusters)
+// Clusters of `size` CTAs of the plan's kernel that can be resident at once
+// (each CTA needs an SM to itself; clusters must fit in one GPC).  Cached per
+// kernel variant and size.
+int max_clusters(const Plan& pl, int size)
 {
     static std::mutex mu;
     static std::map<std::tuple<int, const void*, int>, int> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess)
-        return false;
+        return 0;
     const auto key = std::make_tuple(dev, pl.func, size);
     int active = -1;
     {
@@ -1395,7 +1526,7 @@ bool clusters_fit(const Plan& pl, int size, int clusters)
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(static_cast<unsigned>(size * clusters));
+        cfg.gridDim = dim3(static_cast<unsigned>(size * std::max(1, sm_count() / size)));
         cfg.blockDim = dim3(pl.threads);
         cfg.dynamicSmemBytes = static_cast<size_t>(pl.smem);
         cfg.attrs = attr;
@@ -1407,7 +1538,12 @@ bool clusters_fit(const Plan& pl, int size, int clusters)
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = active;
     }
-    return active >= clusters;
+    return active;
+}
+
+bool clusters_fit(const Plan& pl, int size, int clusters)
+{
+    return max_clusters(pl, size) >= clusters;
 }
 
 // ---------------------------------------------------------------- tile choice
@@ -1458,6 +1594,11 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
     TileChoice c;
     if (expl && expl->mt) {
         c = *expl;
+        bool pair_ok = n > 0 && jobs[0].sfp == nullptr;
+        for (int i = 0; i < n; ++i)
+            pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
+        if (c.mt == 3 && !pair_ok)
+            c.mt = 1;
     } else {
         c.mt = g_force_mt.load(std::memory_order_relaxed);
         c.group_m = g_force_group_m.load(std::memory_order_relaxed);
@@ -1470,6 +1611,12 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
                     c.group_m = it->second.group_m;
             }
         }
+        // CTA pairs (mt 3) take dense problems whose N tiles are 256 wide
+        bool pair_ok = n > 0 && jobs[0].sfp == nullptr;
+        for (int i = 0; i < n; ++i)
+            pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
+        if (c.mt == 3 && !pair_ok)
+            c.mt = 0;
         if (c.mt == 0) {
             int64_t tiles2 = 0;
             bool ok2 = true;
@@ -1505,8 +1652,8 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
         all_sparse = all_sparse && jobs[i].E != nullptr;
     }
     // two k-blocks per stage for 128-row tiles up to 128 wide, unless the
-    // launch mixes dense and sparse problems
-    const int kc = (c.mt == 1 && max_bn <= 128 && (!any_sparse || all_sparse)) ? 2 : 1;
+    // launch mixes dense and sparse problems, and for CTA pairs
+    const int kc = ((c.mt == 1 && max_bn <= 128 && (!any_sparse || all_sparse)) || c.mt == 3) ? 2 : 1;
     for (int i = 0; i < n; ++i) {
         int bn = bns_in[i];
         if (c.mt == 2 && sparse)
@@ -1524,6 +1671,8 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
                            : plan<MAXP, 1, false, 128, 1, true>(prm, max_ctas, pl);
         return FP8_ERR_UNSUPPORTED;
     }
+    if (c.mt == 3)
+        return plan<MAXP, 1, false, BN_MAX, 2, false, true>(prm, max_ctas, pl);
     if (c.mt == 1) {
         if (kc == 2 && all_sparse) {
             if (max_bn <= 16)
@@ -1567,6 +1716,14 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
 {
     const int rc = build_plan_tiles(prm, jobs, bns_in, n, max_ctas, expl, pl);
     prm.cluster_split = 0;
+    if (rc == FP8_OK && pl->cluster == 2) {
+        // CTA pairs: no more pairs than can be resident at once
+        const int fit = max_clusters(*pl, 2);
+        if (fit < 1)
+            return FP8_ERR_UNSUPPORTED;
+        pl->grid = 2 * std::min(pl->grid / 2, fit);
+        return rc;
+    }
     pl->cluster = 0;
     if (rc != FP8_OK || !allow_cluster || n != 1 || max_ctas != 0)
         return rc;
@@ -1869,6 +2026,41 @@ extern "C" int gemm_fp8_dense_fmt(int64_t M, int64_t N, int64_t K, const uint8_t
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     return run_jobs(prm, &j, &bn, 1, 0, st, nullptr, true);
+}
+
+extern "C" int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info* info)
+{
+    using namespace gb300;
+    if (!info || M <= 0 || N <= 0 || K <= 0 || (out_dtype != 0 && out_dtype != 1))
+        return FP8_ERR_INVALID;
+    if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
+        return FP8_ERR_SHAPE;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    // tensor maps are encoded (never dereferenced) for an aligned stand-in
+    // address; the plan depends on the sizes only
+    const uint8_t* fake = reinterpret_cast<const uint8_t*>(uintptr_t(1) << 20);
+    const int64_t ld = (K + 15) / 16 * 16;
+    const float* one = device_one();
+    Job j = make_job(M, N, K, fake, ld, nullptr, fake, ld, one, 0, one, 0, 1.0f, const_cast<uint8_t*>(fake),
+                     N, out_dtype, 0, FP8_E4M3, FP8_E4M3);
+    const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX);
+    Params<1> prm;
+    memset(&prm, 0, sizeof(prm));
+    Plan pl;
+    const int rc = build_plan(prm, &j, &bn, 1, 0, nullptr, &pl, true);
+    if (rc != FP8_OK)
+        return rc;
+    const ProblemScalars& P = prm.prob[0];
+    info->mt = pl.cluster == 2 && !prm.cluster_split ? 3 : (pl.threads - 64) / 128;
+    info->bn = P.bn;
+    info->k_blocks_per_stage = pl.kc;
+    info->splits = P.splits;
+    info->cluster = pl.cluster > 1 ? pl.cluster : 0;
+    info->grid = pl.grid;
+    info->swapped = M <= 128 && N > M ? 1 : 0;          // make_job's rule for dense products
+    info->workspace_bytes = workspace_bytes(pl);
+    return FP8_OK;
 }
 
 // ---------------------------------------------------------------- no-allocation variant
@@ -2241,7 +2433,7 @@ extern "C" int gemm_fp8_tune_cache_load(const char* path)
         c.mt = static_cast<int>(strtol(p, &end, 10));
         p = end;
         c.group_m = static_cast<int>(strtol(p, &end, 10));
-        if (rc != FP8_OK || (c.mt != 1 && c.mt != 2) || c.group_m <= 0 || c.group_m > 4096) {
+        if (rc != FP8_OK || c.mt < 1 || c.mt > 3 || c.group_m <= 0 || c.group_m > 4096) {
             rc = FP8_ERR_INVALID;
             break;
         }
@@ -2299,6 +2491,14 @@ int graph_params(fp8_grouped_graph* g, const fp8_gemm_problem* problems, int num
     *sig = signature(jobs, bns, n, g->max_ctas);
     memset(&g->prm, 0, sizeof(g->prm));
     rc = build_plan(g->prm, jobs, bns, n, g->max_ctas, nullptr, &g->plan);
+    if (rc == FP8_OK && g->plan.cluster > 1) {
+        // a graph kernel node carries no cluster shape: CTA-pair tiles are
+        // replaced by 256-row tiles of one CTA (the same sums, the same bits)
+        TileChoice c;
+        c.mt = 2;
+        memset(&g->prm, 0, sizeof(g->prm));
+        rc = build_plan(g->prm, jobs, bns, n, g->max_ctas, &c, &g->plan);
+    }
     if (rc == FP8_OK)
         bind_workspace(g->prm, g->plan, g->ws);
     return rc;
@@ -2442,7 +2642,7 @@ void gb300::reset_split_counters()
 
 extern "C" int fp8_gemm_set_tile_config(int mt, int group_m)
 {
-    if (mt < 0 || mt > 2 || group_m < 0 || group_m > 4096)
+    if (mt < 0 || mt > 3 || group_m < 0 || group_m > 4096)
         return FP8_ERR_INVALID;
     gb300::g_force_mt.store(mt);
     gb300::g_force_group_m.store(group_m);

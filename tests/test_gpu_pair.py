@@ -1,0 +1,125 @@
+"""GPU parity of the CTA-pair GEMM tiles (tcgen05 cta_group::2).
+
+A 256 x 256 tile runs on a cluster of two CTAs: each loads 128 rows of A and
+128 rows of B, the even CTA issues the pair's MMAs, each CTA stores its half
+of the tile.  The tests force the pair tiles (fp8_gemm_set_tile_config(3)),
+check through gemm_fp8_dense_plan that the launch really uses them, and
+compare with the oracle (small-integer inputs bit for bit, N(0,1) inputs on
+sampled entries) and bitwise with the single-CTA 256-row tiles, which sum
+each entry in the same order.  Every wait runs with a 500 ms limit here, so
+a pipeline that never completes would show as FP8_ERR_TIMEOUT.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from tests import parity, sampled
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import paper_2602_10262_gb300 as gb
+    gb.library()
+    return gb
+
+
+@pytest.fixture
+def pair(gb):
+    gb.fp8_gemm_set_tile_config(3, 0)
+    gb.fp8_test_stall_gemm_loads(0, 500.0)
+    yield
+    gb.fp8_gemm_set_tile_config(0, 0)
+    gb.fp8_test_stall_gemm_loads(0, 0.0)
+
+
+SHAPES = [(2048, 2560, 1024), (1000, 3000, 640), (4096, 4096, 512), (2304, 2304, 4224)]
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_pair_tiles_are_planned(gb, pair, M, N, K):
+    info = gb.gemm_fp8_dense_plan(M, N, K)
+    assert info["mt"] == 3 and info["cluster"] == 2 and info["bn"] == 256, info
+    assert info["grid"] % 2 == 0 and info["workspace_bytes"] == 0 and info["splits"] == 1
+
+
+def _ones(n):
+    return torch.ones(n, dtype=torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_pair_small_integers_bit_exact(gb, orc, pair, M, N, K):
+    A = workloads.small_int_codes((M, K), seed=M + 1)
+    B = workloads.small_int_codes((N, K), seed=N + 2)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = gb.gemm_fp8_dense(At, Bt, _ones(1), 0, _ones(1), 0, 1.0, gb.OUT_F32)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    ref = orc.gemm(A, B, np.ones(1, np.float32), 0, np.ones(1, np.float32), 0)
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
+    gb.fp8_gemm_set_tile_config(2, 0)                     # single-CTA 256-row tiles
+    C2 = gb.gemm_fp8_dense(At, Bt, _ones(1), 0, _ones(1), 0, 1.0, gb.OUT_F32)
+    torch.cuda.synchronize()
+    assert torch.equal(C, C2)
+
+
+@pytest.mark.parametrize("out_dtype", [0, 1])
+def test_pair_normal_inputs_sampled(gb, orc, pair, out_dtype):
+    M, N, K = 4096, 4096, 4096
+    x = workloads.randn_f32((M, K), seed=71)
+    w = workloads.randn_f32((N, K), seed=72)
+    A, dA = gb.fp8_quantize_e4m3(torch.from_numpy(x).cuda(), 1)
+    B, dB = gb.fp8_quantize_e4m3(torch.from_numpy(w).cuda(), 1)
+    C = gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 0.5, out_dtype)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    ms, ns = sampled.entries(M, N, seed=73)
+    ref, S = sampled.reference(orc, x, w, ms, ns, alpha=0.5)
+    got = C[torch.from_numpy(ms).cuda(), torch.from_numpy(ns).cuda()].float().cpu().numpy()
+    if out_dtype:
+        parity.check_bf16(got, ref, S, K)
+    else:
+        parity.check_fp32(got, ref)
+
+
+def test_pair_grouped_equals_single_cta_tiles(gb, orc, pair):
+    shapes = [(2048, 2048, 1024), (1536, 4096, 512), (1024, 2560, 2048)]
+    probs, outs, keep = [], [], []
+    for i, (M, N, K) in enumerate(shapes):
+        A, dA = orc.quantize(workloads.randn_f32((M, K), seed=80 + i), 1)
+        B, dB = orc.quantize(workloads.randn_f32((N, K), seed=90 + i), 1)
+        t = [torch.from_numpy(v).cuda() for v in (A, B, dA, dB)]
+        C = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+        keep += t
+        outs.append(C)
+        probs.append(gb.make_problem(t[0], t[1], t[2], 1, t[3], 1, C, 1.0, gb.OUT_BF16))
+    gb.gemm_fp8_grouped(probs)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    got = [c.clone() for c in outs]
+    gb.fp8_gemm_set_tile_config(2, 0)
+    gb.gemm_fp8_grouped(probs)
+    torch.cuda.synchronize()
+    for a, b in zip(got, outs):
+        assert torch.equal(a, b)
+
+
+def test_pair_stalled_launch_times_out(gb, pair):
+    M, N, K = 2048, 2560, 1024
+    At = torch.from_numpy(workloads.small_int_codes((M, K), seed=5)).cuda()
+    Bt = torch.from_numpy(workloads.small_int_codes((N, K), seed=6)).cuda()
+    ref = gb.gemm_fp8_dense(At, Bt, _ones(1), 0, _ones(1), 0, 1.0, gb.OUT_F32)
+    assert gb.fp8_last_device_error() == 0
+    C = torch.full((M, N), float("nan"), device="cuda")
+    gb.fp8_test_stall_gemm_loads(1, 50.0)
+    try:
+        gb.gemm_fp8_dense(At, Bt, _ones(1), 0, _ones(1), 0, 1.0, gb.OUT_F32, C=C)
+        assert gb.fp8_last_device_error() == -7
+    finally:
+        gb.fp8_test_stall_gemm_loads(0, 500.0)
+    assert torch.isnan(C).all()
+    gb.gemm_fp8_dense(At, Bt, _ones(1), 0, _ones(1), 0, 1.0, gb.OUT_F32, C=C)
+    assert gb.fp8_last_device_error() == 0
+    assert torch.equal(C, ref)

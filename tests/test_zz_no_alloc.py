@@ -57,6 +57,13 @@ class DefaultPool:
         return self._attr(RESERVED_MEM_CURRENT), self._attr(USED_MEM_CURRENT)
 
 
+def _plan(lib, M, N, K):
+    from paper_2602_10262_gb300 import _lib
+    info = _lib.FP8PlanInfo()
+    assert lib.gemm_fp8_dense_plan(M, N, K, 0, ctypes.byref(info)) == 0
+    return info
+
+
 def _args(A, B, sa, sb, C, stream):
     M, K = A.shape
     N = B.shape[0]
@@ -88,6 +95,9 @@ def test_noalloc_equals_dense_and_oracle_two_calls(lib, orc):
     sms = lib.fp8_device_sm_count()
     M, N, K, need = _scratch_shape(min(sms // 8, 15))   # 15 tiles: 3.9 MB of the 4 MiB
     assert need <= SCRATCH_BYTES
+    info = _plan(lib, M, N, K)
+    assert info.splits == 8 and info.cluster == 0 and info.workspace_bytes == need, \
+        (info.splits, info.cluster, info.workspace_bytes, need)
     host, (A, B, sa, sb) = _operands(M, N, K)
     pool = DefaultPool()
     ref = torch.empty((M, N), dtype=torch.float32, device="cuda")
@@ -124,6 +134,8 @@ def test_noalloc_equals_dense_and_oracle_two_calls(lib, orc):
 def test_noalloc_without_scratch_equals_dense(lib, orc, M, N, K):
     # slices added up within clusters (the first two) or no split at all:
     # no scratch, and the same bits as gemm_fp8_dense
+    info = _plan(lib, M, N, K)
+    assert info.workspace_bytes == 0 and (info.splits == 1 or info.cluster == info.splits)
     host, (A, B, sa, sb) = _operands(M, N, K)
     st = torch.cuda.current_stream()
     ref = torch.empty((M, N), dtype=torch.float32, device="cuda")
@@ -143,6 +155,7 @@ def test_noalloc_rejects_scratch_beyond_the_array(lib):
     M, N, K, need = _scratch_shape(sms // 8)             # GB300: 19 tiles, 4.98 MB
     if need <= SCRATCH_BYTES:
         pytest.skip(f"{sms} SMs: the largest eight-slice split needs only {need} bytes")
+    assert _plan(lib, M, N, K).workspace_bytes == need
     dev = torch.device("cuda")
     A = torch.zeros((M, K), dtype=torch.uint8, device=dev)
     B = torch.zeros((N, K), dtype=torch.uint8, device=dev)
