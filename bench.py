@@ -1045,6 +1045,54 @@ def mx_sweep(gb, dev):
     return rows
 
 
+def pair_sweep(gb, dev):
+    """Dense GEMMs on CTA-pair tiles (mt 3, tcgen05 cta_group::2, 256 x 256
+    per SM pair) against one-CTA 256-row tiles (mt 2) and 128-row tiles
+    (mt 1): device time per call, L2-cold operand rotation, per-row scales,
+    bf16 out; the transformer layer as one grouped launch."""
+    rows = []
+    shapes = [(2048, 2048, 2048), (4096, 4096, 4096), (8192, 8192, 8192), (16384, 16384, 16384),
+              (2048, 8192, 8192), (8192, 2048, 8192), (4096, 14336, 4096)]
+    for M, N, K in shapes:
+        n = _l2_copies(dev, M * K + N * K)
+        ops = []
+        for i in range(n):
+            x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 200 + i)
+            del x, w
+            ops.append((A, dA, B, dB, torch.empty((M, N), dtype=torch.bfloat16, device=dev)))
+        fns = [lambda A=A, dA=dA, B=B, dB=dB, C=C: gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C)
+               for A, dA, B, dB, C in ops]
+        row = {"M": M, "N": N, "K": K, "operand_copies": n}
+        for mt in (1, 2, 3):
+            gb.fp8_gemm_set_tile_config(mt, 0)
+            row[f"mt{mt}_plan"] = gb.gemm_fp8_dense_plan(M, N, K)["mt"]
+            ms = _time_ms(fns)
+            row[f"mt{mt}_us"] = ms * 1e3
+            row[f"mt{mt}_tflops"] = 2.0 * M * N * K / ms / 1e9
+        gb.fp8_gemm_set_tile_config(0, 0)
+        rows.append(row)
+        del ops, fns
+    # transformer layer, one grouped launch
+    probs, keep = [], []
+    flops = 0.0
+    for i, (_, M, N, K) in enumerate(workloads.TRANSFORMER_LAYER):
+        x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 300 + i)
+        del x, w
+        C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+        keep += [A, dA, B, dB, C]
+        probs.append(gb.make_problem(A, B, dA, 1, dB, 1, C, 1.0, gb.OUT_BF16))
+        flops += 2.0 * M * N * K
+    layer = {"shape": "transformer layer, 4 GEMMs grouped"}
+    for mt in (1, 2, 3):
+        gb.fp8_gemm_set_tile_config(mt, 0)
+        ms = _time_ms(lambda: gb.gemm_fp8_grouped(probs))
+        layer[f"mt{mt}_ms"] = ms
+        layer[f"mt{mt}_tflops"] = flops / ms / 1e9
+    gb.fp8_gemm_set_tile_config(0, 0)
+    del keep
+    return {"gemms": rows, "layer": layer}
+
+
 def serving_policy_sweep(gb, dev, n=20000, load=0.8):
     """The batched server with the bulk tenant leaving R SMs free for the
     latency tenant, R in {0, 8, 16, 24, 32}, against per-call serving, on
@@ -1074,7 +1122,7 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
 
 
 SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency", "mx",
-                  "serving_policy", "served_concurrency")
+                  "serving_policy", "served_concurrency", "pair")
 
 
 def sweep(gb, dev, sections=SWEEP_SECTIONS):
@@ -1100,6 +1148,8 @@ def sweep(gb, dev, sections=SWEEP_SECTIONS):
         out["serving_policy"] = serving_policy_sweep(gb, dev)
     if "served_concurrency" in sections:
         out["served_concurrency"] = served_concurrency_sweep(gb, dev)
+    if "pair" in sections:
+        out["pair"] = pair_sweep(gb, dev)
     return out
 
 
@@ -1226,7 +1276,7 @@ def main():
     ap.add_argument("--sections", default=",".join(SWEEP_SECTIONS),
                     help="comma list of sweep tables: " + ", ".join(SWEEP_SECTIONS))
     ap.add_argument("--gemm", default=None,
-                    help="M,N,K[,sparse|mx][,e4m3|e5m2,e4m3|e5m2]: run only this GEMM (warmup + "
+                    help="M,N,K[,sparse|mx][,mt1|mt2|mt3][,e4m3|e5m2,e4m3|e5m2]: run only this GEMM (warmup + "
                          "steps launches; for profilers); the two formats are A's and B's")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -1244,10 +1294,13 @@ def main():
         M, N, K = (int(v) for v in f[:3])
         sparse = "sparse" in f[3:]
         mx = "mx" in f[3:]
-        fmts = [{"e4m3": 0, "e5m2": 1}[t] for t in f[3:] if t not in ("sparse", "mx")] or [0, 0]
+        fmts = [{"e4m3": 0, "e5m2": 1}[t] for t in f[3:] if t in ("e4m3", "e5m2")] or [0, 0]
         af, bf = fmts[0], fmts[-1]
         x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, 1, af, bf)
         C = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+        for t in f[3:]:
+            if t.startswith("mt"):
+                gb.fp8_gemm_set_tile_config(int(t[2:]), 0)
         if mx:
             A, SA = gb.fp8_quantize_mx(x, af, scale_layout=1)
             B, SB = gb.fp8_quantize_mx(w, bf, scale_layout=1)

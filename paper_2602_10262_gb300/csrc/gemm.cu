@@ -92,7 +92,8 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 // k-blocks per stage, three 64 KB stages) and holding its 128 x 256 half of
 // the accumulator; the even CTA issues the MMAs.  Per SM that is MT = 2's
 // bytes per FLOP with half of MT = 2's tensor memory per accumulator.
-constexpr int PAIR_TMEM_COLS = 256;       // columns per CTA (one accumulator)
+constexpr int PAIR_TMEM_COLS = 512;       // columns per CTA: two accumulators (the epilogue of
+                                          // one tile overlaps the MMAs of the next)
 
 template <int MT, bool SP = false, int BNC = BN_MAX, int KC = 1, bool MX = false, bool PAIR = false>
 struct Cfg {
