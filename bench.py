@@ -1093,6 +1093,31 @@ def pair_sweep(gb, dev):
     return {"gemms": rows, "layer": layer}
 
 
+def raster_sweep(gb, dev):
+    """Raster band height (M-blocks per band) of the tile walk for CTA-pair
+    tiles (mt 3) and one-CTA 256-row tiles (mt 2) on large squares: device
+    time per call, L2-cold rotation."""
+    rows = []
+    for n_ in (8192, 16384):
+        n = _l2_copies(dev, 2 * n_ * n_)
+        ops = []
+        for i in range(n):
+            x, w, A, dA, B, dB = _operands(gb, n_, n_, n_, dev, 400 + i)
+            del x, w
+            ops.append((A, dA, B, dB, torch.empty((n_, n_), dtype=torch.bfloat16, device=dev)))
+        fns = [lambda A=A, dA=dA, B=B, dB=dB, C=C: gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=C)
+               for A, dA, B, dB, C in ops]
+        for mt in (2, 3):
+            for gm in (2, 4, 8, 12, 16, 32, 64):
+                gb.fp8_gemm_set_tile_config(mt, gm)
+                ms = _time_ms(fns)
+                rows.append({"n": n_, "mt": mt, "group_m": gm, "us": ms * 1e3,
+                             "tflops": 2.0 * n_ ** 3 / ms / 1e9})
+        gb.fp8_gemm_set_tile_config(0, 0)
+        del ops, fns
+    return rows
+
+
 def serving_policy_sweep(gb, dev, n=20000, load=0.8):
     """The batched server with the bulk tenant leaving R SMs free for the
     latency tenant, R in {0, 8, 16, 24, 32}, against per-call serving, on
@@ -1122,7 +1147,7 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
 
 
 SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency", "mx",
-                  "serving_policy", "served_concurrency", "pair")
+                  "serving_policy", "served_concurrency", "pair", "raster")
 
 
 def sweep(gb, dev, sections=SWEEP_SECTIONS):
@@ -1150,6 +1175,8 @@ def sweep(gb, dev, sections=SWEEP_SECTIONS):
         out["served_concurrency"] = served_concurrency_sweep(gb, dev)
     if "pair" in sections:
         out["pair"] = pair_sweep(gb, dev)
+    if "raster" in sections:
+        out["raster"] = raster_sweep(gb, dev)
     return out
 
 
@@ -1271,6 +1298,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--tile", default=None,
+                    help="mt[,group_m]: force the GEMM tile kind (1, 2, 3 = CTA pairs) and raster band")
     ap.add_argument("--sweep", default=None,
                     help="write the measurement tables to this JSON file and exit")
     ap.add_argument("--sections", default=",".join(SWEEP_SECTIONS),
@@ -1289,6 +1318,9 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     gb.library()
+    if args.tile:
+        t = [int(v) for v in args.tile.split(",")]
+        gb.fp8_gemm_set_tile_config(t[0], t[1] if len(t) > 1 else 0)
     if args.gemm:
         f = args.gemm.split(",")
         M, N, K = (int(v) for v in f[:3])
