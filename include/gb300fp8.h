@@ -380,9 +380,11 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * per FLOP), 3 (256 x 256 tiles of a CTA pair, tcgen05 cta_group::2: each
  * CTA of a two-CTA cluster loads 128 rows of A and 128 rows of B and holds
  * its half of the accumulator; dense launches whose N tiles are 256 wide,
- * otherwise as 0), 0 = chosen per launch (2 when every problem fills
- * 256-row tiles with N tiles >= 128 wide and those tiles number at least
- * half the SMs; a launch mixing dense and sparse problems always uses 1).
+ * otherwise as 0), 0 = chosen per launch (256-row tiles when every problem
+ * fills them with N tiles >= 128 wide and those tiles number at least half
+ * the SMs: 3 when the problems are dense with 256-wide N tiles, else 2; a
+ * launch mixing dense and sparse problems always uses 1; CUDA-graph
+ * launches (gemm_fp8_grouped_graph_*) use 2 in place of 3).
  * group_m: M-blocks per raster band (0 = 16).  Results do not depend on
  * either.  Affects launches enqueued after the call, from any thread. */
 int fp8_gemm_set_tile_config(int mt, int group_m);
@@ -403,26 +405,32 @@ typedef struct {
 
 int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info *info);
 
-/* Autotuner: times every candidate tile configuration (mt in {1, 2}, raster
- * band group_m in {2, 4, 8, 16, 32}) of this exact problem list on `stream`
- * (iters timed launches each, after one warm-up; the problems' outputs are
- * written each time), records the fastest in the process-wide tile cache
- * under the list's shape signature (sizes, dense/sparse, output type and
- * layout, max_ctas) and returns it.  Later launches with the same signature
+/* Autotuner: times every candidate tile configuration of this exact problem
+ * list on `stream` (iters timed launches each, after one warm-up; the
+ * problems' outputs are written each time): tile kind mt in {1, 2, 3} (3 only
+ * for dense lists whose N tiles are 256 wide), raster band group_m in {2, 4,
+ * 8, 16, 32}, and for 128-row tiles a cap of 128 or 64 on the N tile width
+ * (which also selects the pipeline ring: two k-blocks per stage up to 128
+ * wide).  K splits stay as the problems fix them, so no candidate changes a
+ * result.  Records the fastest in the process-wide tile cache under the
+ * list's shape signature (sizes, dense/sparse, output type and layout,
+ * max_ctas) and returns it.  Later launches with the same signature
  * (grouped or single calls) use the cached choice unless
  * fp8_gemm_set_tile_config forces one.  Synchronises `stream`. */
 typedef struct {
     int mt;
     int group_m;
     float ms_per_launch;
+    int bn_max;               /* N tile cap of the choice (0: the problems' own widths) */
 } fp8_tile_config;
 
 int gemm_fp8_grouped_autotune(const fp8_gemm_problem *problems, int num_problems, int max_ctas,
                               int iters, fp8_stream_t stream, fp8_tile_config *best);
 
 /* Persist / restore / empty the tile cache (a text file, one signature per
- * line).  Loading merges into the current cache; a malformed file changes
- * nothing and returns FP8_ERR_INVALID. */
+ * line: the signature, mt, group_m and the N tile cap; lines without the
+ * cap read as 0).  Loading merges into the current cache; a malformed file
+ * changes nothing and returns FP8_ERR_INVALID. */
 int gemm_fp8_tune_cache_save(const char *path);
 int gemm_fp8_tune_cache_load(const char *path);
 int gemm_fp8_tune_cache_clear(void);

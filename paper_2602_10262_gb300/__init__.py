@@ -420,13 +420,14 @@ def gemm_fp8_grouped_ex(problems: Sequence[_lib.FP8Problem], max_ctas: int = 0,
 def gemm_fp8_grouped_autotune(problems: Sequence[_lib.FP8Problem], max_ctas: int = 0,
                               iters: int = 3, stream=None) -> dict:
     """Time every tile configuration for this problem list, cache the fastest
-    and return it as {"mt", "group_m", "ms_per_launch"}."""
+    and return it as {"mt", "group_m", "ms_per_launch", "bn_max"}."""
     arr = (_lib.FP8Problem * len(problems))(*problems)
     best = _lib.FP8TileConfig()
     rc = library().gemm_fp8_grouped_autotune(arr, len(problems), int(max_ctas), int(iters),
                                              _stream(stream), ctypes.byref(best))
     _check(rc, "gemm_fp8_grouped_autotune")
-    return {"mt": best.mt, "group_m": best.group_m, "ms_per_launch": best.ms_per_launch}
+    return {"mt": best.mt, "group_m": best.group_m, "ms_per_launch": best.ms_per_launch,
+            "bn_max": best.bn_max}
 
 
 def gemm_fp8_tune_cache_save(path: str) -> None:

@@ -44,7 +44,7 @@ class FP8QuantJob(ctypes.Structure):
 
 class FP8TileConfig(ctypes.Structure):
     """Mirror of ``fp8_tile_config``."""
-    _fields_ = [("mt", I32), ("group_m", I32), ("ms_per_launch", F32)]
+    _fields_ = [("mt", I32), ("group_m", I32), ("ms_per_launch", F32), ("bn_max", I32)]
 
 
 class FP8PlanInfo(ctypes.Structure):

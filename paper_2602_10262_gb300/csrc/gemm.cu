@@ -1555,6 +1555,7 @@ std::atomic<int> g_force_group_m{0};
 struct TileChoice {
     int mt = 0;        // 0: not set
     int group_m = 0;
+    int bn_cap = 0;    // > 0: N tiles at most this wide (and the ring that width selects)
 };
 
 // Shape signature of a launch: what the best tile choice depends on.
@@ -1584,18 +1585,19 @@ bool mixed_kinds(const Job* jobs, int n)
 
 // Tile shape of a launch, in order of precedence: an explicit choice (the
 // autotuner's candidates), the process-wide override, the autotuner's cached
-// winner for this shape signature, the heuristic.  Heuristic: MT = 2
-// (256-row tiles, a third fewer operand bytes per FLOP) when every problem
-// fills 256-row tiles with a wide N tile, there are at least as many such
-// tiles as SMs and the problems are all dense or all sparse; otherwise MT = 1
+// winner for this shape signature, the heuristic.  Heuristic: 256-row tiles
+// (a third fewer operand bytes per FLOP) when every problem fills them with
+// a wide N tile, they give at least half the SMs a tile and the problems are
+// all dense or all sparse: as CTA pairs (mt 3) when every problem is dense
+// with 256-wide N tiles, else on one CTA (mt 2); otherwise 128-row tiles
 // (more, smaller tiles keep every SM busy on skinny and small problems).
-// Dense and sparse problems share only the MT = 1 layout.
+// Dense and sparse problems share only the 128-row layout.
 TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const TileChoice* expl)
 {
     TileChoice c;
     if (expl && expl->mt) {
         c = *expl;
-        bool pair_ok = n > 0 && jobs[0].sfp == nullptr;
+        bool pair_ok = n > 0 && jobs[0].sfp == nullptr && (c.bn_cap == 0 || c.bn_cap >= BN_MAX);
         for (int i = 0; i < n; ++i)
             pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
         if (c.mt == 3 && !pair_ok)
@@ -1608,12 +1610,13 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
             auto it = g_tuned.find(signature(jobs, bns, n, max_ctas));
             if (it != g_tuned.end()) {
                 c.mt = it->second.mt;
+                c.bn_cap = it->second.bn_cap;
                 if (c.group_m == 0)
                     c.group_m = it->second.group_m;
             }
         }
         // CTA pairs (mt 3) take dense problems whose N tiles are 256 wide
-        bool pair_ok = n > 0 && jobs[0].sfp == nullptr;
+        bool pair_ok = n > 0 && jobs[0].sfp == nullptr && (c.bn_cap == 0 || c.bn_cap >= BN_MAX);
         for (int i = 0; i < n; ++i)
             pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
         if (c.mt == 3 && !pair_ok)
@@ -1627,8 +1630,10 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
                 tiles2 += ((jobs[i].rows_p + 2 * BM - 1) / (2 * BM)) * ((jobs[i].rows_q + bns[i] - 1) / bns[i]);
             }
             // 256-row tiles load a third fewer bytes per MMA; take them
-            // while they still give at least half the SMs a tile
-            c.mt = ok2 && 2 * tiles2 >= sm_count() ? 2 : 1;
+            // while they still give at least half the SMs a tile, on CTA
+            // pairs where the launch allows them (measured: the tensor pipe
+            // 85 % busy at 8192^3 against 75 % for one-CTA 256-row tiles)
+            c.mt = ok2 && 2 * tiles2 >= sm_count() ? (pair_ok ? 3 : 2) : 1;
         }
     }
     if (mixed_kinds(jobs, n) || (n > 0 && jobs[0].sfp != nullptr))
@@ -1645,10 +1650,15 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
 {
     const TileChoice c = choose(jobs, bns_in, n, max_ctas, expl);
     const bool sparse = n > 0 && jobs[0].E != nullptr;     // all alike when mt == 2
+    // N tile widths: the problems' own, under the tuned cap if any (block-
+    // scaled launches always use 128)
+    int bns[MAXP > 0 ? MAXP : 1];
+    for (int i = 0; i < n; ++i)
+        bns[i] = (c.bn_cap > 0 && jobs[i].sfp == nullptr) ? std::min(bns_in[i], c.bn_cap) : bns_in[i];
     int max_bn = 0;
     bool any_sparse = false, all_sparse = n > 0;
     for (int i = 0; i < n; ++i) {
-        max_bn = std::max(max_bn, bns_in[i]);
+        max_bn = std::max(max_bn, bns[i]);
         any_sparse = any_sparse || jobs[i].E != nullptr;
         all_sparse = all_sparse && jobs[i].E != nullptr;
     }
@@ -1656,7 +1666,7 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
     // launch mixes dense and sparse problems, and for CTA pairs
     const int kc = ((c.mt == 1 && max_bn <= 128 && (!any_sparse || all_sparse)) || c.mt == 3) ? 2 : 1;
     for (int i = 0; i < n; ++i) {
-        int bn = bns_in[i];
+        int bn = bns[i];
         if (c.mt == 2 && sparse)
             bn = std::min(bn, SPARSE_BN_MAX_MT2);
         int rc = fill_problem(prm.prob[i], jobs[i], bn, c.mt, kc);
@@ -2332,37 +2342,53 @@ extern "C" int gemm_fp8_grouped_autotune(const fp8_gemm_problem* problems, int n
     GB_CUDA_OK(cudaEventCreate(&e1));
     TileChoice winner;
     float best_ms = 0.0f;
-    const int mts[2] = {1, 2};
+    // candidates: tile kind (128-row, 256-row, CTA pair), raster band height,
+    // and for 128-row tiles a cap on the N width (which also picks the ring:
+    // two k-blocks per stage up to 128 wide); split counts stay fixed per
+    // problem, so no candidate changes a result
+    int max_bn = 0;
+    bool pair_ok = jobs[0].sfp == nullptr;
+    for (int i = 0; i < n; ++i) {
+        max_bn = std::max(max_bn, bns[i]);
+        pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
+    }
+    std::vector<TileChoice> cands;
     const int gms[5] = {2, 4, 8, 16, 32};
-    for (int mt : mts) {
-        if (mt == 2 && mixed_kinds(jobs, n))
+    for (int mt = 1; mt <= 3; ++mt) {
+        if ((mt == 2 && mixed_kinds(jobs, n)) || (mt == 3 && !pair_ok))
             continue;
-        for (int gm : gms) {
-            TileChoice c;
-            c.mt = mt;
-            c.group_m = gm;
-            memset(&prm, 0, sizeof(prm));
-            rc = run_jobs(prm, jobs, bns, n, max_ctas, st, &c);            // warm-up
-            for (int it = 0; rc == FP8_OK && it < iters; ++it) {
-                if (it == 0 && cudaEventRecord(e0, st) != cudaSuccess)
-                    rc = FP8_ERR_CUDA;
-                if (rc == FP8_OK)
-                    rc = run_jobs(prm, jobs, bns, n, max_ctas, st, &c);
-            }
-            float ms = 0.0f;
-            if (rc == FP8_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
-                                 cudaEventSynchronize(e1) != cudaSuccess ||
-                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                rc = FP8_ERR_CUDA;
-            if (rc != FP8_OK)
-                break;
-            if (winner.mt == 0 || ms < best_ms) {
-                winner = c;
-                best_ms = ms;
+        for (int cap : {0, 128, 64}) {
+            if (cap && (mt != 1 || cap >= max_bn))
+                continue;
+            for (int gm : gms) {
+                TileChoice c;
+                c.mt = mt;
+                c.group_m = gm;
+                c.bn_cap = cap;
+                cands.push_back(c);
             }
         }
+    }
+    for (const TileChoice& c : cands) {
+        memset(&prm, 0, sizeof(prm));
+        rc = run_jobs(prm, jobs, bns, n, max_ctas, st, &c);                // warm-up
+        for (int it = 0; rc == FP8_OK && it < iters; ++it) {
+            if (it == 0 && cudaEventRecord(e0, st) != cudaSuccess)
+                rc = FP8_ERR_CUDA;
+            if (rc == FP8_OK)
+                rc = run_jobs(prm, jobs, bns, n, max_ctas, st, &c);
+        }
+        float ms = 0.0f;
+        if (rc == FP8_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = FP8_ERR_CUDA;
         if (rc != FP8_OK)
             break;
+        if (winner.mt == 0 || ms < best_ms) {
+            winner = c;
+            best_ms = ms;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2376,6 +2402,7 @@ extern "C" int gemm_fp8_grouped_autotune(const fp8_gemm_problem* problems, int n
         best->mt = winner.mt;
         best->group_m = winner.group_m;
         best->ms_per_launch = best_ms / static_cast<float>(iters);
+        best->bn_max = winner.bn_cap;
     }
     return FP8_OK;
 }
@@ -2389,12 +2416,12 @@ extern "C" int gemm_fp8_tune_cache_save(const char* path)
     if (!f)
         return FP8_ERR_INVALID;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    fprintf(f, "# gb300fp8 tile cache v1: <signature length> <signature...> <mt> <group_m>\n");
+    fprintf(f, "# gb300fp8 tile cache v2: <signature length> <signature...> <mt> <group_m> <bn cap>\n");
     for (const auto& kv : g_tuned) {
         fprintf(f, "%zu", kv.first.size());
         for (int64_t v : kv.first)
             fprintf(f, " %lld", static_cast<long long>(v));
-        fprintf(f, " %d %d\n", kv.second.mt, kv.second.group_m);
+        fprintf(f, " %d %d %d\n", kv.second.mt, kv.second.group_m, kv.second.bn_cap);
     }
     fclose(f);
     return FP8_OK;
@@ -2434,7 +2461,12 @@ extern "C" int gemm_fp8_tune_cache_load(const char* path)
         c.mt = static_cast<int>(strtol(p, &end, 10));
         p = end;
         c.group_m = static_cast<int>(strtol(p, &end, 10));
-        if (rc != FP8_OK || c.mt < 1 || c.mt > 3 || c.group_m <= 0 || c.group_m > 4096) {
+        p = end;                                  // optional bn cap (v2 lines)
+        c.bn_cap = static_cast<int>(strtol(p, &end, 10));
+        if (end == p)
+            c.bn_cap = 0;
+        if (rc != FP8_OK || c.mt < 1 || c.mt > 3 || c.group_m <= 0 || c.group_m > 4096 ||
+            (c.bn_cap != 0 && c.bn_cap != 64 && c.bn_cap != 128)) {
             rc = FP8_ERR_INVALID;
             break;
         }

@@ -137,9 +137,15 @@ def test_tune_cache_file_round_trip(lib, tmp_path):
     out = tmp_path / "saved.txt"
     assert lib.gemm_fp8_tune_cache_save(str(out).encode()) == 0
     lines = [l for l in out.read_text().splitlines() if not l.startswith("#")]
-    assert lines == ["9 1 0 8192 4096 4096 0 256 1 0 2 16"]
+    assert lines == ["9 1 0 8192 4096 4096 0 256 1 0 2 16 0"]        # a line without a cap reads as 0
+    good.write_text("9 1 0 8192 4096 4096 0 256 1 0 1 8 64\n")
+    assert lib.gemm_fp8_tune_cache_clear() == 0
+    assert lib.gemm_fp8_tune_cache_load(str(good).encode()) == 0
+    assert lib.gemm_fp8_tune_cache_save(str(out).encode()) == 0
+    lines = [l for l in out.read_text().splitlines() if not l.startswith("#")]
+    assert lines == ["9 1 0 8192 4096 4096 0 256 1 0 1 8 64"]
     for bad in ("3 1 2\n", "9 1 0 8192 4096 4096 0 256 1 0 7 16\n", "x y z\n",
-                "9 1 0 8192 4096 4096 0 256 1 0 2 0\n"):
+                "9 1 0 8192 4096 4096 0 256 1 0 2 0\n", "9 1 0 8192 4096 4096 0 256 1 0 1 8 96\n"):
         f = tmp_path / "bad.txt"
         f.write_text(bad)
         assert lib.gemm_fp8_tune_cache_load(str(f).encode()) == -1
