@@ -1132,9 +1132,10 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
     out = {"offered_req_per_s": rate, "requests": n, "rows": []}
     cfgs = [("per_call", dict(batching=False))] + \
         [(f"batched_reserve_{r}", dict(batching=True, bulk_max_ctas=(sms - r) if r else 0))
-         for r in (0, 8, 16, 24, 32)] + \
-        [(f"batched_reserve_{r}_latency_capped", dict(batching=True, bulk_max_ctas=sms - r, latency_max_ctas=r))
-         for r in (8, 16, 24, 32, 48)]
+         for r in (0, 16, 32)] + \
+        [(f"batched_waves_{w}x", dict(batching=True, bulk_max_ctas=w * sms)) for w in (2, 4, 8, 16)] + \
+        [(f"batched_waves_{w}x_latency_waves", dict(batching=True, bulk_max_ctas=w * sms,
+                                                    latency_max_ctas=w * sms)) for w in (4,)]
     for name, cfg in cfgs:
         lat, span, _, _ = sb.run(reqs, cfg, rate)
         _, cspan, _, _ = sb.run(reqs[:8000], cfg)

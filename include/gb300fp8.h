@@ -366,11 +366,14 @@ typedef struct {
 
 int gemm_fp8_grouped(const fp8_gemm_problem *problems, int num_problems, fp8_stream_t stream);
 
-/* As gemm_fp8_grouped, with the persistent grid capped at max_ctas CTAs
- * (one per SM; max_ctas <= 0 means every SM).  Leaving SMs free lets work on
- * another stream (a latency-sensitive tenant) run beside this launch — the
- * occupancy-aware co-scheduling the paper recommends in section 8.2.  The
- * results do not depend on max_ctas. */
+/* As gemm_fp8_grouped, with the grid capped at max_ctas CTAs (max_ctas <= 0:
+ * one CTA per SM).  Below the SM count, SMs are left free so work on another
+ * stream (a latency-sensitive tenant) runs beside this launch — the
+ * occupancy-aware co-scheduling the paper recommends in section 8.2.  Above
+ * it, the launch has more CTAs than SMs, each taking a few tiles and
+ * running in waves, so SMs are handed back between tiles (higher-priority
+ * streams get them then) instead of being held to the launch's last tile.
+ * The results do not depend on max_ctas. */
 int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int max_ctas,
                         fp8_stream_t stream);
 
@@ -492,7 +495,9 @@ typedef struct {
     int batching;             /* 1: continuous batching; 0: one launch per request */
     int max_batch;            /* requests per batch, 1..FP8_GROUPED_MAX_PROBLEMS (0: max) */
     int max_inflight;         /* in-flight batches per bulk tenant (0: 4) */
-    int bulk_max_ctas;        /* CTA cap for non-latency tenants' GEMMs (0: all SMs) */
+    int bulk_max_ctas;        /* grid cap for non-latency tenants' GEMMs (0: one CTA
+                                 per SM; above the SM count: CTAs in waves, see
+                                 gemm_fp8_grouped_ex) */
     size_t pool_bytes;        /* workspace pool; 0: free HBM minus reserve_bytes */
     size_t reserve_bytes;     /* HBM left untouched when sizing the pool (0: 1 GiB) */
     int latency_max_batch;    /* with batching: requests per batch of the latency

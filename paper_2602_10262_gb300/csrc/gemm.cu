@@ -1442,16 +1442,14 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     prm.err = device_error_word();
     prm.wait_ns = kWaitLimitNs;
     prm.withhold_loads = 0;
-    int grid = std::min(tiles, sm_count());
-    if (max_ctas > 0)
-        grid = std::min(grid, max_ctas);
+    // persistent: one CTA per SM; a cap above the SM count launches more
+    // CTAs than SMs, which then run in waves of a few tiles each
+    const int cap = max_ctas > 0 ? max_ctas : sm_count();
+    int grid = std::min(tiles, cap);
     if (PAIR) {
-        // one pair of CTAs per tile at most, SMs / 2 pairs (build_plan trims
-        // this to the pairs that can be resident at once)
-        int pairs = std::min(tiles, sm_count() / 2);
-        if (max_ctas > 0)
-            pairs = std::min(pairs, std::max(1, max_ctas / 2));
-        grid = 2 * pairs;
+        // one pair of CTAs per tile at most (build_plan trims a persistent
+        // launch to the pairs that can be resident at once)
+        grid = 2 * std::min(tiles, std::max(1, cap / 2));
     }
     out->cluster = PAIR ? 2 : 0;
     out->kc = KC;
@@ -1728,11 +1726,13 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
     const int rc = build_plan_tiles(prm, jobs, bns_in, n, max_ctas, expl, pl);
     prm.cluster_split = 0;
     if (rc == FP8_OK && pl->cluster == 2) {
-        // CTA pairs: no more pairs than can be resident at once
+        // CTA pairs: a persistent launch takes no more pairs than can be
+        // resident at once (a launch in waves may take more)
         const int fit = max_clusters(*pl, 2);
         if (fit < 1)
             return FP8_ERR_UNSUPPORTED;
-        pl->grid = 2 * std::min(pl->grid / 2, fit);
+        if (max_ctas <= sm_count())
+            pl->grid = 2 * std::min(pl->grid / 2, fit);
         return rc;
     }
     pl->cluster = 0;

@@ -53,7 +53,7 @@ def test_autotune_picks_a_config_and_keeps_results(gb, orc, tmp_path):
     path = str(tmp_path / "tiles.txt")
     gb.gemm_fp8_tune_cache_save(path)
     text = open(path).read()
-    assert f" {best['mt']} {best['group_m']}\n" in text
+    assert f" {best['mt']} {best['group_m']} {best['bn_max']}\n" in text
     gb.gemm_fp8_tune_cache_clear()
     gb.gemm_fp8_tune_cache_load(path)
     assert gb.fp8_last_device_error() == 0
