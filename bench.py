@@ -385,15 +385,20 @@ class ServingBench:
         return [dict(tenant=int(t), M=int(m), N=int(nn), K=int(k), sparse=bool(sp), gap=float(gp), row=int(r0))
                 for t, m, nn, k, sp, gp, r0 in zip(tenant, M, N, K, sparse, gap, row)]
 
+    LATENCY_POOL = 1 << 30         # pool bytes the bulk tenant leaves to the latency tenant
+
     def modes(self):
         sms = self.gb.fp8_device_sm_count()
         return {"per_call": dict(batching=False),
-                "batched": dict(batching=True, bulk_max_ctas=max(sms - self.RESERVE, 1)),
-                "batched_no_reserve": dict(batching=True)}
+                "batched": dict(batching=True, bulk_max_ctas=max(sms - self.RESERVE, 1),
+                                latency_pool_bytes=self.LATENCY_POOL),
+                "batched_no_reserve": dict(batching=True, latency_pool_bytes=self.LATENCY_POOL)}
 
     def _server(self, mode_cfg):
         from paper_2602_10262_gb300.server import Server
-        srv = Server(num_tenants=2, latency_tenant=0, pool_bytes=8 << 30, **mode_cfg)
+        cfg = dict(mode_cfg)
+        pool = cfg.pop("pool_bytes", 8 << 30)
+        srv = Server(num_tenants=2, latency_tenant=0, pool_bytes=pool, **cfg)
         handles = {}
         for (N, K), (Wd, dW, vals, meta) in self.weights.items():
             handles[(N, K, False)] = srv.register_weight(N, K, Wd, dW, 1)
@@ -533,6 +538,8 @@ def serving_report(gb, dev, n_cap=20000, n_load=20000, loads=(0.8,), n_iso=2000)
                 "fairness_min_over_max": min(x) / max(x),
                 "overlap_efficiency": overlap_efficiency(res),
                 "mean_batch": float(np.mean([r.batch_size for r in res])),
+                "max_batch": int(stats["max_batch_seen"]),
+                "pool_high_water_mb": stats["pool_high_water"] / 2 ** 20,
                 "kernel_launches": stats["kernel_launches"],
             }
         if i == 0:
@@ -1130,20 +1137,29 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
     _, span, _, _ = sb.run(reqs, dict(batching=False))
     rate = load * n / (span * 1e-6)
     out = {"offered_req_per_s": rate, "requests": n, "rows": []}
-    cfgs = [("per_call", dict(batching=False))] + \
-        [(f"batched_reserve_{r}", dict(batching=True, bulk_max_ctas=(sms - r) if r else 0))
-         for r in (0, 16, 32)] + \
-        [(f"batched_waves_{w}x", dict(batching=True, bulk_max_ctas=w * sms)) for w in (2, 4, 8, 16)] + \
-        [(f"batched_waves_{w}x_latency_waves", dict(batching=True, bulk_max_ctas=w * sms,
-                                                    latency_max_ctas=w * sms)) for w in (4,)]
+    share = dict(latency_pool_bytes=ServingBench.LATENCY_POOL)
+    cfgs = [("per_call", dict(batching=False)),
+            ("batched_reserve_16", dict(batching=True, bulk_max_ctas=sms - 16)),
+            ("batched_reserve_16_latency_pool", dict(batching=True, bulk_max_ctas=sms - 16, **share)),
+            ("batched_reserve_16_pool_32g", dict(batching=True, bulk_max_ctas=sms - 16, pool_bytes=32 << 30)),
+            ("batched_reserve_0_latency_pool", dict(batching=True, **share)),
+            ("batched_reserve_32_latency_pool", dict(batching=True, bulk_max_ctas=sms - 32, **share)),
+            ("batched_waves_8x_latency_pool", dict(batching=True, bulk_max_ctas=8 * sms, **share))]
+    traces = [reqs, sb.trace(n, workloads.SEED_REQUESTS + 7)]
     for name, cfg in cfgs:
-        lat, span, _, _ = sb.run(reqs, cfg, rate)
-        _, cspan, _, _ = sb.run(reqs[:8000], cfg)
-        out["rows"].append({"mode": name,
-                            "p99_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 99)) for t in (0, 1)},
-                            "p50_us": {f"tenant{t}": float(np.percentile(lat[tenant == t], 50)) for t in (0, 1)},
-                            "p99_all_us": float(np.percentile(lat, 99)),
-                            "capacity_req_per_s": 8000 / (cspan * 1e-6)})
+        for k, tr in enumerate(traces):
+            ten = np.array([r["tenant"] for r in tr])
+            lat, span, stats, _ = sb.run(tr, cfg, rate)
+            row = {"mode": name, "trace": k,
+                   "p99_us": {f"tenant{t}": float(np.percentile(lat[ten == t], 99)) for t in (0, 1)},
+                   "p50_us": {f"tenant{t}": float(np.percentile(lat[ten == t], 50)) for t in (0, 1)},
+                   "p99_all_us": float(np.percentile(lat, 99)),
+                   "pool_high_water_mb": stats["pool_high_water"] / 2 ** 20,
+                   "max_batch": int(stats["max_batch_seen"])}
+            if k == 0:
+                _, cspan, _, _ = sb.run(tr[:8000], cfg)
+                row["capacity_req_per_s"] = 8000 / (cspan * 1e-6)
+            out["rows"].append(row)
     return out
 
 

@@ -506,6 +506,8 @@ typedef struct {
     int latency_max_ctas;     /* CTA cap for the latency tenant's GEMMs (0: all
                                  SMs); set to the SMs bulk_max_ctas leaves free,
                                  its work never waits for SMs held by bulk GEMMs */
+    size_t latency_pool_bytes; /* pool bytes that bulk tenants may not take, kept
+                                 for the latency tenant's workspace (0: none) */
 } fp8_server_config;
 
 typedef struct fp8_server fp8_server;

@@ -58,7 +58,8 @@ class FP8ServerConfig(ctypes.Structure):
     _fields_ = [("num_tenants", I32), ("latency_tenant", I32), ("batching", I32),
                 ("max_batch", I32), ("max_inflight", I32), ("bulk_max_ctas", I32),
                 ("pool_bytes", ctypes.c_size_t), ("reserve_bytes", ctypes.c_size_t),
-                ("latency_max_batch", I32), ("latency_max_ctas", I32)]
+                ("latency_max_batch", I32), ("latency_max_ctas", I32),
+                ("latency_pool_bytes", ctypes.c_size_t)]
 
 
 class FP8Request(ctypes.Structure):

@@ -560,6 +560,10 @@ struct fp8_server {
                 b.max_ctas = latency ? cfg.latency_max_ctas : cfg.bulk_max_ctas;
                 while (!queue[t].empty() && static_cast<int>(b.reqs.size()) < cap) {
                     Req* q = queue[t].front();
+                    // bulk tenants leave latency_pool_bytes of the pool to the
+                    // latency tenant, so a full pool never holds its requests
+                    if (!latency && pool.in_use() + q->ws_bytes + cfg.latency_pool_bytes > pool.capacity())
+                        break;
                     if (!pool.alloc(q->ws_bytes, &q->ws_off))
                         break;                      // FIFO: wait for space
                     b.reqs.push_back(q);
@@ -626,6 +630,8 @@ int normalise(const fp8_server_config* in, fp8_server_config* out)
         c.bulk_max_ctas = 0;
     if (c.latency_max_ctas < 0)
         c.latency_max_ctas = 0;
+    if (c.latency_tenant < 0)
+        c.latency_pool_bytes = 0;
     *out = c;
     return FP8_OK;
 }
@@ -761,7 +767,9 @@ extern "C" int fp8_server_submit(fp8_server* s, const fp8_request* r, uint64_t* 
         return FP8_ERR_INVALID;
     }
     q->ws_bytes = workspace_bytes(std::max<int64_t>(r->M, 1), q->w.K);
-    if (q->ws_bytes > s->pool.capacity()) {
+    const size_t limit = s->pool.capacity() - (r->tenant == s->cfg.latency_tenant
+                                                  ? 0 : std::min(s->cfg.latency_pool_bytes, s->pool.capacity()));
+    if (q->ws_bytes > limit) {
         ++s->stats.rejected;
         delete q;
         return FP8_ERR_OOM;

@@ -104,11 +104,11 @@ class Server:
     def __init__(self, num_tenants: int = 2, latency_tenant: int = 0, batching: bool = True,
                  max_batch: int = 0, max_inflight: int = 0, bulk_max_ctas: int = 0,
                  pool_bytes: int = 0, reserve_bytes: int = 0, latency_max_batch: int = 0,
-                 latency_max_ctas: int = 0, simulate=None):
+                 latency_max_ctas: int = 0, latency_pool_bytes: int = 0, simulate=None):
         self.lib = _lib.load()
         cfg = _lib.FP8ServerConfig(num_tenants, latency_tenant, int(bool(batching)), max_batch,
                                    max_inflight, bulk_max_ctas, pool_bytes, reserve_bytes,
-                                   latency_max_batch, latency_max_ctas)
+                                   latency_max_batch, latency_max_ctas, latency_pool_bytes)
         h = ctypes.c_void_p()
         if simulate is None:
             rc = self.lib.fp8_server_create(ctypes.byref(cfg), ctypes.byref(h))

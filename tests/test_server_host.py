@@ -81,6 +81,26 @@ def test_latency_tenant_is_not_held_to_the_inflight_limit():
             max(r.t_launch_us for r in rb) >= min(r.t_end_us for r in rb) - 1.0
 
 
+def test_latency_pool_share_keeps_the_latency_tenant_admitted():
+    # a 64 MiB pool with 16 MiB kept for the latency tenant: the bulk
+    # tenant's 8 MiB requests fill at most 48 MiB, so a latency request that
+    # arrives meanwhile is admitted at once instead of waiting for bulk work
+    with _server(num_tenants=2, latency_tenant=0, max_inflight=8, pool_bytes=64 << 20,
+                 latency_pool_bytes=16 << 20, simulate=(50000.0, 0.0, 0)) as s:
+        w = _weight(s)
+        bulk = [s.submit(1, w, 2048, FAKE, 4096, FAKE, 4096) for _ in range(10)]
+        time.sleep(0.005)
+        assert s.stats()["pool_in_use"] <= (48 << 20)
+        t = s.submit(0, w, 16, FAKE, 4096, FAKE, 4096)
+        r = s.wait(t, 5)
+        assert r.status == OK and r.t_launch_us - r.t_submit_us < 20000.0
+        assert all(s.wait(b, 5).status == OK for b in bulk)
+        # a bulk request larger than the pool minus the latency share is refused
+        with pytest.raises(ServerError) as e:
+            s.submit(1, w, 13000, FAKE, 4096, FAKE, 4096)
+        assert e.value.status == ERR_OOM
+
+
 def test_latency_batches_capped():
     with _server(num_tenants=2, latency_tenant=0, latency_max_batch=4, simulate=(20000.0, 0.0, 0)) as s:
         w = _weight(s)
