@@ -434,6 +434,10 @@ class ServingBench:
                     got = True
             return got
 
+        import gc
+        lag = np.zeros(len(reqs))
+        gc_was = gc.isenabled()
+        gc.disable()                 # a collector pause would bunch the Poisson arrivals
         try:
             times = None
             if rate is not None:
@@ -444,6 +448,7 @@ class ServingBench:
                     target = t0 + times[i]
                     while srv.now_us() < target:
                         collect(False)
+                    lag[i] = srv.now_us() - target
                 while not free or (rate is None and inflight >= window):
                     if not collect(False):
                         oldest = min((q for q in pend if q), key=lambda q: q[0][2])
@@ -463,6 +468,11 @@ class ServingBench:
             stats = srv.stats()
         finally:
             srv.close()
+            if gc_was:
+                gc.enable()
+        # how late the generator submitted (open loop: late submissions bunch up)
+        stats["submit_lag_us"] = {"p50": float(np.percentile(lag, 50)), "p99": float(np.percentile(lag, 99)),
+                                  "max": float(lag.max())}
         if any(x is None or x.status != 0 for x in res):
             raise RuntimeError("serving request failed")
         lat = np.array([x.t_end_us - x.t_submit_us for x in res])
@@ -540,6 +550,7 @@ def serving_report(gb, dev, n_cap=20000, n_load=20000, loads=(0.8,), n_iso=2000)
                 "mean_batch": float(np.mean([r.batch_size for r in res])),
                 "max_batch": int(stats["max_batch_seen"]),
                 "pool_high_water_mb": stats["pool_high_water"] / 2 ** 20,
+                "submit_lag_us": stats["submit_lag_us"],
                 "kernel_launches": stats["kernel_launches"],
             }
         if i == 0:
@@ -1155,7 +1166,8 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
                    "p50_us": {f"tenant{t}": float(np.percentile(lat[ten == t], 50)) for t in (0, 1)},
                    "p99_all_us": float(np.percentile(lat, 99)),
                    "pool_high_water_mb": stats["pool_high_water"] / 2 ** 20,
-                   "max_batch": int(stats["max_batch_seen"])}
+                   "max_batch": int(stats["max_batch_seen"]),
+                   "submit_lag_us": stats["submit_lag_us"]}
             if k == 0:
                 _, cspan, _, _ = sb.run(tr[:8000], cfg)
                 row["capacity_req_per_s"] = 8000 / (cspan * 1e-6)

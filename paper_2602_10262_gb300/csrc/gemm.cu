@@ -121,8 +121,13 @@ struct Cfg {
     static constexpr int kAcc = PAIR ? PAIR_TMEM_COLS / BN_MAX : (MT == 2 ? 1 : 2);   // accumulator buffers
     static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
     static constexpr int kEpiWarps = 4 * MT;
-    static constexpr int kEpiBytes = kEpiWarps * 32 * 128;       // 32 rows x 128 B per warp
-    static constexpr int kSmem = 1024 + kStages * kStageBytes + 256 + kEpiBytes;
+    // staging buffers of 32 rows x 128 B per epilogue warp: two where they
+    // fit, so a chunk is packed while the previous chunk's TMA store still
+    // reads its buffer
+    static constexpr int kSmemBase = 1024 + kStages * kStageBytes + 256;
+    static constexpr int kEpiBufs = kSmemBase + 2 * kEpiWarps * 32 * 128 <= 232448 ? 2 : 1;
+    static constexpr int kEpiBytes = kEpiBufs * kEpiWarps * 32 * 128;
+    static constexpr int kSmem = kSmemBase + kEpiBytes;
     static_assert(PAIR || kMetaCol0 + 4 * kStages * KC <= BN_MAX, "metadata ring must fit beside the accumulator");
     static_assert(KC * (kSpChunk + kMetaChunk) <= kABytes || (MT == 2 && !SP),
                   "sparse A + metadata fit the A region");
@@ -435,14 +440,17 @@ __device__ __forceinline__ void cluster_reduce_store(const ProblemScalars& P, co
 // buffer is written again.  A partial last chunk (bn not a multiple of the
 // chunk width) is copied out by the lanes, masked, so no store reaches the
 // next tile's columns.
-template <int ESZ, int LB>       // LB: 16-column TMEM loads in flight per wait (1 or 2)
+template <int ESZ, int LB, int NB>  // LB: 16-column TMEM loads in flight per wait (1 or 2); NB: staging buffers
 __device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P, uint32_t taddr, int row0,
-                                                        float fi, int jbase, uint8_t* buf, int lane,
+                                                        float fi, int jbase, uint8_t* bufs, int lane,
                                                         ScaleWindows& sw, const CUtensorMap* tmC)
 {
     constexpr int CW = 128 / ESZ;                     // columns per chunk
     const int rows_q = P.rows_q;
+    int nb = 0;                                       // staging buffer of this chunk
     for (int c0 = 0; c0 < P.bn; c0 += CW) {
+        uint8_t* buf = bufs + nb * (32 * 128);
+        nb = NB == 2 ? nb ^ 1 : 0;
         const int cw = min(CW, P.bn - c0);           // multiple of 16
         // column scales of the chunk: lane l holds columns c0 + l and c0 + 32 + l
         const float s_lo = sw.take(P, jbase, lane);
@@ -494,9 +502,13 @@ __device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P,
         const int nck = cw * ESZ / 16;                   // 16-byte pieces per row
         const bool via_tma = tmC != nullptr && cw == CW;
         if (tmC != nullptr) {
-            // the previous chunk's store must have read the buffer
-            if (lane == 0)
-                bulk_wait_read_all();
+            // the store that last used this buffer (NB chunks ago) must have read it
+            if (lane == 0) {
+                if (NB == 2)
+                    bulk_wait_read_1();
+                else
+                    bulk_wait_read_all();
+            }
             __syncwarp();
         }
         uint8_t* my_row = buf + lane * 128;
@@ -1021,14 +1033,16 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                 continue;
             }
             if (!P.trans_out && P.vec_store) {
-                uint8_t* buf = epi_smem + (warp - 2) * 32 * 128;
+                uint8_t* buf = epi_smem + (warp - 2) * C::kEpiBufs * 32 * 128;
                 const int row0 = i - lane;
                 const CUtensorMap* tmC = P.tma_store ? &prm.prob[tc.p].tmC : nullptr;
                 // (256-row tiles have the smaller register budget: one load per wait)
                 if (P.out_bf16)
-                    epilogue_rows_coalesced<2, MT == 1 ? 2 : 1>(P, taddr, row0, fi, jbase, buf, lane, sw, tmC);
+                    epilogue_rows_coalesced<2, MT == 1 ? 2 : 1, C::kEpiBufs>(P, taddr, row0, fi, jbase, buf, lane, sw,
+                                                                            tmC);
                 else
-                    epilogue_rows_coalesced<4, MT == 1 ? 2 : 1>(P, taddr, row0, fi, jbase, buf, lane, sw, tmC);
+                    epilogue_rows_coalesced<4, MT == 1 ? 2 : 1, C::kEpiBufs>(P, taddr, row0, fi, jbase, buf, lane, sw,
+                                                                            tmC);
             } else {
                 float s_cur = 0.0f;
                 for (int c0 = 0; c0 < P.bn; c0 += 16) {

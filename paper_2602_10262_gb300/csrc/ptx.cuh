@@ -216,6 +216,13 @@ __device__ __forceinline__ void bulk_wait_read_all()
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+// Wait until at most one of this thread's committed bulk stores (the most
+// recent) may still be reading its shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_1()
+{
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
 // Wait until this thread's committed bulk stores are complete.
 __device__ __forceinline__ void bulk_wait_all()
 {
