@@ -1111,6 +1111,24 @@ def pair_sweep(gb, dev):
     return {"gemms": rows, "layer": layer}
 
 
+def prune_sweep(gb, dev):
+    """prune24_compress alone: device time per call and HBM rate (1 byte
+    read + 0.625 bytes written per element), L2-cold rotation."""
+    rows = []
+    for M, K in ((4096, 4096), (8192, 8192), (16384, 16384), (512, 1024)):
+        n = _l2_copies(dev, M * K)
+        ops = []
+        for i in range(n):
+            A = torch.randint(0, 256, (M, K), dtype=torch.uint8, device=dev)
+            ops.append((A, torch.empty((M, K // 2), dtype=torch.uint8, device=dev),
+                        torch.empty((M, K // 8), dtype=torch.uint8, device=dev)))
+        fns = [lambda A=A, v=v, m=m: gb.prune24_compress(A, v, m) for A, v, m in ops]
+        ms = _time_ms(fns)
+        rows.append({"M": M, "K": K, "us": ms * 1e3, "gbs": M * K * 1.625 / ms / 1e6, "copies": n})
+        del ops, fns
+    return rows
+
+
 def raster_sweep(gb, dev):
     """Raster band height (M-blocks per band) of the tile walk for CTA-pair
     tiles (mt 3) and one-CTA 256-row tiles (mt 2) on large squares: device
@@ -1176,7 +1194,7 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
 
 
 SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency", "mx",
-                  "serving_policy", "served_concurrency", "pair", "raster")
+                  "serving_policy", "served_concurrency", "pair", "raster", "prune")
 
 
 def sweep(gb, dev, sections=SWEEP_SECTIONS):
@@ -1206,6 +1224,8 @@ def sweep(gb, dev, sections=SWEEP_SECTIONS):
         out["pair"] = pair_sweep(gb, dev)
     if "raster" in sections:
         out["raster"] = raster_sweep(gb, dev)
+    if "prune" in sections:
+        out["prune"] = prune_sweep(gb, dev)
     return out
 
 

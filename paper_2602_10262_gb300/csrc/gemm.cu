@@ -957,6 +957,11 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
             const bool row_ok = i < P.rows_p;
             const float fi = row_ok ? __fmul_rn(P.alpha, __ldg(P.sp + (P.sp_mode ? i : 0))) : 0.0f;
             const int jbase = tc.n_blk * P.bn;
+            // every column scale of the tile reaches L1 while its MMAs run:
+            // read window by window during the epilogue, each would
+            // otherwise wait a memory round trip (one line per 32 columns)
+            if (warp == 2 && P.sq_mode && lane < (P.bn + 31) / 32 && jbase + 32 * lane < P.rows_q)
+                prefetch_l1(P.sq + jbase + 32 * lane);
             ScaleWindows sw;
             sw.init(P, jbase, lane);
             // the whole warp takes the same branch (tcgen05.ld is warp-collective)

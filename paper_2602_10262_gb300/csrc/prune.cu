@@ -1,10 +1,11 @@
 // 2:4 prune + compress (prune24_compress) and its inverse.
 //
 // Vector path: a thread takes pieces of 16 input bytes (four groups of four
-// codes): one 16-byte load, a branch-free rank selection per group, an
-// 8-byte store of the kept codes and a 2-byte store of the four metadata
-// nibbles.  Rows whose length or alignment does not allow it fall back to one
-// metadata byte per iteration.  Bandwidth-bound: 1 byte read, 0.625 bytes written per
+// codes): one 16-byte load, a branch-free rank selection for two groups at
+// a time (packed 16-bit scores), an 8-byte store of the kept codes and a
+// 2-byte store of the four metadata nibbles.  Rows whose length or
+// alignment does not allow it fall back to one metadata byte per
+// iteration.  Bandwidth-bound: 1 byte read, 0.625 bytes written per
 // element; no allocation, one launch.
 #include "common.cuh"
 
@@ -33,6 +34,34 @@ __device__ __forceinline__ uint32_t select_group(uint32_t w)
     const uint32_t i1 = 3u - min(t1 & 3u, t2 & 3u);
     const uint32_t vals = __byte_perm(w, 0u, i0 | (i1 << 4)) & 0xFFFFu;
     return vals | ((i0 | (i1 << 2)) << 16);
+}
+
+// Two groups at once (group a = word wa, group b = word wb): the same scores
+// and tournament as select_group, with the scores of element j of both
+// groups side by side in the two 16-bit halves of a register, so one
+// packed max / min does the work of two.  Returns the kept codes of a in
+// bits 0-15 and of b in bits 16-31 of *vals, and the nibble of a in bits
+// 0-3 and of b in bits 4-7 of the result.
+__device__ __forceinline__ uint32_t select_group_pair(uint32_t wa, uint32_t wb, uint32_t* vals)
+{
+    // element j of a in bytes 0-1, of b in bytes 2-3; keep its key, * 4, | (3 - j)
+    const uint32_t s0 = ((__byte_perm(wa, wb, 0x4400u) << 2) & 0x01FC01FCu) | 0x00030003u;
+    const uint32_t s1 = ((__byte_perm(wa, wb, 0x5511u) << 2) & 0x01FC01FCu) | 0x00020002u;
+    const uint32_t s2 = ((__byte_perm(wa, wb, 0x6622u) << 2) & 0x01FC01FCu) | 0x00010001u;
+    const uint32_t s3 = (__byte_perm(wa, wb, 0x7733u) << 2) & 0x01FC01FCu;
+    const uint32_t a = __vmaxu2(s0, s1), b = __vminu2(s0, s1);
+    const uint32_t c = __vmaxu2(s2, s3), d = __vminu2(s2, s3);
+    const uint32_t t1 = __vmaxu2(a, c);
+    const uint32_t t2 = __vmaxu2(__vminu2(a, c), __vmaxu2(b, d));
+    const uint32_t x1 = t1 & 0x00030003u, x2 = t2 & 0x00030003u;
+    const uint32_t i0 = __vmaxu2(x1, x2) ^ 0x00030003u;       // 3 - (larger low bits)
+    const uint32_t i1 = __vminu2(x1, x2) ^ 0x00030003u;
+    const uint32_t sel = i0 | (i1 << 4);                       // byte selectors, per half
+    const uint32_t va = __byte_perm(wa, 0u, sel & 0xFFFFu);
+    const uint32_t vb = __byte_perm(wb, 0u, sel >> 16);
+    *vals = __byte_perm(va, vb, 0x5410u);
+    const uint32_t nib = i0 | (i1 << 2);
+    return (nib & 0xFu) | ((nib >> 12) & 0xF0u);
 }
 
 // Vector path: K % 16 == 0, a 16-aligned with lda % 16 == 0, vals 8-aligned,
@@ -65,10 +94,11 @@ __global__ void __launch_bounds__(kThreads) prune24_vec_kernel(const uint8_t* __
             const int p = p_first + u * kThreads;
             if (p >= pieces)
                 continue;
-            const uint32_t s0 = select_group(x[u].x), s1 = select_group(x[u].y);
-            const uint32_t s2 = select_group(x[u].z), s3 = select_group(x[u].w);
-            const uint2 v = make_uint2((s0 & 0xFFFFu) | (s1 << 16), (s2 & 0xFFFFu) | (s3 << 16));
-            const uint32_t nib = (s0 >> 16) | ((s1 >> 16) << 4) | ((s2 >> 16) << 8) | ((s3 >> 16) << 12);
+            uint32_t v01, v23;
+            const uint32_t n01 = select_group_pair(x[u].x, x[u].y, &v01);
+            const uint32_t n23 = select_group_pair(x[u].z, x[u].w, &v23);
+            const uint2 v = make_uint2(v01, v23);
+            const uint32_t nib = n01 | (n23 << 8);
             *reinterpret_cast<uint2*>(vals + r * ldv + p * 8) = v;
             *reinterpret_cast<uint16_t*>(meta + r * ldm + p * 2) = static_cast<uint16_t>(nib);
         }
