@@ -119,8 +119,12 @@ struct Cfg {
     static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : (BNC == 256 ? SPARSE_BN_MAX : BNC);
     static constexpr int kTmemCols = PAIR ? PAIR_TMEM_COLS : TMEM_COLS;
     static constexpr int kAcc = PAIR ? PAIR_TMEM_COLS / BN_MAX : (MT == 2 ? 1 : 2);   // accumulator buffers
-    static constexpr int kThreads = 64 + 128 * MT;               // producer, MMA, epilogue warps
-    static constexpr int kEpiWarps = 4 * MT;
+    // epilogue warps: 4 per 128 rows (one per TMEM lane quarter); 256-wide
+    // 128-row tiles (and pairs) use 8, two per lane quarter splitting the
+    // columns, so each SM sub-partition has a second warp to hide latencies
+    static constexpr int kEpiSplit = (MT == 1 && BNC == BN_MAX && !MX) ? 2 : 1;
+    static constexpr int kEpiWarps = 4 * MT * kEpiSplit;
+    static constexpr int kThreads = 64 + 32 * kEpiWarps;         // producer, MMA, epilogue warps
     // staging buffers of 32 rows x 128 B per epilogue warp: two where they
     // fit, so a chunk is packed while the previous chunk's TMA store still
     // reads its buffer
@@ -234,17 +238,19 @@ __device__ __forceinline__ void abort_pipeline(volatile int* flag, int* err)
 // add their latency to the epilogue.
 struct ScaleWindows {
     float w0, w1;           // the next two windows to hand out
-    int next;               // tile column of the window after w1
+    int next;               // column (from the first) of the window after w1
+    int width;              // columns this warp covers
 
     __device__ __forceinline__ static float load(const ProblemScalars& P, int j, int lane)
     {
         j += lane;
         return j < P.rows_q ? __ldg(P.sq + (P.sq_mode ? j : 0)) : 0.0f;
     }
-    __device__ __forceinline__ void init(const ProblemScalars& P, int jbase, int lane)
+    __device__ __forceinline__ void init(const ProblemScalars& P, int jbase, int lane, int cols)
     {
+        width = cols;
         w0 = load(P, jbase, lane);
-        w1 = P.bn > 32 ? load(P, jbase + 32, lane) : 0.0f;
+        w1 = cols > 32 ? load(P, jbase + 32, lane) : 0.0f;
         next = 64;
     }
     // The window at tile columns 32 k .. 32 k + 31 for k = 0, 1, 2, ... in turn.
@@ -252,7 +258,7 @@ struct ScaleWindows {
     {
         const float s = w0;
         w0 = w1;
-        w1 = next < P.bn ? load(P, jbase + next, lane) : 0.0f;
+        w1 = next < width ? load(P, jbase + next, lane) : 0.0f;
         next += 32;
         return s;
     }
@@ -338,10 +344,11 @@ __device__ __forceinline__ void store_chunk16(const ProblemScalars& P, int i, bo
 // lanes of a warp, which own 32 consecutive rows, store 128 contiguous bytes
 // per column.
 __device__ __forceinline__ void split_write_partial(const ProblemScalars& P, float* ws, int rows_per_tile,
-                                                    int tile, int slice, int row, uint32_t taddr)
+                                                    int tile, int slice, int row, uint32_t taddr, int c_lo,
+                                                    int c_hi)
 {
     float* dst = ws + P.ws_off + (static_cast<long long>(tile) * P.splits + slice) * rows_per_tile * P.bn + row;
-    for (int c0 = 0; c0 < P.bn; c0 += 16) {
+    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
         uint32_t r[16];
         tmem_ld_32x32b_x16(taddr + c0, r);
         tmem_ld_wait();
@@ -355,14 +362,14 @@ __device__ __forceinline__ void split_write_partial(const ProblemScalars& P, flo
 // slice in slice order and store the scaled result.
 __device__ __forceinline__ void split_reduce_store(const ProblemScalars& P, const float* ws, int rows_per_tile,
                                                    int tile, int row, int i, bool row_ok, float fi, int jbase,
-                                                   ScaleWindows& sw, int lane)
+                                                   ScaleWindows& sw, int lane, int c_lo, int c_hi)
 {
     const float* src = ws + P.ws_off + static_cast<long long>(tile) * P.splits * rows_per_tile * P.bn + row;
     const long long slot = static_cast<long long>(rows_per_tile) * P.bn;
     float s_cur = 0.0f;
-    for (int c0 = 0; c0 < P.bn; c0 += 16) {
+    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
         if ((c0 & 31) == 0)
-            s_cur = sw.take(P, jbase, lane);
+            s_cur = sw.take(P, jbase + c_lo, lane);
         float acc[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t)
@@ -383,10 +390,11 @@ __device__ __forceinline__ void split_reduce_store(const ProblemScalars& P, cons
 // (element (row, col) of slice r at ((r - 1) * bn + col) * rows_per_tile +
 // row floats from the ring's start).
 __device__ __forceinline__ void cluster_send_partial(const ProblemScalars& P, uint32_t leader_ring,
-                                                     int rows_per_tile, int slice, int row, uint32_t taddr)
+                                                     int rows_per_tile, int slice, int row, uint32_t taddr,
+                                                     int c_lo, int c_hi)
 {
     const uint32_t base = leader_ring + 4u * static_cast<uint32_t>((slice - 1) * P.bn * rows_per_tile + row);
-    for (int c0 = 0; c0 < P.bn; c0 += 16) {
+    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
         uint32_t r[16];
         tmem_ld_32x32b_x16(taddr + c0, r);
         tmem_ld_wait();
@@ -402,13 +410,13 @@ __device__ __forceinline__ void cluster_send_partial(const ProblemScalars& P, ui
 __device__ __forceinline__ void cluster_reduce_store(const ProblemScalars& P, const uint8_t* ring,
                                                      int rows_per_tile, int row, uint32_t taddr, int i,
                                                      bool row_ok, float fi, int jbase, ScaleWindows& sw,
-                                                     int lane)
+                                                     int lane, int c_lo, int c_hi)
 {
     const float* recv = reinterpret_cast<const float*>(ring) + row;
     float s_cur = 0.0f;
-    for (int c0 = 0; c0 < P.bn; c0 += 16) {
+    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
         if ((c0 & 31) == 0)
-            s_cur = sw.take(P, jbase, lane);
+            s_cur = sw.take(P, jbase + c_lo, lane);
         uint32_t r[16];
         tmem_ld_32x32b_x16(taddr + c0, r);
         tmem_ld_wait();
@@ -443,18 +451,19 @@ __device__ __forceinline__ void cluster_reduce_store(const ProblemScalars& P, co
 template <int ESZ, int LB, int NB>  // LB: 16-column TMEM loads in flight per wait (1 or 2); NB: staging buffers
 __device__ __forceinline__ void epilogue_rows_coalesced(const ProblemScalars& P, uint32_t taddr, int row0,
                                                         float fi, int jbase, uint8_t* bufs, int lane,
-                                                        ScaleWindows& sw, const CUtensorMap* tmC)
+                                                        ScaleWindows& sw, const CUtensorMap* tmC, int c_lo,
+                                                        int c_hi)
 {
     constexpr int CW = 128 / ESZ;                     // columns per chunk
     const int rows_q = P.rows_q;
     int nb = 0;                                       // staging buffer of this chunk
-    for (int c0 = 0; c0 < P.bn; c0 += CW) {
+    for (int c0 = c_lo; c0 < c_hi; c0 += CW) {
         uint8_t* buf = bufs + nb * (32 * 128);
         nb = NB == 2 ? nb ^ 1 : 0;
-        const int cw = min(CW, P.bn - c0);           // multiple of 16
+        const int cw = min(CW, c_hi - c0);           // multiple of 16
         // column scales of the chunk: lane l holds columns c0 + l and c0 + 32 + l
-        const float s_lo = sw.take(P, jbase, lane);
-        const float s_hi = (CW > 32 && c0 + 32 < P.bn) ? sw.take(P, jbase, lane) : 0.0f;
+        const float s_lo = sw.take(P, jbase + c_lo, lane);
+        const float s_hi = (CW > 32 && c0 + 32 < c_hi) ? sw.take(P, jbase + c_lo, lane) : 0.0f;
         uint32_t packed[32];
         // scale + convert 16 columns starting at column c of the chunk
         auto convert16 = [&](const uint32_t (&r)[16], int q) {
@@ -614,12 +623,12 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
         for (int b = 0; b < C::kAcc; ++b) {
             mbar_init(tfull_bar(b), 1);
             // pairs: the even CTA's barrier counts both CTAs' epilogue threads
-            mbar_init(tempty_bar(b), PAIR ? 2 * 128 : 128 * MT);
+            mbar_init(tempty_bar(b), (PAIR ? 2 : 1) * 32 * C::kEpiWarps);
         }
         mbar_init(drain_bar, 1);
         // cluster split-K: "written" counts the other slices' epilogue
         // threads, "verdict" is the rank-0 CTA's "ring free" signal
-        mbar_init(split_written_bar, cluster_split ? (cluster_split - 1) * 128 * MT : 128 * MT);
+        mbar_init(split_written_bar, cluster_split ? (cluster_split - 1) * 32 * C::kEpiWarps : 32 * C::kEpiWarps);
         mbar_init(split_verdict_bar, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -940,9 +949,12 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
         }
     } else {
         // ---------------------------------------------------- epilogue
-        // warp w reads TMEM lanes 32 (w % 4) .. of half (w - 2) / 4
+        // warp w reads TMEM lanes 32 (w % 4) ..; with 256-row tiles of half
+        // (w - 2) / 4, with two warps per lane quarter of columns [0, mid) or
+        // [mid, bn) (mid: half the tile rounded up to 64 columns)
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int half = MT == 2 ? (warp - 2) >> 2 : 0;
+        const int cpart = C::kEpiSplit == 2 ? (warp - 2) >> 2 : 0;
         const int row = half * BM + quarter * 32 + lane;
         int local = 0;
         uint32_t split_phase = 0;
@@ -962,8 +974,14 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
             // otherwise wait a memory round trip (one line per 32 columns)
             if (warp == 2 && P.sq_mode && lane < (P.bn + 31) / 32 && jbase + 32 * lane < P.rows_q)
                 prefetch_l1(P.sq + jbase + 32 * lane);
+            int c_lo = 0, c_hi = P.bn;
+            if (C::kEpiSplit == 2) {
+                const int mid = min(P.bn, (P.bn / 2 + 63) & ~63);
+                c_lo = cpart ? mid : 0;
+                c_hi = cpart ? P.bn : mid;
+            }
             ScaleWindows sw;
-            sw.init(P, jbase, lane);
+            sw.init(P, jbase + c_lo, lane, c_hi - c_lo);
             // the whole warp takes the same branch (tcgen05.ld is warp-collective)
             const bool got = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, wlim);
             if (!__all_sync(0xFFFFFFFFu, got)) {
@@ -989,14 +1007,14 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                         abort_pipeline(abort_flag, err);
                         break;
                     }
-                    cluster_reduce_store(P, smem, BM * MT, row, taddr, i, row_ok, fi, jbase, sw, lane);
+                    cluster_reduce_store(P, smem, BM * MT, row, taddr, i, row_ok, fi, jbase, sw, lane, c_lo, c_hi);
                 } else {
                     const bool got = mbar_wait_cluster(split_verdict_bar, 0u, abort_flag, wlim);
                     if (!__all_sync(0xFFFFFFFFu, got)) {
                         abort_pipeline(abort_flag, err);
                         break;
                     }
-                    cluster_send_partial(P, cluster_map(smem_base, 0u), BM * MT, crank, row, taddr);
+                    cluster_send_partial(P, cluster_map(smem_base, 0u), BM * MT, crank, row, taddr, c_lo, c_hi);
                     mbar_arrive_remote(cluster_map(split_written_bar, 0u));
                 }
                 tc_fence_before();
@@ -1008,7 +1026,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                 // thread counts this unit in; the tile's last unit reduces.
                 // (The verdict slot is rewritten only after every thread has
                 // arrived for the next split tile, i.e. after it was read.)
-                split_write_partial(P, ws, BM * MT, tc.tile, tc.slice, row, taddr);
+                split_write_partial(P, ws, BM * MT, tc.tile, tc.slice, row, taddr, c_lo, c_hi);
                 tc_fence_before();
                 mbar_arrive(tempty_bar(acc));          // TMEM is free; the reduction reads global memory
                 __threadfence();
@@ -1031,7 +1049,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                 }
                 if (*split_flag) {
                     __threadfence();
-                    split_reduce_store(P, ws, BM * MT, tc.tile, row, i, row_ok, fi, jbase, sw, lane);
+                    split_reduce_store(P, ws, BM * MT, tc.tile, row, i, row_ok, fi, jbase, sw, lane, c_lo, c_hi);
                     if (threadIdx.x == 64)
                         ctr[P.ctr_off + tc.tile] = 0u;         // ready for the next launch
                 }
@@ -1041,18 +1059,20 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                 uint8_t* buf = epi_smem + (warp - 2) * C::kEpiBufs * 32 * 128;
                 const int row0 = i - lane;
                 const CUtensorMap* tmC = P.tma_store ? &prm.prob[tc.p].tmC : nullptr;
-                // (256-row tiles have the smaller register budget: one load per wait)
+                // (kernels with 8 epilogue warps have the smaller register
+                // budget: one load per wait)
+                constexpr int LB = C::kEpiWarps == 4 ? 2 : 1;
                 if (P.out_bf16)
-                    epilogue_rows_coalesced<2, MT == 1 ? 2 : 1, C::kEpiBufs>(P, taddr, row0, fi, jbase, buf, lane, sw,
-                                                                            tmC);
+                    epilogue_rows_coalesced<2, LB, C::kEpiBufs>(P, taddr, row0, fi, jbase, buf, lane, sw, tmC, c_lo,
+                                                               c_hi);
                 else
-                    epilogue_rows_coalesced<4, MT == 1 ? 2 : 1, C::kEpiBufs>(P, taddr, row0, fi, jbase, buf, lane, sw,
-                                                                            tmC);
+                    epilogue_rows_coalesced<4, LB, C::kEpiBufs>(P, taddr, row0, fi, jbase, buf, lane, sw, tmC, c_lo,
+                                                               c_hi);
             } else {
                 float s_cur = 0.0f;
-                for (int c0 = 0; c0 < P.bn; c0 += 16) {
+                for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
                     if ((c0 & 31) == 0)
-                        s_cur = sw.take(P, jbase, lane);
+                        s_cur = sw.take(P, jbase + c_lo, lane);
                     uint32_t r[16];
                     tmem_ld_32x32b_x16(taddr + c0, r);
                     tmem_ld_wait();
@@ -1390,6 +1410,7 @@ struct Plan {
     int cluster = 0;            // > 1: launched as clusters of this many CTAs (split-K in the
                                 // cluster, or 2: CTA pairs)
     int kc = 1;                 // k-blocks per pipeline stage
+    int rows_per_tile = BM;     // P rows of a CTA's tile (128 or 256)
     size_t ring_bytes = 0;      // bytes of the kernel's TMA ring
     size_t ws_floats = 0;       // split-K partials
     size_t ctr_count = 0;       // split-K tile counters
@@ -1472,6 +1493,7 @@ int plan(Params<MAXP>& prm, int max_ctas, Plan* out)
     }
     out->cluster = PAIR ? 2 : 0;
     out->kc = KC;
+    out->rows_per_tile = BM * MT;
     out->func = reinterpret_cast<const void*>(gemm_fp8_kernel<MAXP, MT, SP, BNC, KC, MX, PAIR>);
     out->ring_bytes = static_cast<size_t>(C::kStages) * C::kStageBytes;
     out->grid = grid;
@@ -1759,7 +1781,7 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
         return rc;
     const ProblemScalars& P = prm.prob[0];
     const int s = P.splits;
-    const size_t rows_per_tile = static_cast<size_t>(pl->threads - 64);        // BM * MT
+    const size_t rows_per_tile = static_cast<size_t>(pl->rows_per_tile);
     if (s < 2 || s > 8 || pl->grid != prm.total_tiles || prm.total_tiles % s != 0 ||
         static_cast<size_t>(s - 1) * P.bn * rows_per_tile * sizeof(float) > pl->ring_bytes ||
         !clusters_fit(*pl, s, prm.total_tiles / s))
@@ -2082,7 +2104,7 @@ extern "C" int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtyp
     if (rc != FP8_OK)
         return rc;
     const ProblemScalars& P = prm.prob[0];
-    info->mt = pl.cluster == 2 && !prm.cluster_split ? 3 : (pl.threads - 64) / 128;
+    info->mt = pl.cluster == 2 && !prm.cluster_split ? 3 : pl.rows_per_tile / BM;
     info->bn = P.bn;
     info->k_blocks_per_stage = pl.kc;
     info->splits = P.splits;
