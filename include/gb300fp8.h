@@ -338,8 +338,11 @@ int gemm_fp8_sparse24_fmt(int64_t M, int64_t N, int64_t K, const uint8_t *a_vals
  * Each problem is a dense (A_meta == NULL) or 2:4-sparse (A = a_vals,
  * A_meta = a_meta) GEMM with the conventions above; out_transposed as in
  * gemm_fp8_sparse24 (dense problems may use it too).  The problem table is
- * passed by value in the kernel parameters (no device workspace); at most
- * FP8_GROUPED_MAX_PROBLEMS problems per call (FP8_ERR_SHAPE otherwise).
+ * passed by value in the kernel parameters (no device workspace), so one
+ * launch holds at most FP8_GROUPED_MAX_PROBLEMS problems; a longer list is
+ * checked as a whole and then run as consecutive launches of up to that
+ * many problems each, in list order, on `stream` (the autotuner and the
+ * CUDA-graph form take at most FP8_GROUPED_MAX_PROBLEMS: FP8_ERR_SHAPE).
  * Results are bitwise identical to issuing each problem alone.
  * ------------------------------------------------------------------------- */
 #define FP8_GROUPED_MAX_PROBLEMS 32

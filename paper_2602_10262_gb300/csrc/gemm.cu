@@ -2290,7 +2290,7 @@ namespace {
 // Validate a problem list and turn it into jobs.  K == 0 problems are written
 // as zeros on `st` (when `zeros_ok`) or rejected.  *n_out: jobs produced.
 int grouped_jobs(const fp8_gemm_problem* problems, int num_problems, cudaStream_t st,
-                 bool zeros_ok, Job* jobs, int* bns, int* n_out)
+                 bool zeros_ok, Job* jobs, int* bns, int* n_out, bool check_only = false)
 {
     *n_out = 0;
     if (num_problems < 0 || (num_problems > 0 && !problems))
@@ -2312,7 +2312,7 @@ int grouped_jobs(const fp8_gemm_problem* problems, int num_problems, cudaStream_
             return FP8_ERR_SHAPE;
         any_sparse |= sp && g.M > 0 && g.N > 0 && g.K > 0;
     }
-    if (num_problems == 0)
+    if (num_problems == 0 || check_only)
         return FP8_OK;
     if (!device_supported())
         return FP8_ERR_UNSUPPORTED;
@@ -2350,6 +2350,26 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
 {
     using namespace gb300;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (num_problems > FP8_GROUPED_MAX_PROBLEMS && problems) {
+        // longer lists: every problem checked first (nothing is launched for
+        // a bad list), then consecutive launches of up to
+        // FP8_GROUPED_MAX_PROBLEMS problems each, in list order
+        Job unused[FP8_GROUPED_MAX_PROBLEMS];
+        int ub[FP8_GROUPED_MAX_PROBLEMS], un = 0;
+        for (int b = 0; b < num_problems; b += FP8_GROUPED_MAX_PROBLEMS) {
+            const int rc = grouped_jobs(problems + b, std::min(FP8_GROUPED_MAX_PROBLEMS, num_problems - b), st, true,
+                                        unused, ub, &un, true);
+            if (rc != FP8_OK)
+                return rc;
+        }
+        for (int b = 0; b < num_problems; b += FP8_GROUPED_MAX_PROBLEMS) {
+            const int rc = gemm_fp8_grouped_ex(problems + b, std::min(FP8_GROUPED_MAX_PROBLEMS, num_problems - b),
+                                               max_ctas, stream);
+            if (rc != FP8_OK)
+                return rc;
+        }
+        return FP8_OK;
+    }
     Job jobs[FP8_GROUPED_MAX_PROBLEMS];
     int bns[FP8_GROUPED_MAX_PROBLEMS];
     int n = 0;

@@ -121,12 +121,18 @@ def test_grouped_rejects_bad_format(lib):
     assert lib.gemm_fp8_grouped(good, 1, None) == -8
 
 
-def test_grouped_rejects_too_many(lib):
+def test_grouped_long_lists(lib):
     from paper_2602_10262_gb300 import _lib
-    arr = (_lib.FP8Problem * 33)()
-    assert lib.gemm_fp8_grouped(arr, 33, None) == -2
+    # more than 32 problems: the whole list is checked before any launch
+    arr = (_lib.FP8Problem * 70)()
+    assert lib.gemm_fp8_grouped(arr, 70, None) in (0, -8)      # empty problems; -8 without a GPU
+    arr[65].a_mode = 7
+    assert lib.gemm_fp8_grouped(arr, 70, None) == -1
     assert lib.gemm_fp8_grouped(None, 1, None) == -1
     assert lib.gemm_fp8_grouped(None, 0, None) in (0, -8)
+    # the autotuner and graphs keep the one-launch limit
+    best = _lib.FP8TileConfig()
+    assert lib.gemm_fp8_grouped_autotune((_lib.FP8Problem * 33)(), 33, 0, 1, None, ctypes.byref(best)) == -2
 
 
 def test_tune_cache_file_round_trip(lib, tmp_path):

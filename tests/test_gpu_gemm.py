@@ -350,3 +350,24 @@ def test_extreme_shapes_small_integers_exact(gb, orc, M, N, K):
     assert np.array_equal(C.astype(np.float64), exact)
     ms, ns = workloads.sample_pairs(M, N, 256, seed=9)
     assert np.array_equal(C[ms, ns].astype(np.float64), orc.gemm_sampled(A, B, one, 0, one, 0, 1.0, ms, ns))
+
+
+def test_grouped_long_list_equals_single_calls(gb, orc):
+    """70 problems (more than one launch holds) give the bits of 70 single calls."""
+    rng = np.random.default_rng(5)
+    probs, outs, refs, keep = [], [], [], []
+    for i in range(70):
+        M, N, K = (int(v) for v in rng.integers(1, 9, 3) * 64)
+        A, dA = orc.quantize(workloads.randn_f32((M, K), seed=2000 + i), 1)
+        B, dB = orc.quantize(workloads.randn_f32((N, K), seed=3000 + i), 1)
+        t = [_cuda(v) for v in (A, B, dA, dB)]
+        C = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+        keep += t
+        outs.append(C)
+        probs.append(gb.make_problem(t[0], t[1], t[2], 1, t[3], 1, C, 1.0, gb.OUT_BF16))
+        refs.append(gb.gemm_fp8_dense(t[0], t[1], t[2], 1, t[3], 1, 1.0, gb.OUT_BF16))
+    gb.gemm_fp8_grouped(probs)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    for a, b in zip(outs, refs):
+        assert torch.equal(a, b)
