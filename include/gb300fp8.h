@@ -391,7 +391,8 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * the SMs: 3 when the problems are dense with 256-wide N tiles, else 2; a
  * launch mixing dense and sparse problems always uses 1; CUDA-graph
  * launches (gemm_fp8_grouped_graph_*) use 2 in place of 3).
- * group_m: M-blocks per raster band (0 = 16).  Results do not depend on
+ * group_m: M-blocks per raster band (0 = 16, or 8 for CTA-pair launches
+ * whose operands exceed the L2 cache).  Results do not depend on
  * either.  Affects launches enqueued after the call, from any thread. */
 int fp8_gemm_set_tile_config(int mt, int group_m);
 
@@ -406,6 +407,7 @@ typedef struct {
     int cluster;            /* CTAs per thread-block cluster (0: no clusters) */
     int grid;               /* CTAs launched */
     int swapped;            /* 1: run as C^T = B A^T (small M on the MMA N side) */
+    int group_m;            /* raster band height in tiles (fp8_gemm_set_tile_config) */
     size_t workspace_bytes; /* split-K scratch the launch needs (0: none) */
 } fp8_gemm_plan_info;
 

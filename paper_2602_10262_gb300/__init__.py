@@ -114,8 +114,8 @@ def fp8_test_stall_gemm_loads(launches: int, wait_limit_ms: float = 0.0) -> None
 
 def gemm_fp8_dense_plan(M: int, N: int, K: int, out_dtype: int = OUT_BF16) -> dict:
     """How gemm_fp8_dense would run [M, K] x [N, K]^T now (tile kind, N width,
-    k-blocks per stage, K slices, cluster size, grid, operand swap, split-K
-    scratch bytes), without launching."""
+    k-blocks per stage, K slices, cluster size, grid, operand swap, raster
+    band, split-K scratch bytes), without launching."""
     info = _lib.FP8PlanInfo()
     _check(library().gemm_fp8_dense_plan(int(M), int(N), int(K), int(out_dtype), ctypes.byref(info)),
            "gemm_fp8_dense_plan")

@@ -50,7 +50,7 @@ class FP8TileConfig(ctypes.Structure):
 class FP8PlanInfo(ctypes.Structure):
     """Mirror of ``fp8_gemm_plan_info``."""
     _fields_ = [("mt", I32), ("bn", I32), ("k_blocks_per_stage", I32), ("splits", I32), ("cluster", I32),
-                ("grid", I32), ("swapped", I32), ("workspace_bytes", ctypes.c_size_t)]
+                ("grid", I32), ("swapped", I32), ("group_m", I32), ("workspace_bytes", ctypes.c_size_t)]
 
 
 class FP8ServerConfig(ctypes.Structure):

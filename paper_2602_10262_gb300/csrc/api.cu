@@ -16,6 +16,7 @@ struct DeviceInfo {
     int* err = nullptr;
     float* one = nullptr;
     int sms = 0;
+    int l2_bytes = 0;
     int major = 0, minor = 0;
 };
 DeviceInfo g_dev[kMaxDevices];
@@ -33,6 +34,7 @@ DeviceInfo* info()
         if (cudaGetSymbolAddress(&p, g_one) == cudaSuccess)
             d->one = static_cast<float*>(p);
         cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&d->l2_bytes, cudaDevAttrL2CacheSize, dev);
         cudaDeviceGetAttribute(&d->major, cudaDevAttrComputeCapabilityMajor, dev);
         cudaDeviceGetAttribute(&d->minor, cudaDevAttrComputeCapabilityMinor, dev);
     });
@@ -56,6 +58,12 @@ int sm_count()
 {
     DeviceInfo* d = info();
     return d ? d->sms : 0;
+}
+
+long long l2_bytes()
+{
+    DeviceInfo* d = info();
+    return d ? d->l2_bytes : 0;
 }
 
 bool device_supported()

@@ -29,6 +29,9 @@ const float* device_one();
 // SM count of the current device (cached per device).
 int sm_count();
 
+// L2 capacity of the current device in bytes (0 if unknown).
+long long l2_bytes();
+
 // True when the current device is an sm_103 part this library was built for.
 bool device_supported();
 

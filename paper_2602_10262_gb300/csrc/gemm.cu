@@ -46,6 +46,7 @@ constexpr int BK = 128;                   // codes per k-block (one 128-byte swi
 constexpr int BN_MAX = 256;
 constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M_DEFAULT = 16;       // raster: M-blocks per band
+constexpr int GROUP_M_PAIR_LARGE = 8;     // CTA-pair launches whose operands exceed L2
 // 2:4-sparse tiles: per stage the kept A codes (rows x 64 bytes, 64-byte
 // swizzle) and the metadata (rows x 16 bytes) fill the A region; the metadata
 // of each 128-row half is copied into a ring of TMEM columns beside that
@@ -1677,8 +1678,20 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
     }
     if (mixed_kinds(jobs, n) || (n > 0 && jobs[0].sfp != nullptr))
         c.mt = 1;
-    if (c.group_m <= 0)
-        c.group_m = GROUP_M_DEFAULT;
+    if (c.group_m <= 0) {
+        // Each wave of concurrent tiles re-reads its band's P rows and its Q
+        // columns from HBM once operands exceed L2 (the band is gone from L2
+        // by the time the raster returns to it), so the traffic per wave
+        // grows with band + tiles per wave / band, least near the square
+        // root of the tiles per wave.  Pairs run half as many tiles at once
+        // as one-CTA tiles: measured at 16384^3, 8-row bands read 4.09 GB
+        // from HBM per launch against 4.95 GB for 16-row ones, in the same
+        // time (one-CTA 256-row tiles: 3.13 GB at 16, 3.25 at 8).
+        bool beyond_l2 = false;
+        for (int i = 0; i < n; ++i)
+            beyond_l2 = beyond_l2 || (jobs[i].rows_p + jobs[i].rows_q) * jobs[i].K > l2_bytes();
+        c.group_m = c.mt == 3 && beyond_l2 ? GROUP_M_PAIR_LARGE : GROUP_M_DEFAULT;
+    }
     return c;
 }
 
@@ -2111,6 +2124,7 @@ extern "C" int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtyp
     info->cluster = pl.cluster > 1 ? pl.cluster : 0;
     info->grid = pl.grid;
     info->swapped = M <= 128 && N > M ? 1 : 0;          // make_job's rule for dense products
+    info->group_m = prm.group_m;
     info->workspace_bytes = workspace_bytes(pl);
     return FP8_OK;
 }

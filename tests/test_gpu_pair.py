@@ -123,3 +123,20 @@ def test_pair_stalled_launch_times_out(gb, pair):
     gb.gemm_fp8_dense(At, Bt, _ones(1), 0, _ones(1), 0, 1.0, gb.OUT_F32, C=C)
     assert gb.fp8_last_device_error() == 0
     assert torch.equal(C, ref)
+
+
+def test_pair_raster_band(gb):
+    """CTA-pair launches whose operands exceed L2 walk 8-row raster bands
+    (fewer HBM re-reads per wave of 76 tiles), others 16; a forced band
+    stands."""
+    gb.fp8_gemm_set_tile_config(0, 0)
+    big = gb.gemm_fp8_dense_plan(16384, 16384, 16384)
+    assert big["mt"] == 3 and big["group_m"] == 8
+    mid = gb.gemm_fp8_dense_plan(4096, 4096, 4096)
+    assert mid["mt"] == 3 and mid["group_m"] == 16
+    assert gb.gemm_fp8_dense_plan(1024, 1024, 1024)["group_m"] == 16
+    gb.fp8_gemm_set_tile_config(3, 4)
+    try:
+        assert gb.gemm_fp8_dense_plan(16384, 16384, 16384)["group_m"] == 4
+    finally:
+        gb.fp8_gemm_set_tile_config(0, 0)
