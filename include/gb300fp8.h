@@ -388,9 +388,9 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * its half of the accumulator; dense launches whose N tiles are 256 wide,
  * otherwise as 0), 0 = chosen per launch (256-row tiles when every problem
  * fills them with N tiles >= 128 wide and those tiles number at least half
- * the SMs: 3 when the problems are dense with 256-wide N tiles, else 2; a
- * launch mixing dense and sparse problems always uses 1; CUDA-graph
- * launches (gemm_fp8_grouped_graph_*) use 2 in place of 3).
+ * the SMs, or, for CTA pairs with K >= 4096, occupy as many SMs as 128-row
+ * tiles would: 3 when the problems are dense with 256-wide N tiles, else 2;
+ * a launch mixing dense and sparse problems always uses 1).
  * group_m: M-blocks per raster band (0 = 16, or 8 for CTA-pair launches
  * whose operands exceed the L2 cache).  Results do not depend on
  * either.  Affects launches enqueued after the call, from any thread. */

@@ -593,6 +593,15 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     grid_launch_dependents();
+    // a launch whose cluster shape does not match its plan (pairs need
+    // clusters of two, cluster split-K one CTA per slice) does nothing: no
+    // CTA addresses a peer that is not there
+    if ((PAIR ? 2u : (prm.cluster_split > 0 ? static_cast<uint32_t>(prm.cluster_split) : 1u)) !=
+        cluster_nctarank()) {
+        if (threadIdx.x == 0)
+            report_device_error(prm.err, FP8_ERR_UNSUPPORTED);
+        return;
+    }
     // Loop-invariant parameters, the first tile's coordinates and problem
     // scalars are read into registers before the setup below, so their
     // parameter loads overlap it (indexed parameter reads are memory loads,
@@ -1662,18 +1671,27 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
         if (c.mt == 3 && !pair_ok)
             c.mt = 0;
         if (c.mt == 0) {
-            int64_t tiles2 = 0;
-            bool ok2 = true;
+            int64_t tiles1 = 0, tiles2 = 0;
+            bool ok2 = true, long_k = n > 0;
             for (int i = 0; i < n && ok2; ++i) {
                 if (jobs[i].rows_p <= BM || bns[i] < 128)
                     ok2 = false;
-                tiles2 += ((jobs[i].rows_p + 2 * BM - 1) / (2 * BM)) * ((jobs[i].rows_q + bns[i] - 1) / bns[i]);
+                const int64_t nb = (jobs[i].rows_q + bns[i] - 1) / bns[i];
+                tiles1 += ((jobs[i].rows_p + BM - 1) / BM) * nb;
+                tiles2 += ((jobs[i].rows_p + 2 * BM - 1) / (2 * BM)) * nb;
+                long_k = long_k && jobs[i].K >= 32 * BK;
             }
             // 256-row tiles load a third fewer bytes per MMA; take them
             // while they still give at least half the SMs a tile, on CTA
             // pairs where the launch allows them (measured: the tensor pipe
-            // 85 % busy at 8192^3 against 75 % for one-CTA 256-row tiles)
-            c.mt = ok2 && 2 * tiles2 >= sm_count() ? (pair_ok ? 3 : 2) : 1;
+            // 85 % busy at 8192^3 against 75 % for one-CTA 256-row tiles).
+            // Pairs also where they occupy as many SMs as 128-row tiles
+            // would and K is long enough for the k-loop to dominate
+            // (512 x 8192 x 8192: 29.4 us against 32.5 us; at K = 2048 the
+            // two run level).
+            const int sms = sm_count();
+            const bool pair_fill = pair_ok && long_k && 2 * tiles2 >= std::min<int64_t>(tiles1, sms);
+            c.mt = ok2 && (2 * tiles2 >= sms || pair_fill) ? (pair_ok ? 3 : 2) : 1;
         }
     }
     if (mixed_kinds(jobs, n) || (n > 0 && jobs[0].sfp != nullptr))
@@ -2599,14 +2617,6 @@ int graph_params(fp8_grouped_graph* g, const fp8_gemm_problem* problems, int num
     *sig = signature(jobs, bns, n, g->max_ctas);
     memset(&g->prm, 0, sizeof(g->prm));
     rc = build_plan(g->prm, jobs, bns, n, g->max_ctas, nullptr, &g->plan);
-    if (rc == FP8_OK && g->plan.cluster > 1) {
-        // a graph kernel node carries no cluster shape: CTA-pair tiles are
-        // replaced by 256-row tiles of one CTA (the same sums, the same bits)
-        TileChoice c;
-        c.mt = 2;
-        memset(&g->prm, 0, sizeof(g->prm));
-        rc = build_plan(g->prm, jobs, bns, n, g->max_ctas, &c, &g->plan);
-    }
     if (rc == FP8_OK)
         bind_workspace(g->prm, g->plan, g->ws);
     return rc;
@@ -2651,8 +2661,16 @@ extern "C" int gemm_fp8_grouped_graph_create(const fp8_gemm_problem* problems, i
     void* args[1];
     if (rc == FP8_OK) {
         cudaKernelNodeParams kp = node_params(g, args);
+        // CTA-pair launches: the node carries the cluster shape
+        cudaKernelNodeAttrValue cv{};
+        cv.clusterDim.x = static_cast<unsigned>(g->plan.cluster > 1 ? g->plan.cluster : 1);
+        cv.clusterDim.y = 1;
+        cv.clusterDim.z = 1;
         if (cudaGraphCreate(&g->graph, 0) != cudaSuccess ||
             cudaGraphAddKernelNode(&g->node, g->graph, nullptr, 0, &kp) != cudaSuccess ||
+            (g->plan.cluster > 1 &&
+             cudaGraphKernelNodeSetAttribute(g->node, cudaKernelNodeAttributeClusterDimension, &cv) !=
+                 cudaSuccess) ||
             cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
             rc = FP8_ERR_CUDA;
     }

@@ -90,6 +90,14 @@ __device__ __forceinline__ uint32_t cluster_ctarank()
     return r;
 }
 
+// CTAs in this CTA's thread-block cluster (1 for a launch without clusters).
+__device__ __forceinline__ uint32_t cluster_nctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
 // Cluster-wide barrier (all threads of every CTA of the cluster); a CTA's
 // shared memory must outlive its peers' accesses to it.
 __device__ __forceinline__ void cluster_sync()

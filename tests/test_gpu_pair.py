@@ -140,3 +140,55 @@ def test_pair_raster_band(gb):
         assert gb.gemm_fp8_dense_plan(16384, 16384, 16384)["group_m"] == 4
     finally:
         gb.fp8_gemm_set_tile_config(0, 0)
+
+
+def test_pair_grouped_graph_equals_direct(gb, orc, pair):
+    """A CUDA-graph grouped launch of CTA-pair tiles (the kernel node carries
+    the cluster shape) equals the direct launch bit for bit, before and after
+    a pointer update.  A node without clusters would do no work and record
+    FP8_ERR_UNSUPPORTED, so both checks would fail."""
+    shapes = [(2048, 2048, 1024), (1536, 4096, 512), (1024, 2560, 2048)]
+
+    def problems(seed):
+        probs, outs, keep = [], [], []
+        for i, (M, N, K) in enumerate(shapes):
+            A, dA = orc.quantize(workloads.randn_f32((M, K), seed=seed + i), 1)
+            B, dB = orc.quantize(workloads.randn_f32((N, K), seed=seed + 10 + i), 1)
+            t = [torch.from_numpy(v).cuda() for v in (A, B, dA, dB)]
+            C = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+            keep += t
+            outs.append(C)
+            probs.append(gb.make_problem(t[0], t[1], t[2], 1, t[3], 1, C, 1.0, gb.OUT_BF16))
+        return probs, outs, keep
+
+    p1, o1, k1 = problems(300)
+    p2, o2, k2 = problems(400)
+    gb.gemm_fp8_grouped(p1)
+    gb.gemm_fp8_grouped(p2)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    ref1, ref2 = [c.clone() for c in o1], [c.clone() for c in o2]
+    for c in o1 + o2:
+        c.zero_()
+    g = gb.GroupedGraph(p1)
+    g.launch()
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    for a, b in zip(ref1, o1):
+        assert torch.equal(a, b)
+    g.update(p2)
+    g.launch()
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    for a, b in zip(ref2, o2):
+        assert torch.equal(a, b)
+    g.close()
+
+
+def test_pair_chosen_for_long_k_mid_rows(gb):
+    """Pairs where they occupy as many SMs as 128-row tiles and K >= 4096;
+    128-row tiles at the same shape with short K."""
+    gb.fp8_gemm_set_tile_config(0, 0)
+    assert gb.gemm_fp8_dense_plan(512, 8192, 8192)["mt"] == 3
+    assert gb.gemm_fp8_dense_plan(2048, 2048, 2048)["mt"] == 1
+    assert gb.gemm_fp8_dense_plan(256, 8192, 8192)["mt"] == 1
