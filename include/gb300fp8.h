@@ -396,6 +396,17 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * either.  Affects launches enqueued after the call, from any thread. */
 int fp8_gemm_set_tile_config(int mt, int group_m);
 
+/* B-block multicast for 128-row-tile launches.  mode 1: a single dense
+ * problem that is not split along K runs as clusters of 4 (else 2) CTAs on
+ * consecutive row blocks of one N column where the tiles, the grid and the
+ * raster divide into such clusters: each CTA loads its own A rows (MMA-M
+ * side) and a quarter (half) of the shared B block (MMA-N side), multicast
+ * to the cluster by TMA, which cuts the bytes each SM reads per k-block.
+ * mode 0 (default): never; measured 2-9 % slower on mid-size and skinny
+ * products on GB300.  Results do not depend on it.  FP8_ERR_INVALID for any
+ * other mode.  Affects launches planned after the call, from any thread. */
+int fp8_gemm_set_multicast(int mode);
+
 /* How gemm_fp8_dense would run a problem now (tile shape, split, grid),
  * without launching anything; for tuning, tests and callers of
  * gemm_fp8_dense_noalloc that size their problems against its scratch. */
@@ -408,6 +419,8 @@ typedef struct {
     int grid;               /* CTAs launched */
     int swapped;            /* 1: run as C^T = B A^T (small M on the MMA N side) */
     int group_m;            /* raster band height in tiles (fp8_gemm_set_tile_config) */
+    int multicast;          /* CTAs sharing one B block by TMA multicast
+                               (fp8_gemm_set_multicast; 0: none) */
     size_t workspace_bytes; /* split-K scratch the launch needs (0: none) */
 } fp8_gemm_plan_info;
 

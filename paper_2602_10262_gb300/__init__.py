@@ -20,7 +20,8 @@ __all__ = [
     "Fp8Error", "library", "fp8_quantize_e4m3", "fp8_quantize_e5m2", "prune24_compress",
     "prune24_decompress", "gemm_fp8_dense", "gemm_fp8_dense_fmt", "gemm_fp8_sparse24",
     "gemm_fp8_sparse24_fmt", "gemm_fp8_grouped", "gemm_fp8_grouped_ex", "fp8_last_device_error",
-    "fp8_device_sm_count", "fp8_test_stall_gemm_loads", "fp8_gemm_set_tile_config", "gemm_fp8_grouped_autotune",
+    "fp8_device_sm_count", "fp8_test_stall_gemm_loads", "fp8_gemm_set_tile_config", "fp8_gemm_set_multicast",
+    "gemm_fp8_grouped_autotune",
     "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
     "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2", "fp8_quantize_mx", "fp8_mx_scales_to_tiled",
     "fp8_mx_scale_tiled_bytes", "gemm_fp8_mx", "gemm_fp8_dense_plan",
@@ -115,7 +116,7 @@ def fp8_test_stall_gemm_loads(launches: int, wait_limit_ms: float = 0.0) -> None
 def gemm_fp8_dense_plan(M: int, N: int, K: int, out_dtype: int = OUT_BF16) -> dict:
     """How gemm_fp8_dense would run [M, K] x [N, K]^T now (tile kind, N width,
     k-blocks per stage, K slices, cluster size, grid, operand swap, raster
-    band, split-K scratch bytes), without launching."""
+    band, B multicast group, split-K scratch bytes), without launching."""
     info = _lib.FP8PlanInfo()
     _check(library().gemm_fp8_dense_plan(int(M), int(N), int(K), int(out_dtype), ctypes.byref(info)),
            "gemm_fp8_dense_plan")
@@ -126,6 +127,12 @@ def fp8_gemm_set_tile_config(mt: int = 0, group_m: int = 0) -> None:
     """Force the GEMM tile shape (mt 1 or 2 row-halves per tile, raster band
     height group_m); 0 restores the per-launch choice."""
     _check(library().fp8_gemm_set_tile_config(int(mt), int(group_m)), "fp8_gemm_set_tile_config")
+
+
+def fp8_gemm_set_multicast(mode: int = 0) -> None:
+    """B-block multicast within clusters of 128-row-tile launches: 1 where it
+    applies, 0 never (default)."""
+    _check(library().fp8_gemm_set_multicast(int(mode)), "fp8_gemm_set_multicast")
 
 
 def _quantize(name: str, x, scale_mode, q, dequant_scale, stream):

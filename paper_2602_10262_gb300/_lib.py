@@ -50,7 +50,8 @@ class FP8TileConfig(ctypes.Structure):
 class FP8PlanInfo(ctypes.Structure):
     """Mirror of ``fp8_gemm_plan_info``."""
     _fields_ = [("mt", I32), ("bn", I32), ("k_blocks_per_stage", I32), ("splits", I32), ("cluster", I32),
-                ("grid", I32), ("swapped", I32), ("group_m", I32), ("workspace_bytes", ctypes.c_size_t)]
+                ("grid", I32), ("swapped", I32), ("group_m", I32), ("multicast", I32),
+                ("workspace_bytes", ctypes.c_size_t)]
 
 
 class FP8ServerConfig(ctypes.Structure):
@@ -109,6 +110,7 @@ SIGNATURES = {
     "fp8_quantize_e4m3_rows_grouped": (I32, [ctypes.POINTER(FP8QuantJob), I32, P]),
     "fp8_gemm_set_tile_config": (I32, [I32, I32]),
     "gemm_fp8_dense_plan": (I32, [I64, I64, I64, I32, ctypes.POINTER(FP8PlanInfo)]),
+    "fp8_gemm_set_multicast": (I32, [I32]),
     "gemm_fp8_grouped_autotune": (I32, [ctypes.POINTER(FP8Problem), I32, I32, I32, P,
                                         ctypes.POINTER(FP8TileConfig)]),
     "gemm_fp8_tune_cache_save": (I32, [ctypes.c_char_p]),

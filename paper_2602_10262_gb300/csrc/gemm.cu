@@ -194,6 +194,8 @@ struct Params {
     float* ws;              // split-K partial sums (nullptr when no problem splits)
     unsigned* ctr;          // split-K arrival counters, zero between launches
     int cluster_split;      // > 0: one problem whose split tiles run as clusters of this many CTAs
+    int mc;                 // > 0: clusters of this many CTAs take consecutive tiles of one N column;
+                            // each loads 1/mc of the shared Q block and multicasts it to all
     unsigned long long wait_ns;   // limit of every bounded wait (kWaitLimitNs unless a test sets another)
     int withhold_loads;     // failure-path test: the producer issues no loads, so the MMA warp's
                             // first wait runs past wait_ns and the launch ends with FP8_ERR_TIMEOUT
@@ -596,8 +598,10 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     // a launch whose cluster shape does not match its plan (pairs need
     // clusters of two, cluster split-K one CTA per slice) does nothing: no
     // CTA addresses a peer that is not there
-    if ((PAIR ? 2u : (prm.cluster_split > 0 ? static_cast<uint32_t>(prm.cluster_split) : 1u)) !=
-        cluster_nctarank()) {
+    const int mc = PAIR || MX || SP || MT != 1 ? 0 : prm.mc;
+    if ((PAIR ? 2u
+              : (prm.cluster_split > 0 ? static_cast<uint32_t>(prm.cluster_split)
+                                       : (mc > 0 ? static_cast<uint32_t>(mc) : 1u))) != cluster_nctarank()) {
         if (threadIdx.x == 0)
             report_device_error(prm.err, FP8_ERR_UNSUPPORTED);
         return;
@@ -616,6 +620,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     // CTA pairs walk the tiles pair by pair (both CTAs of a pair take the
     // same tiles); other launches CTA by CTA
     const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const int qrank = mc > 0 ? static_cast<int>(cluster_ctarank()) : 0;
+    const uint16_t mc_mask = static_cast<uint16_t>((1u << (mc > 0 ? mc : 1)) - 1u);
     const int tile0 = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
     const int tile_step = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
     const TileCoord tc_first = tile_coord(prm, tile0);
@@ -628,7 +634,9 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), 1);
+            // Q multicast: a slot is free once every CTA of the cluster has
+            // finished with it (their commits all arrive here)
+            mbar_init(empty_bar(s), mc > 0 ? mc : 1);
         }
         for (int b = 0; b < C::kAcc; ++b) {
             mbar_init(tfull_bar(b), 1);
@@ -670,6 +678,10 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                 report_device_error(err, FP8_ERR_UNSUPPORTED);
         }
     }
+    // Q multicast: every CTA's barriers exist before a peer's copies or
+    // commits reach them
+    if (!PAIR && mc > 0)
+        cluster_sync();
     // Everything above reads only the kernel parameters and shared memory;
     // from here on the previous kernel's outputs (operands, scales, the
     // split-K workspace) are read and written.
@@ -703,7 +715,6 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                 const bool sparse = P.sparse != 0;
                 const uint32_t a_bytes = sparse ? C::kSpChunk + C::kMetaChunk : C::kAChunk;
                 const uint32_t b_chunk = static_cast<uint32_t>(P.bn) * BK;      // B chunks bn x 128 B apart
-                const uint32_t chunk_bytes = a_bytes + b_chunk;
                 const int row0 = tc.m_blk * BM * MT;
                 const int col0 = tc.n_blk * P.bn;
                 const int kb0 = tc.slice * P.kb_per_split;
@@ -747,9 +758,12 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                         continue;
                     }
                     // a 3-D box always lands all KC chunks (those past K as zeros);
-                    // block scales come for the nck k-blocks of the stage only
+                    // multicast Q slices and block scales come for the nck
+                    // k-blocks of the stage only
+                    const uint32_t p_chunks = static_cast<uint32_t>(KC > 1 && P.tma3d ? KC : nck);
+                    const uint32_t q_chunks = static_cast<uint32_t>(KC > 1 && P.tma3d && mc == 0 ? KC : nck);
                     mbar_arrive_expect_tx(full_bar(stage),
-                                          chunk_bytes * static_cast<uint32_t>(KC > 1 && P.tma3d ? KC : nck) +
+                                          a_bytes * p_chunks + b_chunk * q_chunks +
                                               (MX ? 2u * C::kSfChunk * static_cast<uint32_t>(nck) : 0u));
                     if (sparse && KC > 1) {
                         // kept codes then metadata of all KC k-blocks (3-D chunk boxes)
@@ -766,7 +780,16 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                             if (c < nck)
                                 tma_load_2d(sa + c * C::kAChunk, map_p, full_bar(stage), (kb + c) * BK, row0);
                     }
-                    if (KC > 1 && P.tma3d) {
+                    if (mc > 0) {
+                        // this CTA's 1/mc of the Q rows, into every CTA of the cluster
+                        const int qrows = P.bn / (mc > 0 ? mc : 1);
+                        const uint32_t qoff = static_cast<uint32_t>(qrank * qrows * BK);
+#pragma unroll
+                        for (int c = 0; c < KC; ++c)
+                            if (c < nck)
+                                tma_load_2d_multicast(sa + C::kABytes + c * b_chunk + qoff, map_q, full_bar(stage),
+                                                      (kb + c) * BK, col0 + qrank * qrows, mc_mask);
+                    } else if (KC > 1 && P.tma3d) {
                         tma_load_3d(sa + C::kABytes, map_q, full_bar(stage), 0, col0, kb);
                     } else {
 #pragma unroll
@@ -932,7 +955,10 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                             }
                         }
                     }
-                    mma_commit(empty_bar(stage));
+                    if (mc > 0)
+                        mma_commit_multicast(empty_bar(stage), mc_mask);
+                    else
+                        mma_commit(empty_bar(stage));
                     if (++stage == S) {
                         stage = 0;
                         phase ^= 1u;
@@ -1109,7 +1135,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     // shared memory; pairs: neither CTA frees the pair's tensor memory (or
     // its barriers) while the other may still use them (every wait above is
     // bounded, so all threads get here)
-    if (PAIR || cluster_split)
+    if (PAIR || cluster_split || mc > 0)
         cluster_sync();
     if (warp == 1) {
         tc_fence_after();
@@ -1786,6 +1812,48 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
     return sparse ? plan<MAXP, 2, true>(prm, max_ctas, pl) : plan<MAXP, 2, false>(prm, max_ctas, pl);
 }
 
+// Q multicast (fp8_gemm_set_multicast): 1 = where plan_multicast finds it
+// applies, 0 = never (default: measured slower, see plan_multicast).
+std::atomic<int> g_multicast_mode{0};
+
+// Q multicast for a launch of 128-row tiles of one dense problem that is not
+// split along K: clusters of mc CTAs (4, else 2) take mc consecutive tiles of
+// the raster, i.e. mc row blocks of one N column, and each loads 1/mc of the
+// column's Q block per stage, multicast to the whole cluster.  Every CTA
+// still reads its own P rows.  Applies when the tiles, the grid, the raster
+// band and the row blocks divide into clusters (so every CTA of a cluster
+// walks the same columns in lockstep), the Q slices stay whole swizzle atoms
+// (8 rows), and every cluster can be resident at once.  Remakes the Q map
+// for the slice box; the MMAs and their order do not change, so neither do
+// the results.  Off unless enabled: on GB300 it made every shape it applies
+// to slower (1024^3 by 9 %, 2048^3 by 7 %, 128 x 8192 x 8192 by 2 %, one
+// box, interleaved replays): each SM reads fewer B bytes, but the k-loops
+// here are not bound by them, and the clusters' lockstep ring and launch
+// cost more than that saves.
+template <int MAXP>
+bool plan_multicast(Params<MAXP>& prm, const Job* jobs, int n, Plan* pl)
+{
+    if (g_multicast_mode.load(std::memory_order_relaxed) != 1 || n != 1 || pl->rows_per_tile != BM ||
+        jobs[0].E != nullptr || jobs[0].sfp != nullptr)
+        return false;
+    Problem& P = prm.prob[0];
+    if (P.splits != 1)
+        return false;
+    const int tiles = P.m_blocks * P.n_blocks;
+    for (int mc : {4, 2}) {
+        if (P.bn % (8 * mc) != 0 || P.m_blocks % mc != 0 || prm.group_m % mc != 0 || tiles % mc != 0 ||
+            pl->grid % mc != 0 || max_clusters(*pl, mc) < pl->grid / mc)
+            continue;
+        const Job& j = jobs[0];
+        if (!make_map(&P.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, P.bn / mc, CU_TENSOR_MAP_SWIZZLE_128B))
+            return false;
+        prm.mc = mc;
+        pl->cluster = mc;
+        return true;
+    }
+    return false;
+}
+
 // Plan a launch.  With allow_cluster, a single problem that splits along K
 // runs its tiles' slices as thread-block clusters (the slices add up through
 // distributed shared memory, no workspace) when one unit per CTA covers the
@@ -1797,6 +1865,9 @@ int build_plan(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int n, int
 {
     const int rc = build_plan_tiles(prm, jobs, bns_in, n, max_ctas, expl, pl);
     prm.cluster_split = 0;
+    prm.mc = 0;
+    if (rc == FP8_OK && pl->cluster == 0 && plan_multicast(prm, jobs, n, pl))
+        return rc;
     if (rc == FP8_OK && pl->cluster == 2) {
         // CTA pairs: a persistent launch takes no more pairs than can be
         // resident at once (a launch in waves may take more)
@@ -2135,13 +2206,14 @@ extern "C" int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtyp
     if (rc != FP8_OK)
         return rc;
     const ProblemScalars& P = prm.prob[0];
-    info->mt = pl.cluster == 2 && !prm.cluster_split ? 3 : pl.rows_per_tile / BM;
+    info->mt = pl.cluster == 2 && !prm.cluster_split && !prm.mc ? 3 : pl.rows_per_tile / BM;
     info->bn = P.bn;
     info->k_blocks_per_stage = pl.kc;
     info->splits = P.splits;
     info->cluster = pl.cluster > 1 ? pl.cluster : 0;
     info->grid = pl.grid;
     info->swapped = M <= 128 && N > M ? 1 : 0;          // make_job's rule for dense products
+    info->multicast = prm.mc;
     info->group_m = prm.group_m;
     info->workspace_bytes = workspace_bytes(pl);
     return FP8_OK;
@@ -2772,6 +2844,14 @@ extern "C" int fp8_gemm_set_tile_config(int mt, int group_m)
         return FP8_ERR_INVALID;
     gb300::g_force_mt.store(mt);
     gb300::g_force_group_m.store(group_m);
+    return FP8_OK;
+}
+
+extern "C" int fp8_gemm_set_multicast(int mode)
+{
+    if (mode != 0 && mode != 1)
+        return FP8_ERR_INVALID;
+    gb300::g_multicast_mode.store(mode);
     return FP8_OK;
 }
 

@@ -197,6 +197,20 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// 2-D tiled load multicast to the CTAs of this cluster in `cta_mask` (bit i:
+// cluster rank i): the box lands at the same shared-memory offset `dst` in
+// each of them, and each one's mbarrier at offset `bar` receives the bytes
+// as transaction bytes.  The tensor map is of this GPU's own memory.
+__device__ __forceinline__ void tma_load_2d_multicast(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                                      int32_t x, int32_t y, uint16_t cta_mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(cta_mask)
+        : "memory");
+}
+
 // Plain bulk copy global -> shared (no tensor map): `bytes` (a multiple of
 // 16) from a 16-byte aligned global address to a 16-byte aligned shared
 // address; completion as transaction bytes on `bar`.
@@ -329,6 +343,17 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      bar)
                  : "memory");
+}
+
+// As mma_commit, arriving on the mbarrier at offset `bar` of every CTA of
+// the cluster in `cta_mask` once this thread's MMAs have completed.
+__device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t cta_mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(cta_mask)
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld_wait()
