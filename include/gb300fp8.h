@@ -376,7 +376,8 @@ int gemm_fp8_grouped(const fp8_gemm_problem *problems, int num_problems, fp8_str
  * it, the launch has more CTAs than SMs, each taking a few tiles and
  * running in waves, so SMs are handed back between tiles (higher-priority
  * streams get them then) instead of being held to the launch's last tile.
- * The results do not depend on max_ctas. */
+ * A cap of 1 never uses CTA-pair tiles (a pair needs two CTAs).  The
+ * results do not depend on max_ctas. */
 int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int max_ctas,
                         fp8_stream_t stream);
 

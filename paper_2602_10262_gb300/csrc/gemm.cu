@@ -1672,7 +1672,8 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
     TileChoice c;
     if (expl && expl->mt) {
         c = *expl;
-        bool pair_ok = n > 0 && jobs[0].sfp == nullptr && (c.bn_cap == 0 || c.bn_cap >= BN_MAX);
+        bool pair_ok = n > 0 && jobs[0].sfp == nullptr && (c.bn_cap == 0 || c.bn_cap >= BN_MAX) &&
+                       (max_ctas <= 0 || max_ctas >= 2);
         for (int i = 0; i < n; ++i)
             pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
         if (c.mt == 3 && !pair_ok)
@@ -1690,8 +1691,10 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
                     c.group_m = it->second.group_m;
             }
         }
-        // CTA pairs (mt 3) take dense problems whose N tiles are 256 wide
-        bool pair_ok = n > 0 && jobs[0].sfp == nullptr && (c.bn_cap == 0 || c.bn_cap >= BN_MAX);
+        // CTA pairs (mt 3) take dense problems whose N tiles are 256 wide,
+        // in launches allowed two CTAs or more
+        bool pair_ok = n > 0 && jobs[0].sfp == nullptr && (c.bn_cap == 0 || c.bn_cap >= BN_MAX) &&
+                       (max_ctas <= 0 || max_ctas >= 2);
         for (int i = 0; i < n; ++i)
             pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
         if (c.mt == 3 && !pair_ok)

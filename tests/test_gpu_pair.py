@@ -192,3 +192,21 @@ def test_pair_chosen_for_long_k_mid_rows(gb):
     assert gb.gemm_fp8_dense_plan(512, 8192, 8192)["mt"] == 3
     assert gb.gemm_fp8_dense_plan(2048, 2048, 2048)["mt"] == 1
     assert gb.gemm_fp8_dense_plan(256, 8192, 8192)["mt"] == 1
+
+
+def test_single_cta_cap_takes_no_pairs(gb, orc):
+    """A launch capped at one CTA runs 128-row tiles (a pair needs two CTAs)
+    and gives the bits of the uncapped pair launch."""
+    gb.fp8_gemm_set_tile_config(0, 0)
+    M, N, K = 2048, 2560, 1024
+    A, dA = orc.quantize(workloads.randn_f32((M, K), seed=31), 1)
+    B, dB = orc.quantize(workloads.randn_f32((N, K), seed=32), 1)
+    t = [torch.from_numpy(v).cuda() for v in (A, B, dA, dB)]
+    outs = []
+    for cap in (0, 1, 2):
+        C = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+        gb.gemm_fp8_grouped_ex([gb.make_problem(t[0], t[1], t[2], 1, t[3], 1, C, 1.0, gb.OUT_BF16)], cap)
+        torch.cuda.synchronize()
+        assert gb.fp8_last_device_error() == 0
+        outs.append(C)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
