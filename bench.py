@@ -1236,6 +1236,24 @@ def shape_sweep(gb, dev):
     operands (see _l2_copies) so no timed call finds them in L2; the
     transformer layer's operands are far larger than L2 already."""
     out = {"dense": [], "sparse": [], "transformer_layer": None}
+    # config 1: the small dense case (per-tensor scales, FP32 out): a
+    # latency point, one launch's fixed cost
+    M, N, K = workloads.DENSE_SMALL
+    g = torch.Generator(device=dev).manual_seed(workloads.SEED_A)
+    x = torch.randn((M, K), generator=g, device=dev)
+    w = torch.randn((N, K), generator=g, device=dev)
+    A, dA = gb.fp8_quantize_e4m3(x, 0)
+    B, dB = gb.fp8_quantize_e4m3(w, 0)
+    n1 = _l2_copies(dev, M * K + N * K + 4 * M * N)
+    sets = [(A.clone(), B.clone(), torch.empty((M, N), device=dev)) for _ in range(n1)]
+    ms = _time_ms([lambda a=a, b=b, c=c: gb.gemm_fp8_dense(a, b, dA, 0, dB, 0, 1.0, gb.OUT_F32, C=c)
+                   for a, b, c in sets])
+    bsets = [(x.bfloat16(), w.bfloat16()) for _ in range(n1)]
+    ms_bf16 = _time_ms([lambda xb=xb, wb=wb: torch.matmul(xb, wb.T) for xb, wb in bsets])
+    out["dense_small"] = {"M": M, "N": N, "K": K, "scales": "per tensor", "out": "fp32",
+                          "fp8_us": ms * 1e3, "bf16_matmul_us": ms_bf16 * 1e3,
+                          "fp8_tflops": 2.0 * M * N * K / ms / 1e9}
+    del sets, bsets
     for (M, N, K) in [(s, s, s) for s in workloads.SQUARE_SWEEP] + \
                      [(m, workloads.SKINNY_NK, workloads.SKINNY_NK) for m in workloads.SKINNY_M]:
         x, w, A, dA, B, dB = _operands(gb, M, N, K, dev, M + N)
@@ -1424,7 +1442,7 @@ def main():
     Cs = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
     stream = torch.cuda.current_stream()
 
-    # does this build have the sparse path?
+    # does the loaded library run the sparse path?
     sparse_ok = True
     try:
         gb.fp8_quantize_e4m3(x, 1, A, dA)
