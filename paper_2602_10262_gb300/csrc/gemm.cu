@@ -84,10 +84,12 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 // (2 KB each), then the B chunks: 4 / 5 / 7 / 8 stages for BNC = 128 / 64 /
 // 32 / 16, each k-block's metadata in its own 4 TMEM columns.  Launches
 // mixing dense and sparse problems, BNC = 256 and MT = 2 keep KC = 1.
-// MX: block-scaled launches (kind::mxf8f6f4): 128 x 128 tiles, dense codes
-// as above, and per k-block two 512-byte chunks of E8M0 scales after the B
-// chunks (A's 128 rows, then B's), copied into a ring of TMEM columns
-// 128..255 (8 per k-block: A's 4 then B's 4) beside the first accumulator.
+// MX: block-scaled launches (kind::mxf8f6f4): 128 x 128 or 128 x 256 tiles,
+// dense codes as above, and per k-block 512-byte chunks of E8M0 scales after
+// the B chunks (A's 128 rows, then B's, 128 rows per chunk), copied into a
+// ring of TMEM columns (per k-block A's 4, then 4 per 128 rows of B):
+// columns 128..255 beside the first of two accumulators for 128-wide tiles,
+// from column 256 after the single accumulator for 256-wide ones.
 // PAIR: CTA-pair launches (cta_group::2, clusters of two): a 256 x 256 tile
 // per pair, each CTA loading its 128 rows of A and 128 rows of B (two
 // k-blocks per stage, three 64 KB stages) and holding its 128 x 256 half of
@@ -114,12 +116,20 @@ struct Cfg {
     static constexpr int kABytes = KC * kAChunk;
     static constexpr int kBBytes = KC * kBChunk;
     static constexpr int kSfChunk = 512;                        // scales of 128 rows x one k-block
-    static constexpr int kSfBytes = MX ? KC * 2 * kSfChunk : 0;
-    static constexpr int kSfCol0 = BNC;                         // MX: scale ring in TMEM columns
+    static constexpr int kSfQ = MX ? BNC / 128 : 0;              // MX: 128-row scale chunks of B per k-block
+    // MX: A's chunk and B's chunks of each k-block, rounded up to whole
+    // swizzle atoms
+    static constexpr int kSfBytes = MX ? (KC * (1 + kSfQ) * kSfChunk + 1023) / 1024 * 1024 : 0;
+    // MX: the scale ring's TMEM columns (per k-block 4 for A, 4 per 128 rows
+    // of B): beside the first accumulator for 128-wide tiles, after the
+    // single accumulator for 256-wide ones
+    static constexpr int kSfCols = 4 * (1 + kSfQ);
+    static constexpr int kSfCol0 = (MX && BNC == BN_MAX) ? BN_MAX : BNC;
     static constexpr int kStageBytes = kABytes + kBBytes + kSfBytes;
     static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : (BNC == 256 ? SPARSE_BN_MAX : BNC);
     static constexpr int kTmemCols = PAIR ? PAIR_TMEM_COLS : TMEM_COLS;
-    static constexpr int kAcc = PAIR ? PAIR_TMEM_COLS / BN_MAX : (MT == 2 ? 1 : 2);   // accumulator buffers
+    static constexpr int kAcc = PAIR ? PAIR_TMEM_COLS / BN_MAX
+                                     : ((MT == 2 || (MX && BNC == BN_MAX)) ? 1 : 2);   // accumulator buffers
     // epilogue warps: 4 per 128 rows (one per TMEM lane quarter); 256-wide
     // 128-row tiles (and pairs) use 8, two per lane quarter splitting the
     // columns, so each SM sub-partition has a second warp to hide latencies
@@ -143,8 +153,10 @@ struct Cfg {
     static_assert(KC == 1 || (KC == 2 && MT == 1 && (BNC <= 128 || PAIR)), "two-chunk stages: 128-row tiles");
     static_assert(!PAIR || (MT == 1 && !SP && !MX && BNC == BN_MAX && KC == 2), "CTA pairs: dense 256 x 256 tiles");
     static_assert(kBChunk % 1024 == 0, "B chunks stay swizzle-atom aligned");
-    static_assert(!MX || (MT == 1 && !SP && BNC == 128), "block-scaled launches: 128 x 128 dense tiles");
-    static_assert(!MX || kSfCol0 + 8 * kStages * KC <= BN_MAX, "scale ring fits beside the first accumulator");
+    static_assert(!MX || (MT == 1 && !SP && (BNC == 128 || (BNC == BN_MAX && KC == 1))),
+                  "block-scaled launches: 128-row dense tiles, 128 or 256 wide");
+    static_assert(!MX || kSfCol0 + kSfCols * kStages * KC <= (kAcc == 1 ? TMEM_COLS : BN_MAX),
+                  "scale ring fits beside the accumulators");
 };
 
 // Everything of a problem but its tensor maps.  Each role thread copies this
@@ -703,6 +715,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                 const TileCoord tc = tile == tile0 ? tc_first : tile_coord(prm, tile);
                 const bool first = tile == tile0;
                 const ProblemScalars P = first ? P_first : prm.prob[tc.p];
+                const int sf_q_tiles = MX ? (P.rows_q + BM - 1) / BM : 0;     // B's 128-row scale tiles
                 if (!first || P.sparse) {
                     tma_prefetch_desc(&prm.prob[tc.p].tmP);
                     tma_prefetch_desc(&prm.prob[tc.p].tmQ);
@@ -762,9 +775,15 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                     // k-blocks of the stage only
                     const uint32_t p_chunks = static_cast<uint32_t>(KC > 1 && P.tma3d ? KC : nck);
                     const uint32_t q_chunks = static_cast<uint32_t>(KC > 1 && P.tma3d && mc == 0 ? KC : nck);
+                    uint32_t sf_chunks = 0;
+                    if constexpr (MX) {
+                        sf_chunks = 1;
+                        for (int h = 0; h < C::kSfQ; ++h)
+                            sf_chunks += (tc.n_blk * C::kSfQ + h < sf_q_tiles) ? 1u : 0u;
+                    }
                     mbar_arrive_expect_tx(full_bar(stage),
                                           a_bytes * p_chunks + b_chunk * q_chunks +
-                                              (MX ? 2u * C::kSfChunk * static_cast<uint32_t>(nck) : 0u));
+                                              sf_chunks * C::kSfChunk * static_cast<uint32_t>(nck));
                     if (sparse && KC > 1) {
                         // kept codes then metadata of all KC k-blocks (3-D chunk boxes)
                         tma_load_3d(sa, map_p, full_bar(stage), 0, row0, kb);
@@ -799,13 +818,21 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                                             col0);
                     }
                     if constexpr (MX) {
-                        // the k-blocks of one 128-row tile are consecutive chunks
+                        // the k-blocks of one 128-row tile are consecutive chunks;
+                        // B's 128-row halves past its last row tile are not loaded
+                        // (their columns are never stored)
                         const uint32_t sf = sa + C::kABytes + C::kBBytes;
                         const size_t chunk_p = static_cast<size_t>(tc.m_blk) * P.sf_kb + kb;
-                        const size_t chunk_q = static_cast<size_t>(tc.n_blk) * P.sf_kb + kb;
                         bulk_load(sf, P.sfp + chunk_p * C::kSfChunk, C::kSfChunk * nck, full_bar(stage));
-                        bulk_load(sf + KC * C::kSfChunk, P.sfq + chunk_q * C::kSfChunk, C::kSfChunk * nck,
-                                  full_bar(stage));
+#pragma unroll
+                        for (int h = 0; h < C::kSfQ; ++h) {
+                            const int q_tile = tc.n_blk * C::kSfQ + h;
+                            if (q_tile < sf_q_tiles) {
+                                const size_t chunk_q = static_cast<size_t>(q_tile) * P.sf_kb + kb;
+                                bulk_load(sf + (1 + h) * KC * C::kSfChunk, P.sfq + chunk_q * C::kSfChunk,
+                                          C::kSfChunk * nck, full_bar(stage));
+                            }
+                        }
                     }
                     armed |= 1u << stage;
                     if (++stage == S) {
@@ -895,13 +922,17 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                         for (int c = 0; c < KC; ++c) {
                             if (c >= nck)
                                 break;
-                            // scales of k-block c (A's 128 rows, B's 128 rows) -> their
-                            // ring columns, each 32-row group to every lane quarter
-                            const uint32_t sf_col = static_cast<uint32_t>(C::kSfCol0 + 8 * (stage * KC + c));
+                            // scales of k-block c (A's 128 rows, then B's rows 128 at a
+                            // time) -> their ring columns, each 32-row group to every
+                            // lane quarter: B row r in column 4 + r / 32
+                            const uint32_t sf_col =
+                                static_cast<uint32_t>(C::kSfCol0 + C::kSfCols * (stage * KC + c));
                             const uint32_t sm_sf = sa + C::kABytes + C::kBBytes + c * C::kSfChunk;
                             tmem_cp_32x128b_warpx4(tmem_base + sf_col, sdesc_rows16_noswizzle(sm_sf));
-                            tmem_cp_32x128b_warpx4(tmem_base + sf_col + 4u,
-                                                   sdesc_rows16_noswizzle(sm_sf + KC * C::kSfChunk));
+#pragma unroll
+                            for (int h = 0; h < C::kSfQ; ++h)
+                                tmem_cp_32x128b_warpx4(tmem_base + sf_col + 4u * (1 + h),
+                                                       sdesc_rows16_noswizzle(sm_sf + (1 + h) * KC * C::kSfChunk));
                             const uint64_t adesc = sdesc_kmajor_sw128(sa + c * C::kAChunk);
                             const uint64_t bdesc_c = sdesc_kmajor_sw128(sa + C::kABytes + c * b_chunk);
 #pragma unroll
@@ -1750,7 +1781,7 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
     const TileChoice c = choose(jobs, bns_in, n, max_ctas, expl);
     const bool sparse = n > 0 && jobs[0].E != nullptr;     // all alike when mt == 2
     // N tile widths: the problems' own, under the tuned cap if any (block-
-    // scaled launches always use 128)
+    // scaled launches: 128 or 256, as gemm_fp8_mx chose)
     int bns[MAXP > 0 ? MAXP : 1];
     for (int i = 0; i < n; ++i)
         bns[i] = (c.bn_cap > 0 && jobs[i].sfp == nullptr) ? std::min(bns_in[i], c.bn_cap) : bns_in[i];
@@ -1775,10 +1806,14 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
     prm.num_problems = n;
     prm.group_m = c.group_m;
     if (n > 0 && jobs[0].sfp != nullptr) {
-        // block-scaled launches (single problems): 128 x 128 tiles
-        if constexpr (MAXP == 1)
+        // block-scaled launches (single problems): 128 x 256 tiles (one
+        // accumulator, the scale ring after it) or 128 x 128 tiles (two)
+        if constexpr (MAXP == 1) {
+            if (max_bn > 128)
+                return plan<MAXP, 1, false, BN_MAX, 1, true>(prm, max_ctas, pl);
             return kc == 2 ? plan<MAXP, 1, false, 128, 2, true>(prm, max_ctas, pl)
                            : plan<MAXP, 1, false, 128, 1, true>(prm, max_ctas, pl);
+        }
         return FP8_ERR_UNSUPPORTED;
     }
     if (c.mt == 3)
@@ -2340,7 +2375,9 @@ extern "C" int gemm_fp8_mx(int64_t M, int64_t N, int64_t K, const uint8_t* A, in
     const bool swapped = M <= 128 && N > M;          // make_job's rule for small-M dense products
     j.sfp = swapped ? b_scales : a_scales;
     j.sfq = swapped ? a_scales : b_scales;
-    const int bn = 128;
+    // 256-wide tiles (two 128-row scale tiles of B per k-block) where the
+    // problem has enough tiles for them, else 128-wide
+    const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX) == BN_MAX ? BN_MAX : 128;
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     return run_jobs(prm, &j, &bn, 1, 0, st);

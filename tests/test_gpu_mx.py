@@ -187,3 +187,60 @@ def test_mx_large_blocks(gb, orc):
     ref = orc.gemm_mx(Ao, SAo, Bo, SBo)
     S = orc.gemm_mx(parity.abs_codes(Ao), SAo, parity.abs_codes(Bo), SBo)
     parity.check_bf16(C[np.ix_(rows, rows)], ref, S, K)
+
+
+# Shapes whose N tiles are 256 wide (the planner keeps 256 while 2 x row
+# blocks x column blocks reach the SM count): one accumulator, B's scales
+# in two 128-row chunks per k-block, ring after the accumulator.  N = 800
+# leaves the last tile's second 128-row scale chunk outside B (not loaded).
+WIDE = [(4096, 1024, 256), (4096, 1000, 640), (4096, 800, 1024)]
+
+
+@pytest.mark.parametrize("case", ["a_rows", "a_blocks", "b_cols", "b_blocks"])
+def test_mx_wide_tiles_structured_scales(gb, orc, case):
+    M, N, K = 4096, 1024, 256
+    A = np.full((M, K), ONE, np.uint8)
+    B = np.full((N, K), ONE, np.uint8)
+    SA = np.full((M, K // 32), 127, np.uint8)
+    SB = np.full((N, K // 32), 127, np.uint8)
+    if case == "a_rows":
+        SA += ((np.arange(M) // 32) % 8).astype(np.uint8)[:, None]
+    elif case == "a_blocks":
+        SA += (np.arange(K // 32) % 8).astype(np.uint8)[None, :]
+    elif case == "b_cols":
+        SB += ((np.arange(N) // 32) % 8).astype(np.uint8)[:, None]
+    else:
+        SB += (np.arange(K // 32) % 8).astype(np.uint8)[None, :]
+    C = _gemm(gb, A, SA, B, SB)
+    rows = np.r_[0:160, M - 160:M]
+    ref = orc.gemm_mx(A[rows], SA[rows], B, SB)
+    assert np.array_equal(C[rows].astype(np.float64), ref), (C[rows][::32, ::32], ref[::32, ::32])
+
+
+@pytest.mark.parametrize("fmt", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K", WIDE)
+def test_mx_wide_tiles_small_integers_bit_exact(gb, orc, fmt, M, N, K):
+    A = workloads.small_int_codes((M, K), seed=M + K + 3, fmt=fmt[0])
+    B = workloads.small_int_codes((N, K), seed=N + K + 4, fmt=fmt[1])
+    g = np.random.default_rng(M + N + K)
+    SA = g.integers(127, 129, size=(M, K // 32)).astype(np.uint8)
+    SB = g.integers(126, 128, size=(N, K // 32)).astype(np.uint8)
+    C = _gemm(gb, A, SA, B, SB, fmt)
+    rows = np.r_[0:128, 1900:2100, M - 128:M]
+    ref = orc.gemm_mx(A[rows], SA[rows], B, SB, a_fmt=fmt[0], b_fmt=fmt[1])
+    assert np.array_equal(C[rows].astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("M,N,K", WIDE)
+def test_mx_wide_tiles_normal_inputs(gb, orc, M, N, K):
+    x = workloads.randn_f32((M, K), seed=M + 13)
+    w = workloads.randn_f32((N, K), seed=N + 14)
+    A, SA = orc.mx_quantize(x, 0)
+    B, SB = orc.mx_quantize(w, 0)
+    rows = np.r_[0:128, M - 256:M]
+    ref = orc.gemm_mx(A[rows], SA[rows], B, SB, alpha=0.5)
+    C = _gemm(gb, A, SA, B, SB, alpha=0.5, out_dtype=0)
+    parity.check_fp32(C[rows], ref)
+    Cb = _gemm(gb, A, SA, B, SB, alpha=0.5, out_dtype=1)
+    S = orc.gemm_mx(parity.abs_codes(A[rows]), SA[rows], parity.abs_codes(B), SB, alpha=0.5)
+    parity.check_bf16(Cb[rows], ref, S, K)
