@@ -89,6 +89,20 @@ def test_stall_switch_validates_and_resets(lib):
     assert lib.fp8_test_stall_gemm_loads(0, 0.0) == 0
 
 
+def test_tile_and_multicast_switches_validate(lib):
+    # launch-shape switches (no CUDA call): out-of-range values are refused,
+    # the defaults are restored
+    assert lib.fp8_gemm_set_tile_config(4, 0) == -1
+    assert lib.fp8_gemm_set_tile_config(-1, 0) == -1
+    assert lib.fp8_gemm_set_tile_config(0, -1) == -1
+    assert lib.fp8_gemm_set_tile_config(3, 8) == 0
+    assert lib.fp8_gemm_set_tile_config(0, 0) == 0
+    for bad in (-1, 2, 4):
+        assert lib.fp8_gemm_set_multicast(bad) == -1
+    assert lib.fp8_gemm_set_multicast(1) == 0
+    assert lib.fp8_gemm_set_multicast(0) == 0
+
+
 def test_mx_host_checks(lib):
     P = ctypes.c_void_p
     # tiled scale bytes: 512 per 128 rows x 128 columns, partial tiles rounded up
