@@ -427,6 +427,11 @@ typedef struct {
 
 int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info *info);
 
+/* How gemm_fp8_mx would run a block-scaled problem now: mt 3 (CTA pairs,
+ * 256 x 256 tiles, one accumulator per CTA, scale chunks loaded by TMA) or
+ * mt 1 with bn 256 or 128 (128-row tiles).  FP8_ERR_SHAPE unless K % 32 == 0. */
+int gemm_fp8_mx_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info *info);
+
 /* Autotuner: times every candidate tile configuration of this exact problem
  * list on `stream` (iters timed launches each, after one warm-up; the
  * problems' outputs are written each time): tile kind mt in {1, 2, 3} (3 only

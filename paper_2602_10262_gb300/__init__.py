@@ -24,7 +24,7 @@ __all__ = [
     "gemm_fp8_grouped_autotune",
     "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
     "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2", "fp8_quantize_mx", "fp8_mx_scales_to_tiled",
-    "fp8_mx_scale_tiled_bytes", "gemm_fp8_mx", "gemm_fp8_dense_plan",
+    "fp8_mx_scale_tiled_bytes", "gemm_fp8_mx", "gemm_fp8_dense_plan", "gemm_fp8_mx_plan",
 ]
 
 OUT_F32 = 0
@@ -120,6 +120,15 @@ def gemm_fp8_dense_plan(M: int, N: int, K: int, out_dtype: int = OUT_BF16) -> di
     info = _lib.FP8PlanInfo()
     _check(library().gemm_fp8_dense_plan(int(M), int(N), int(K), int(out_dtype), ctypes.byref(info)),
            "gemm_fp8_dense_plan")
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def gemm_fp8_mx_plan(M: int, N: int, K: int, out_dtype: int = OUT_BF16) -> dict:
+    """How gemm_fp8_mx would run [M, K] x [N, K]^T now (fields as
+    gemm_fp8_dense_plan), without launching."""
+    info = _lib.FP8PlanInfo()
+    _check(library().gemm_fp8_mx_plan(int(M), int(N), int(K), int(out_dtype), ctypes.byref(info)),
+           "gemm_fp8_mx_plan")
     return {name: getattr(info, name) for name, _ in info._fields_}
 
 

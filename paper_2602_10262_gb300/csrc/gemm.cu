@@ -116,7 +116,9 @@ struct Cfg {
     static constexpr int kABytes = KC * kAChunk;
     static constexpr int kBBytes = KC * kBChunk;
     static constexpr int kSfChunk = 512;                        // scales of 128 rows x one k-block
-    static constexpr int kSfQ = MX ? BNC / 128 : 0;              // MX: 128-row scale chunks of B per k-block
+    // MX: 128-row scale chunks of B per k-block (a pair's MMA reads all 256
+    // rows' scales from each CTA's tensor memory, so each CTA holds both)
+    static constexpr int kSfQ = MX ? BNC / 128 : 0;
     // MX: A's chunk and B's chunks of each k-block, rounded up to whole
     // swizzle atoms
     static constexpr int kSfBytes = MX ? (KC * (1 + kSfQ) * kSfChunk + 1023) / 1024 * 1024 : 0;
@@ -128,8 +130,8 @@ struct Cfg {
     static constexpr int kStageBytes = kABytes + kBBytes + kSfBytes;
     static constexpr int kMetaCol0 = kSparse2 ? SPARSE_BN_MAX_MT2 : (BNC == 256 ? SPARSE_BN_MAX : BNC);
     static constexpr int kTmemCols = PAIR ? PAIR_TMEM_COLS : TMEM_COLS;
-    static constexpr int kAcc = PAIR ? PAIR_TMEM_COLS / BN_MAX
-                                     : ((MT == 2 || (MX && BNC == BN_MAX)) ? 1 : 2);   // accumulator buffers
+    static constexpr int kAcc = (PAIR && !MX) ? PAIR_TMEM_COLS / BN_MAX
+                                              : ((MT == 2 || (MX && BNC == BN_MAX)) ? 1 : 2);   // accumulators
     // epilogue warps: 4 per 128 rows (one per TMEM lane quarter); 256-wide
     // 128-row tiles (and pairs) use 8, two per lane quarter splitting the
     // columns, so each SM sub-partition has a second warp to hide latencies
@@ -151,10 +153,10 @@ struct Cfg {
     static_assert((2 * kStages + 2 * kAcc + 3) * 8 + 12 <= 256, "barriers and flags fit their 256-byte region");
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
     static_assert(KC == 1 || (KC == 2 && MT == 1 && (BNC <= 128 || PAIR)), "two-chunk stages: 128-row tiles");
-    static_assert(!PAIR || (MT == 1 && !SP && !MX && BNC == BN_MAX && KC == 2), "CTA pairs: dense 256 x 256 tiles");
+    static_assert(!PAIR || (MT == 1 && !SP && BNC == BN_MAX && KC == 2), "CTA pairs: dense 256 x 256 tiles");
     static_assert(kBChunk % 1024 == 0, "B chunks stay swizzle-atom aligned");
-    static_assert(!MX || (MT == 1 && !SP && (BNC == 128 || (BNC == BN_MAX && KC == 1))),
-                  "block-scaled launches: 128-row dense tiles, 128 or 256 wide");
+    static_assert(!MX || (MT == 1 && !SP && (BNC == 128 || (BNC == BN_MAX && (KC == 1 || PAIR)))),
+                  "block-scaled launches: 128-row dense tiles, 128 or 256 wide, or CTA pairs");
     static_assert(!MX || kSfCol0 + kSfCols * kStages * KC <= (kAcc == 1 ? TMEM_COLS : BN_MAX),
                   "scale ring fits beside the accumulators");
 };
@@ -192,7 +194,9 @@ struct ProblemScalars {
 struct Problem : ProblemScalars {
     CUtensorMap tmP;        // P [rows_p, K] codes, box {128, 128 * MT}
     CUtensorMap tmQ;        // Q [rows_q, K] codes, box {128, bn}
-    CUtensorMap tmE;        // sparse only: metadata [rows_p, K/8], box {16, 128 * MT}
+    CUtensorMap tmE;        // sparse: metadata [rows_p, K/8], box {16, 128 * MT}; block-scaled CTA
+                            // pairs: P's scale chunks [chunks][32][16 bytes], box {16, 32, KC}
+    CUtensorMap tmSFQ;      // block-scaled CTA pairs: Q's scale chunks, as tmE
     CUtensorMap tmC;        // C [rows_p, rows_q] (row stride ldc), box {128 bytes, 32 rows}, 128-byte swizzle
 };
 
@@ -716,11 +720,13 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                 const bool first = tile == tile0;
                 const ProblemScalars P = first ? P_first : prm.prob[tc.p];
                 const int sf_q_tiles = MX ? (P.rows_q + BM - 1) / BM : 0;     // B's 128-row scale tiles
-                if (!first || P.sparse) {
+                if (!first || P.sparse || (PAIR && MX)) {
                     tma_prefetch_desc(&prm.prob[tc.p].tmP);
                     tma_prefetch_desc(&prm.prob[tc.p].tmQ);
-                    if (P.sparse)
+                    if (P.sparse || (PAIR && MX))
                         tma_prefetch_desc(&prm.prob[tc.p].tmE);
+                    if (PAIR && MX)
+                        tma_prefetch_desc(&prm.prob[tc.p].tmSFQ);
                 }
                 const CUtensorMap* map_p = &prm.prob[tc.p].tmP;
                 const CUtensorMap* map_q = &prm.prob[tc.p].tmQ;
@@ -747,9 +753,22 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                         const uint32_t fb = rank == 0 ? full_bar(stage) : cluster_map(full_bar(stage), 0u);
                         const int prow0 = tc.m_blk * 2 * BM + BM * static_cast<int>(rank);
                         const int pcol0 = tc.n_blk * P.bn + (BN_MAX / 2) * static_cast<int>(rank);
+                        // block-scaled: by TMA, completing on the same barrier, each
+                        // CTA's scale chunks of its 128 rows of A and of both 128-row
+                        // halves of the tile's B (KC k-blocks each)
                         if (rank == 0)
                             mbar_arrive_expect_tx(fb, 2u * static_cast<uint32_t>(C::kAChunk + C::kBChunk) *
-                                                          static_cast<uint32_t>(P.tma3d ? KC : nck));
+                                                              static_cast<uint32_t>(P.tma3d ? KC : nck) +
+                                                          (MX ? 2u * (1 + C::kSfQ) * KC * C::kSfChunk : 0u));
+                        if constexpr (MX) {
+                            const uint32_t sf = sa + C::kABytes + C::kBBytes;
+                            const int chunk_p = (tc.m_blk * 2 + static_cast<int>(rank)) * P.sf_kb + kb;
+                            tma_load_3d_pair(sf, &prm.prob[tc.p].tmE, fb, 0, 0, chunk_p);
+#pragma unroll
+                            for (int h = 0; h < C::kSfQ; ++h)
+                                tma_load_3d_pair(sf + (1 + h) * KC * C::kSfChunk, &prm.prob[tc.p].tmSFQ, fb, 0, 0,
+                                                 (tc.n_blk * C::kSfQ + h) * P.sf_kb + kb);
+                        }
                         if (P.tma3d) {
                             tma_load_3d_pair(sa, map_p, fb, 0, prow0, kb);
                             tma_load_3d_pair(sa + C::kABytes, map_q, fb, 0, pcol0, kb);
@@ -904,10 +923,30 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                             // each CTA's 128 rows of A and of B sit at these offsets
                             const uint64_t adesc = sdesc_kmajor_sw128(sa + c * C::kAChunk);
                             const uint64_t bdesc_c = sdesc_kmajor_sw128(sa + C::kABytes + c * b_chunk);
+                            if constexpr (MX) {
+                                // both CTAs' scale chunks of k-block c -> their own
+                                // tensor memory: A's 4 ring columns (the CTA's rows),
+                                // then B's 8 (all 256 rows of the tile)
+                                const uint32_t sf_col =
+                                    static_cast<uint32_t>(C::kSfCol0 + C::kSfCols * (stage * KC + c));
+                                const uint32_t sm_sf = sa + C::kABytes + C::kBBytes + c * C::kSfChunk;
+                                tmem_cp_32x128b_warpx4_pair(tmem_base + sf_col, sdesc_rows16_noswizzle(sm_sf));
 #pragma unroll
-                            for (int k = 0; k < BK / 32; ++k)
-                                mma_f8f6f4_pair(d_tmem, adesc + 2u * k, bdesc_c + 2u * k, idesc,
-                                                (first | c | k) != 0 ? 1u : 0u);
+                                for (int h = 0; h < C::kSfQ; ++h)
+                                    tmem_cp_32x128b_warpx4_pair(
+                                        tmem_base + sf_col + 4u * (1 + h),
+                                        sdesc_rows16_noswizzle(sm_sf + (1 + h) * KC * C::kSfChunk));
+#pragma unroll
+                                for (int k = 0; k < BK / 32; ++k)
+                                    mma_mx_f8f6f4_pair(d_tmem, adesc + 2u * k, bdesc_c + 2u * k,
+                                                       mx_sf_ids(idesc, static_cast<uint32_t>(k)), tmem_base + sf_col,
+                                                       tmem_base + sf_col + 4u, (first | c | k) != 0 ? 1u : 0u);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < BK / 32; ++k)
+                                    mma_f8f6f4_pair(d_tmem, adesc + 2u * k, bdesc_c + 2u * k, idesc,
+                                                    (first | c | k) != 0 ? 1u : 0u);
+                            }
                         }
                         // the stage is free in both CTAs once these MMAs are done
                         mma_commit_pair_multicast(empty_bar(stage), 0x3);
@@ -1252,6 +1291,24 @@ bool make_map3(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, i
     return r == CUDA_SUCCESS;
 }
 
+// 3-D map over block-scale chunks viewed as [chunks][32][16 bytes] (the
+// tiled layout: 512 bytes per 128 rows x one k-block); box {16, 32, kc}
+// lands kc consecutive chunks as the contiguous bytes a bulk copy would.
+bool make_sf_map(CUtensorMap* map, const void* base, int64_t chunks, int kc)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return false;
+    cuuint64_t dims[3] = {16, 32, static_cast<cuuint64_t>(chunks)};
+    cuuint64_t strides[2] = {16, 512};
+    cuuint32_t box[3] = {16, 32, static_cast<cuuint32_t>(kc)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // N of the MMA tile for a problem of rows_p x rows_q: the smallest of
 // {16, 32, 64, 128, 256} covering rows_q, then halved (down to 64) while the
 // problem has fewer 128-row tiles than half the SMs, so small problems still
@@ -1454,10 +1511,15 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
     pr.splits = (pr.k_blocks + pr.kb_per_split - 1) / pr.kb_per_split;     // no empty slice
     pr.idesc = idesc_f8_f32(pair ? 2 * BM : BM, bn, pr.sparse != 0, 0, mma_format(j.fmt_p), mma_format(j.fmt_q));
     if (j.sfp) {
-        pr.idesc = idesc_mx_f8(BM, bn, mma_format(j.fmt_p), mma_format(j.fmt_q));
+        pr.idesc = idesc_mx_f8(pair ? 2 * BM : BM, bn, mma_format(j.fmt_p), mma_format(j.fmt_q));
         pr.sfp = j.sfp;
         pr.sfq = j.sfq;
         pr.sf_kb = pr.k_blocks;
+        // pairs load the scale chunks by TMA (their copies complete on the
+        // even CTA's barrier); chunks past the arrays read as zeros
+        if (pair && (!make_sf_map(&pr.tmE, j.sfp, ((j.rows_p + BM - 1) / BM) * pr.sf_kb, kc) ||
+                     !make_sf_map(&pr.tmSFQ, j.sfq, ((j.rows_q + BM - 1) / BM) * pr.sf_kb, kc)))
+            return FP8_ERR_CUDA;
     }
     return FP8_OK;
 }
@@ -1703,7 +1765,7 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
     TileChoice c;
     if (expl && expl->mt) {
         c = *expl;
-        bool pair_ok = n > 0 && jobs[0].sfp == nullptr && (c.bn_cap == 0 || c.bn_cap >= BN_MAX) &&
+        bool pair_ok = n > 0 && (jobs[0].sfp == nullptr || n == 1) && (c.bn_cap == 0 || c.bn_cap >= BN_MAX) &&
                        (max_ctas <= 0 || max_ctas >= 2);
         for (int i = 0; i < n; ++i)
             pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
@@ -1724,7 +1786,7 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
         }
         // CTA pairs (mt 3) take dense problems whose N tiles are 256 wide,
         // in launches allowed two CTAs or more
-        bool pair_ok = n > 0 && jobs[0].sfp == nullptr && (c.bn_cap == 0 || c.bn_cap >= BN_MAX) &&
+        bool pair_ok = n > 0 && (jobs[0].sfp == nullptr || n == 1) && (c.bn_cap == 0 || c.bn_cap >= BN_MAX) &&
                        (max_ctas <= 0 || max_ctas >= 2);
         for (int i = 0; i < n; ++i)
             pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
@@ -1754,7 +1816,8 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
             c.mt = ok2 && (2 * tiles2 >= sms || pair_fill) ? (pair_ok ? 3 : 2) : 1;
         }
     }
-    if (mixed_kinds(jobs, n) || (n > 0 && jobs[0].sfp != nullptr))
+    // block-scaled launches: CTA pairs or 128-row tiles
+    if (mixed_kinds(jobs, n) || (n > 0 && jobs[0].sfp != nullptr && c.mt != 3))
         c.mt = 1;
     if (c.group_m <= 0) {
         // Each wave of concurrent tiles re-reads its band's P rows and its Q
@@ -1809,6 +1872,8 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
         // block-scaled launches (single problems): 128 x 256 tiles (one
         // accumulator, the scale ring after it) or 128 x 128 tiles (two)
         if constexpr (MAXP == 1) {
+            if (c.mt == 3)
+                return plan<MAXP, 1, false, BN_MAX, 2, true, true>(prm, max_ctas, pl);
             if (max_bn > 128)
                 return plan<MAXP, 1, false, BN_MAX, 1, true>(prm, max_ctas, pl);
             return kc == 2 ? plan<MAXP, 1, false, 128, 2, true>(prm, max_ctas, pl)
@@ -2152,6 +2217,14 @@ int run_jobs(Params<MAXP>& prm, const Job* jobs, const int* bns, int n, int max_
     return launch_split(prm, pl, st);
 }
 
+// N width of a block-scaled launch: 256 (CTA pairs, or 128 x 256 tiles with
+// two 128-row scale chunks of B per k-block) where the problem has enough
+// tiles for it, else 128.
+int mx_tile_width(const Job& j)
+{
+    return pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX) == BN_MAX ? BN_MAX : 128;
+}
+
 // Map a user-level GEMM (A [M,K], B [N,K], C [M,N] or C^T) onto (P, Q)
 // roles.  A dense product with small M puts A on the MMA N side (Q = A,
 // P = B) and writes the output transposed back; a sparse A always stays on
@@ -2220,27 +2293,16 @@ extern "C" int gemm_fp8_dense_fmt(int64_t M, int64_t N, int64_t K, const uint8_t
     return run_jobs(prm, &j, &bn, 1, 0, st, nullptr, true);
 }
 
-extern "C" int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info* info)
+namespace gb300 {
+namespace {
+
+// The plan of one job, as its entry point would launch it, into `info`.
+int describe_plan(const Job& j, int bn, bool allow_cluster, int64_t M, int64_t N, fp8_gemm_plan_info* info)
 {
-    using namespace gb300;
-    if (!info || M <= 0 || N <= 0 || K <= 0 || (out_dtype != 0 && out_dtype != 1))
-        return FP8_ERR_INVALID;
-    if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
-        return FP8_ERR_SHAPE;
-    if (!device_supported())
-        return FP8_ERR_UNSUPPORTED;
-    // tensor maps are encoded (never dereferenced) for an aligned stand-in
-    // address; the plan depends on the sizes only
-    const uint8_t* fake = reinterpret_cast<const uint8_t*>(uintptr_t(1) << 20);
-    const int64_t ld = (K + 15) / 16 * 16;
-    const float* one = device_one();
-    Job j = make_job(M, N, K, fake, ld, nullptr, fake, ld, one, 0, one, 0, 1.0f, const_cast<uint8_t*>(fake),
-                     N, out_dtype, 0, FP8_E4M3, FP8_E4M3);
-    const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     Plan pl;
-    const int rc = build_plan(prm, &j, &bn, 1, 0, nullptr, &pl, true);
+    const int rc = build_plan(prm, &j, &bn, 1, 0, nullptr, &pl, allow_cluster);
     if (rc != FP8_OK)
         return rc;
     const ProblemScalars& P = prm.prob[0];
@@ -2255,6 +2317,54 @@ extern "C" int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtyp
     info->group_m = prm.group_m;
     info->workspace_bytes = workspace_bytes(pl);
     return FP8_OK;
+}
+
+int check_plan_args(int64_t M, int64_t N, int64_t K, int out_dtype, const fp8_gemm_plan_info* info)
+{
+    if (!info || M <= 0 || N <= 0 || K <= 0 || (out_dtype != 0 && out_dtype != 1))
+        return FP8_ERR_INVALID;
+    if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
+        return FP8_ERR_SHAPE;
+    if (!device_supported() || !device_one())
+        return FP8_ERR_UNSUPPORTED;
+    return FP8_OK;
+}
+
+}  // namespace
+}  // namespace gb300
+
+extern "C" int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info* info)
+{
+    using namespace gb300;
+    const int rc = check_plan_args(M, N, K, out_dtype, info);
+    if (rc != FP8_OK)
+        return rc;
+    // tensor maps are encoded (never dereferenced) for an aligned stand-in
+    // address; the plan depends on the sizes only
+    const uint8_t* fake = reinterpret_cast<const uint8_t*>(uintptr_t(1) << 20);
+    const int64_t ld = (K + 15) / 16 * 16;
+    const float* one = device_one();
+    Job j = make_job(M, N, K, fake, ld, nullptr, fake, ld, one, 0, one, 0, 1.0f, const_cast<uint8_t*>(fake),
+                     N, out_dtype, 0, FP8_E4M3, FP8_E4M3);
+    return describe_plan(j, pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX), true, M, N, info);
+}
+
+extern "C" int gemm_fp8_mx_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info* info)
+{
+    using namespace gb300;
+    int rc = check_plan_args(M, N, K, out_dtype, info);
+    if (rc != FP8_OK)
+        return rc;
+    if (K % 32 != 0)
+        return FP8_ERR_SHAPE;
+    const uint8_t* fake = reinterpret_cast<const uint8_t*>(uintptr_t(1) << 20);
+    const int64_t ld = (K + 15) / 16 * 16;
+    const float* one = device_one();
+    Job j = make_job(M, N, K, fake, ld, nullptr, fake, ld, one, 0, one, 0, 1.0f, const_cast<uint8_t*>(fake),
+                     N, out_dtype, 0, FP8_E4M3, FP8_E4M3);
+    j.sfp = fake;
+    j.sfq = fake;
+    return describe_plan(j, mx_tile_width(j), false, M, N, info);
 }
 
 // ---------------------------------------------------------------- no-allocation variant
@@ -2375,9 +2485,7 @@ extern "C" int gemm_fp8_mx(int64_t M, int64_t N, int64_t K, const uint8_t* A, in
     const bool swapped = M <= 128 && N > M;          // make_job's rule for small-M dense products
     j.sfp = swapped ? b_scales : a_scales;
     j.sfq = swapped ? a_scales : b_scales;
-    // 256-wide tiles (two 128-row scale tiles of B per k-block) where the
-    // problem has enough tiles for them, else 128-wide
-    const int bn = pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX) == BN_MAX ? BN_MAX : 128;
+    const int bn = mx_tile_width(j);
     Params<1> prm;
     memset(&prm, 0, sizeof(prm));
     return run_jobs(prm, &j, &bn, 1, 0, st);

@@ -431,6 +431,30 @@ __device__ __forceinline__ void mma_f8f6f4_pair(uint32_t d_tmem, uint64_t adesc,
         : "memory");
 }
 
+// Block-scaled MMA of a CTA pair (M = 256 over the two CTAs): each CTA's
+// tensor memory holds the scale factors of its own 128 rows of A at
+// sfa_tmem and of all N rows of B from sfb_tmem (row r in column r / 32,
+// the layout of mma_mx_f8f6f4).
+__device__ __forceinline__ void mma_mx_f8f6f4_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                                   uint32_t idesc, uint32_t sfa_tmem, uint32_t sfb_tmem,
+                                                   uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa_tmem), "r"(sfb_tmem), "r"(accumulate)
+        : "memory");
+}
+
+// As tmem_cp_32x128b_warpx4 for a CTA pair: each CTA's shared memory at the
+// descriptor's offset goes to its own tensor memory at taddr.
+__device__ __forceinline__ void tmem_cp_32x128b_warpx4_pair(uint32_t taddr, uint64_t sdesc)
+{
+    asm volatile("tcgen05.cp.cta_group::2.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
 // Arrive once on the mbarrier at shared-memory offset `bar` of every CTA in
 // cta_mask (cluster ranks) when the pair's tcgen05 operations issued so far
 // by this thread have completed.

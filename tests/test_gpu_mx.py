@@ -196,6 +196,13 @@ def test_mx_large_blocks(gb, orc):
 WIDE = [(4096, 1024, 256), (4096, 1000, 640), (4096, 800, 1024)]
 
 
+def test_mx_wide_tiles_are_planned(gb):
+    for M, N, K in WIDE:
+        info = gb.gemm_fp8_mx_plan(M, N, K)
+        assert info["mt"] == 1 and info["bn"] == 256 and info["cluster"] == 0, (M, N, K, info)
+    assert gb.gemm_fp8_mx_plan(1024, 1024, 1024)["bn"] == 128
+
+
 @pytest.mark.parametrize("case", ["a_rows", "a_blocks", "b_cols", "b_blocks"])
 def test_mx_wide_tiles_structured_scales(gb, orc, case):
     M, N, K = 4096, 1024, 256
@@ -238,6 +245,69 @@ def test_mx_wide_tiles_normal_inputs(gb, orc, M, N, K):
     A, SA = orc.mx_quantize(x, 0)
     B, SB = orc.mx_quantize(w, 0)
     rows = np.r_[0:128, M - 256:M]
+    ref = orc.gemm_mx(A[rows], SA[rows], B, SB, alpha=0.5)
+    C = _gemm(gb, A, SA, B, SB, alpha=0.5, out_dtype=0)
+    parity.check_fp32(C[rows], ref)
+    Cb = _gemm(gb, A, SA, B, SB, alpha=0.5, out_dtype=1)
+    S = orc.gemm_mx(parity.abs_codes(A[rows]), SA[rows], parity.abs_codes(B), SB, alpha=0.5)
+    parity.check_bf16(Cb[rows], ref, S, K)
+
+
+# CTA pairs (256 x 256 tiles over two CTAs, each holding its 128 rows of A
+# and of B, their scale chunks loaded by TMA into each CTA's tensor memory):
+# problems whose 256-row tiles fill the SMs.  Ragged N and M put part of the
+# odd CTA's half outside B or A.
+PAIRS = [(4096, 2048, 256), (4096, 2000, 640), (4000, 2048, 1024)]
+
+
+def test_mx_pairs_are_planned(gb):
+    for M, N, K in PAIRS + [(8192, 8192, 8192)]:
+        info = gb.gemm_fp8_mx_plan(M, N, K)
+        assert info["mt"] == 3 and info["bn"] == 256 and info["cluster"] == 2, (M, N, K, info)
+
+
+@pytest.mark.parametrize("case", ["a_rows", "a_blocks", "b_cols", "b_blocks"])
+def test_mx_pairs_structured_scales(gb, orc, case):
+    M, N, K = PAIRS[0]
+    A = np.full((M, K), ONE, np.uint8)
+    B = np.full((N, K), ONE, np.uint8)
+    SA = np.full((M, K // 32), 127, np.uint8)
+    SB = np.full((N, K // 32), 127, np.uint8)
+    if case == "a_rows":
+        SA += ((np.arange(M) // 32) % 8).astype(np.uint8)[:, None]
+    elif case == "a_blocks":
+        SA += (np.arange(K // 32) % 8).astype(np.uint8)[None, :]
+    elif case == "b_cols":
+        SB += ((np.arange(N) // 32) % 8).astype(np.uint8)[:, None]
+    else:
+        SB += (np.arange(K // 32) % 8).astype(np.uint8)[None, :]
+    C = _gemm(gb, A, SA, B, SB)
+    rows = np.r_[0:288, M - 160:M]
+    ref = orc.gemm_mx(A[rows], SA[rows], B, SB)
+    assert np.array_equal(C[rows].astype(np.float64), ref), (C[rows][::32, ::32], ref[::32, ::32])
+
+
+@pytest.mark.parametrize("fmt", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K", PAIRS)
+def test_mx_pairs_small_integers_bit_exact(gb, orc, fmt, M, N, K):
+    A = workloads.small_int_codes((M, K), seed=M + K + 5, fmt=fmt[0])
+    B = workloads.small_int_codes((N, K), seed=N + K + 6, fmt=fmt[1])
+    g = np.random.default_rng(M + 2 * N + K)
+    SA = g.integers(127, 129, size=(M, K // 32)).astype(np.uint8)
+    SB = g.integers(126, 128, size=(N, K // 32)).astype(np.uint8)
+    C = _gemm(gb, A, SA, B, SB, fmt)
+    rows = np.r_[0:300, 1900:2100, M - 300:M]
+    ref = orc.gemm_mx(A[rows], SA[rows], B, SB, a_fmt=fmt[0], b_fmt=fmt[1])
+    assert np.array_equal(C[rows].astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("M,N,K", PAIRS)
+def test_mx_pairs_normal_inputs(gb, orc, M, N, K):
+    x = workloads.randn_f32((M, K), seed=M + 23)
+    w = workloads.randn_f32((N, K), seed=N + 24)
+    A, SA = orc.mx_quantize(x, 0)
+    B, SB = orc.mx_quantize(w, 0)
+    rows = np.r_[0:256, M - 256:M]
     ref = orc.gemm_mx(A[rows], SA[rows], B, SB, alpha=0.5)
     C = _gemm(gb, A, SA, B, SB, alpha=0.5, out_dtype=0)
     parity.check_fp32(C[rows], ref)
