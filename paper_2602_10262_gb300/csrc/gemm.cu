@@ -84,12 +84,13 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 // (2 KB each), then the B chunks: 4 / 5 / 7 / 8 stages for BNC = 128 / 64 /
 // 32 / 16, each k-block's metadata in its own 4 TMEM columns.  Launches
 // mixing dense and sparse problems, BNC = 256 and MT = 2 keep KC = 1.
-// MX: block-scaled launches (kind::mxf8f6f4): 128 x 128 or 128 x 256 tiles,
-// dense codes as above, and per k-block 512-byte chunks of E8M0 scales after
-// the B chunks (A's 128 rows, then B's, 128 rows per chunk), copied into a
-// ring of TMEM columns (per k-block A's 4, then 4 per 128 rows of B):
-// columns 128..255 beside the first of two accumulators for 128-wide tiles,
-// from column 256 after the single accumulator for 256-wide ones.
+// MX: block-scaled launches (kind::mxf8f6f4): 128 x 128 or 128 x 256 tiles
+// or CTA pairs, dense codes as above, and per k-block 512-byte chunks of
+// E8M0 scales after the B chunks (A's 128 rows, then B's, 128 rows per
+// chunk; a pair's CTA holds all 256 rows of B's), copied into a ring of
+// TMEM columns (per k-block A's 4, then 4 per 128 rows of B): columns
+// 128..255 beside the first of two accumulators for 128-wide tiles, from
+// column 256 after the single accumulator for 256-wide ones and pairs.
 // PAIR: CTA-pair launches (cta_group::2, clusters of two): a 256 x 256 tile
 // per pair, each CTA loading its 128 rows of A and 128 rows of B (two
 // k-blocks per stage, three 64 KB stages) and holding its 128 x 256 half of
@@ -612,8 +613,8 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     const int lane = threadIdx.x & 31;
     grid_launch_dependents();
     // a launch whose cluster shape does not match its plan (pairs need
-    // clusters of two, cluster split-K one CTA per slice) does nothing: no
-    // CTA addresses a peer that is not there
+    // clusters of two, cluster split-K one CTA per slice, B multicast its
+    // group) does nothing: no CTA addresses a peer that is not there
     const int mc = PAIR || MX || SP || MT != 1 ? 0 : prm.mc;
     if ((PAIR ? 2u
               : (prm.cluster_split > 0 ? static_cast<uint32_t>(prm.cluster_split)
@@ -1806,7 +1807,7 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
             // 256-row tiles load a third fewer bytes per MMA; take them
             // while they still give at least half the SMs a tile, on CTA
             // pairs where the launch allows them (measured: the tensor pipe
-            // 85 % busy at 8192^3 against 75 % for one-CTA 256-row tiles).
+            // 88 % busy at 8192^3 against 75 % for one-CTA 256-row tiles).
             // Pairs also where they occupy as many SMs as 128-row tiles
             // would and K is long enough for the k-loop to dominate
             // (512 x 8192 x 8192: 29.4 us against 32.5 us; at K = 2048 the
@@ -1869,8 +1870,9 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
     prm.num_problems = n;
     prm.group_m = c.group_m;
     if (n > 0 && jobs[0].sfp != nullptr) {
-        // block-scaled launches (single problems): 128 x 256 tiles (one
-        // accumulator, the scale ring after it) or 128 x 128 tiles (two)
+        // block-scaled launches (single problems): CTA pairs or 128 x 256
+        // tiles (one accumulator, the scale ring after it) or 128 x 128
+        // tiles (two)
         if constexpr (MAXP == 1) {
             if (c.mt == 3)
                 return plan<MAXP, 1, false, BN_MAX, 2, true, true>(prm, max_ctas, pl);
