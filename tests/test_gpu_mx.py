@@ -314,3 +314,29 @@ def test_mx_pairs_normal_inputs(gb, orc, M, N, K):
     Cb = _gemm(gb, A, SA, B, SB, alpha=0.5, out_dtype=1)
     S = orc.gemm_mx(parity.abs_codes(A[rows]), SA[rows], parity.abs_codes(B), SB, alpha=0.5)
     parity.check_bf16(Cb[rows], ref, S, K)
+
+
+def test_mx_pairs_stalled_launch_times_out(gb):
+    """The failure path on block-scaled pairs: loads withheld, every wait
+    bounded (50 ms here), FP8_ERR_TIMEOUT recorded, C unwritten, and the
+    next launch exact."""
+    M, N, K = PAIRS[0]
+    A = workloads.small_int_codes((M, K), seed=41)
+    B = workloads.small_int_codes((N, K), seed=42)
+    SA = np.full((M, K // 32), 127, np.uint8)
+    SB = np.full((N, K // 32), 128, np.uint8)
+    ref = _gemm(gb, A, SA, B, SB)
+    At, Bt = _dev(A), _dev(B)
+    SAt, SBt = _dev(tiled_layout(SA, M, K)), _dev(tiled_layout(SB, N, K))
+    C = torch.full((M, N), float("nan"), device="cuda")
+    gb.fp8_test_stall_gemm_loads(1, 50.0)
+    try:
+        gb.gemm_fp8_mx(At, SAt, Bt, SBt, 1.0, gb.OUT_F32, C=C)
+        assert gb.fp8_last_device_error() == -7
+    finally:
+        gb.fp8_test_stall_gemm_loads(0, 0.0)
+    assert torch.isnan(C).all()
+    gb.gemm_fp8_mx(At, SAt, Bt, SBt, 1.0, gb.OUT_F32, C=C)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    assert np.array_equal(C.cpu().numpy(), ref)
