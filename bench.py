@@ -1063,6 +1063,30 @@ def mx_sweep(gb, dev):
     return rows
 
 
+def mx_quant_sweep(gb, dev):
+    """Quantisers alone: per-row E4M3 against block-scaled (tiled and
+    row-major scale layouts), device time per call with L2-cold rotation;
+    GB/s counts 4 bytes read and 1 written per element."""
+    rows = []
+    for R, C in ((4096, 4096), (8192, 8192), (16384, 8192)):
+        n = _l2_copies(dev, R * C * 4)
+        xs = [torch.randn((R, C), generator=torch.Generator(device=dev).manual_seed(300 + i), device=dev)
+              for i in range(n)]
+        q = torch.empty((R, C), dtype=torch.uint8, device=dev)
+        d = torch.empty(R, device=dev)
+        st = torch.empty(gb.fp8_mx_scale_tiled_bytes(R, C), dtype=torch.uint8, device=dev)
+        sr = torch.empty((R, C // 32), dtype=torch.uint8, device=dev)
+        ms_row = _time_ms([lambda x=x: gb.fp8_quantize_e4m3(x, 1, q, d) for x in xs])
+        ms_t = _time_ms([lambda x=x: gb.fp8_quantize_mx(x, gb.E4M3, 1, q, st) for x in xs])
+        ms_r = _time_ms([lambda x=x: gb.fp8_quantize_mx(x, gb.E4M3, 0, q, sr) for x in xs])
+        b = R * C * 5
+        rows.append({"rows": R, "cols": C, "per_row_us": ms_row * 1e3, "per_row_gbs": b / ms_row / 1e6,
+                     "mx_tiled_us": ms_t * 1e3, "mx_tiled_gbs": b / ms_t / 1e6,
+                     "mx_row_major_us": ms_r * 1e3, "mx_row_major_gbs": b / ms_r / 1e6, "copies": n})
+        del xs
+    return rows
+
+
 def pair_sweep(gb, dev):
     """Dense GEMMs on CTA-pair tiles (mt 3, tcgen05 cta_group::2, 256 x 256
     per SM pair) against one-CTA 256-row tiles (mt 2) and 128-row tiles
@@ -1193,7 +1217,7 @@ def serving_policy_sweep(gb, dev, n=20000, load=0.8):
     return out
 
 
-SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency", "mx",
+SWEEP_SECTIONS = ("shapes", "formats", "occupancy", "aspect", "serving", "concurrency", "mx", "mx_quant",
                   "serving_policy", "served_concurrency", "pair", "raster", "prune")
 
 
@@ -1216,6 +1240,8 @@ def sweep(gb, dev, sections=SWEEP_SECTIONS):
         out["concurrency"] = concurrency_sweep(gb, dev)
     if "mx" in sections:
         out["mx"] = mx_sweep(gb, dev)
+    if "mx_quant" in sections:
+        out["mx_quant"] = mx_quant_sweep(gb, dev)
     if "serving_policy" in sections:
         out["serving_policy"] = serving_policy_sweep(gb, dev)
     if "served_concurrency" in sections:
