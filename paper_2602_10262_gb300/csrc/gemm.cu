@@ -47,6 +47,7 @@ constexpr int BN_MAX = 256;
 constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M_DEFAULT = 16;       // raster: M-blocks per band
 constexpr int GROUP_M_PAIR_LARGE = 8;     // CTA-pair launches whose operands exceed L2
+constexpr int PREFETCH_STAGES = 2;        // first-tile stages prefetched into L2 at kernel entry
 // 2:4-sparse tiles: per stage the kept A codes (rows x 64 bytes, 64-byte
 // swizzle) and the metadata (rows x 16 bytes) fill the A region; the metadata
 // of each 128-row half is copied into a ring of TMEM columns beside that
@@ -646,6 +647,48 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     if (threadIdx.x == 0) {
         tma_prefetch_desc(&prm.prob[tc_first.p].tmP);
         tma_prefetch_desc(&prm.prob[tc_first.p].tmQ);
+    }
+    // The operand boxes of the first tile's first stages are prefetched into
+    // L2 now, by an epilogue warp (idle until the first accumulator is
+    // ready), so that the setup below and the dependency wait overlap their
+    // DRAM latency.  A prefetch only warms L2, which every later load reads
+    // through and which the hardware keeps coherent, so data the previous
+    // kernel writes after it is still what the loads return.  Coordinates
+    // are those of the producer's loads below (block scales are not
+    // prefetched).
+    if (warp == 2 && lane == 0 && tile0 < total_tiles && !prm.withhold_loads) {
+        const int bn = P_first.bn;
+        const int prow0 = PAIR ? tc_first.m_blk * 2 * BM + BM * static_cast<int>(rank) : tc_first.m_blk * BM * MT;
+        const int pcol0 = tc_first.n_blk * bn + (PAIR ? (BN_MAX / 2) * static_cast<int>(rank) : 0) +
+                          (mc > 0 ? qrank * (bn / (mc > 0 ? mc : 1)) : 0);
+        const int kb0 = tc_first.slice * P_first.kb_per_split;
+        const int kb1 = min(min(P_first.k_blocks, kb0 + P_first.kb_per_split), kb0 + PREFETCH_STAGES * KC);
+        const CUtensorMap* map_p = &prm.prob[tc_first.p].tmP;
+        const CUtensorMap* map_q = &prm.prob[tc_first.p].tmQ;
+        const CUtensorMap* map_e = &prm.prob[tc_first.p].tmE;
+        const bool box3d = KC > 1 && P_first.tma3d;
+        for (int kb = kb0; kb < kb1; kb += KC) {
+            if (P_first.sparse) {
+                if (KC > 1) {
+                    tma_prefetch_l2_3d(map_p, 0, prow0, kb);
+                    tma_prefetch_l2_3d(map_e, 0, prow0, kb);
+                } else {
+                    tma_prefetch_l2_2d(map_p, kb * (BK / 2), prow0);
+                    tma_prefetch_l2_2d(map_e, kb * (BK / 8), prow0);
+                }
+            } else if (box3d) {
+                tma_prefetch_l2_3d(map_p, 0, prow0, kb);
+            } else {
+                for (int c = 0; c < KC && kb + c < kb1; ++c)
+                    tma_prefetch_l2_2d(map_p, (kb + c) * BK, prow0);
+            }
+            if (box3d && mc == 0) {
+                tma_prefetch_l2_3d(map_q, 0, pcol0, kb);
+            } else {
+                for (int c = 0; c < KC && kb + c < kb1; ++c)
+                    tma_prefetch_l2_2d(map_q, (kb + c) * BK, pcol0);
+            }
+        }
     }
 
     if (threadIdx.x == 0) {
