@@ -386,12 +386,15 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * tiles of one CTA: two MMAs share each B tile, a third fewer operand bytes
  * per FLOP), 3 (256 x 256 tiles of a CTA pair, tcgen05 cta_group::2: each
  * CTA of a two-CTA cluster loads 128 rows of A and 128 rows of B and holds
- * its half of the accumulator; dense launches whose N tiles are 256 wide,
- * otherwise as 0), 0 = chosen per launch (256-row tiles when every problem
- * fills them with N tiles >= 128 wide and those tiles number at least half
- * the SMs, or, for CTA pairs with K >= 4096, occupy as many SMs as 128-row
- * tiles would: 3 when the problems are dense with 256-wide N tiles, else 2;
- * a launch mixing dense and sparse problems always uses 1).
+ * its half of the accumulator; 2:4 launches take 256 x 224 pair tiles,
+ * each CTA loading the kept codes and metadata of its 128 rows of A and
+ * 112 rows of B; dense launches whose N tiles are 256 wide and 2:4 launches
+ * whose N tiles are at least 224 wide, otherwise as 0), 0 = chosen per
+ * launch (256-row tiles when every problem fills them with N tiles >= 128
+ * wide and those tiles number at least half the SMs, or, for CTA pairs
+ * with K >= 4096, occupy as many SMs as 128-row tiles would: 3 when pairs
+ * apply as above, else 2; a launch mixing dense and sparse problems always
+ * uses 1).
  * group_m: M-blocks per raster band (0 = 16, or 8 for CTA-pair launches
  * whose operands exceed the L2 cache).  Results do not depend on
  * either.  Affects launches enqueued after the call, from any thread. */
@@ -432,10 +435,18 @@ int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm
  * mt 1 with bn 256 or 128 (128-row tiles).  FP8_ERR_SHAPE unless K % 32 == 0. */
 int gemm_fp8_mx_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info *info);
 
+/* How gemm_fp8_sparse24 would run an M x N x K 2:4 problem now: mt 3 (CTA
+ * pairs, 256 x 224 tiles, two accumulators per CTA), mt 2 (256-row tiles of
+ * one CTA, N <= 224) or mt 1 (128-row tiles).  A is always the sparse side
+ * (swapped = 0).  FP8_ERR_SHAPE unless K % 128 == 0.  Paper: section 6 (2:4
+ * sparse GEMM against dense on the same operands). */
+int gemm_fp8_sparse24_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info *info);
+
 /* Autotuner: times every candidate tile configuration of this exact problem
  * list on `stream` (iters timed launches each, after one warm-up; the
  * problems' outputs are written each time): tile kind mt in {1, 2, 3} (3 only
- * for dense lists whose N tiles are 256 wide), raster band group_m in {2, 4,
+ * for dense lists whose N tiles are 256 wide and 2:4 lists whose N tiles are
+ * at least 224 wide), raster band group_m in {2, 4,
  * 8, 16, 32}, and for 128-row tiles a cap of 128 or 64 on the N tile width
  * (which also selects the pipeline ring: two k-blocks per stage up to 128
  * wide).  K splits stay as the problems fix them, so no candidate changes a

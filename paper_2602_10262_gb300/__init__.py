@@ -24,7 +24,7 @@ __all__ = [
     "gemm_fp8_grouped_autotune",
     "gemm_fp8_tune_cache_save", "gemm_fp8_tune_cache_load", "gemm_fp8_tune_cache_clear",
     "GroupedGraph", "OUT_F32", "OUT_BF16", "E4M3", "E5M2", "fp8_quantize_mx", "fp8_mx_scales_to_tiled",
-    "fp8_mx_scale_tiled_bytes", "gemm_fp8_mx", "gemm_fp8_dense_plan", "gemm_fp8_mx_plan",
+    "fp8_mx_scale_tiled_bytes", "gemm_fp8_mx", "gemm_fp8_dense_plan", "gemm_fp8_mx_plan", "gemm_fp8_sparse24_plan",
 ]
 
 OUT_F32 = 0
@@ -132,9 +132,19 @@ def gemm_fp8_mx_plan(M: int, N: int, K: int, out_dtype: int = OUT_BF16) -> dict:
     return {name: getattr(info, name) for name, _ in info._fields_}
 
 
+def gemm_fp8_sparse24_plan(M: int, N: int, K: int, out_dtype: int = OUT_BF16) -> dict:
+    """How gemm_fp8_sparse24 would run a 2:4 [M, K] x [N, K]^T product now
+    (fields as gemm_fp8_dense_plan), without launching."""
+    info = _lib.FP8PlanInfo()
+    _check(library().gemm_fp8_sparse24_plan(int(M), int(N), int(K), int(out_dtype), ctypes.byref(info)),
+           "gemm_fp8_sparse24_plan")
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
 def fp8_gemm_set_tile_config(mt: int = 0, group_m: int = 0) -> None:
-    """Force the GEMM tile shape (mt 1 or 2 row-halves per tile, raster band
-    height group_m); 0 restores the per-launch choice."""
+    """Force the GEMM tile shape (mt 1 or 2 row-halves per tile of one CTA,
+    3 CTA-pair tiles; raster band height group_m); 0 restores the per-launch
+    choice."""
     _check(library().fp8_gemm_set_tile_config(int(mt), int(group_m)), "fp8_gemm_set_tile_config")
 
 

@@ -111,6 +111,7 @@ SIGNATURES = {
     "fp8_gemm_set_tile_config": (I32, [I32, I32]),
     "gemm_fp8_dense_plan": (I32, [I64, I64, I64, I32, ctypes.POINTER(FP8PlanInfo)]),
     "gemm_fp8_mx_plan": (I32, [I64, I64, I64, I32, ctypes.POINTER(FP8PlanInfo)]),
+    "gemm_fp8_sparse24_plan": (I32, [I64, I64, I64, I32, ctypes.POINTER(FP8PlanInfo)]),
     "fp8_gemm_set_multicast": (I32, [I32]),
     "gemm_fp8_grouped_autotune": (I32, [ctypes.POINTER(FP8Problem), I32, I32, I32, P,
                                         ctypes.POINTER(FP8TileConfig)]),

@@ -104,7 +104,7 @@ template <int MT, bool SP = false, int BNC = BN_MAX, int KC = 1, bool MX = false
 struct Cfg {
     static constexpr bool kSparse2 = MT == 2 && SP;
     static constexpr int kStages =
-        PAIR ? 3 :
+        PAIR ? (SP ? 4 : 3) :
         KC == 2 ? (SP ? (BNC == 128 ? 4 : (BNC == 64 ? 5 : (BNC == 32 ? 7 : 8)))
                       : (BNC == 128 ? 3 : (BNC == 64 ? 4 : 5)))
                 : MT == 2 ? (SP ? 4 : 3)
@@ -137,7 +137,7 @@ struct Cfg {
     // epilogue warps: 4 per 128 rows (one per TMEM lane quarter); 256-wide
     // 128-row tiles (and pairs) use 8, two per lane quarter splitting the
     // columns, so each SM sub-partition has a second warp to hide latencies
-    static constexpr int kEpiSplit = (MT == 1 && BNC == BN_MAX && !MX) ? 2 : 1;
+    static constexpr int kEpiSplit = (MT == 1 && (BNC == BN_MAX || PAIR) && !MX) ? 2 : 1;
     static constexpr int kEpiWarps = 4 * MT * kEpiSplit;
     static constexpr int kThreads = 64 + 32 * kEpiWarps;         // producer, MMA, epilogue warps
     // staging buffers of 32 rows x 128 B per epilogue warp: two where they
@@ -147,7 +147,8 @@ struct Cfg {
     static constexpr int kEpiBufs = kSmemBase + 2 * kEpiWarps * 32 * 128 <= 232448 ? 2 : 1;
     static constexpr int kEpiBytes = kEpiBufs * kEpiWarps * 32 * 128;
     static constexpr int kSmem = kSmemBase + kEpiBytes;
-    static_assert(PAIR || kMetaCol0 + 4 * kStages * KC <= BN_MAX, "metadata ring must fit beside the accumulator");
+    static_assert((PAIR && !SP) || kMetaCol0 + 4 * kStages * KC <= BN_MAX,
+                  "metadata ring must fit beside the accumulator");
     static_assert(KC * (kSpChunk + kMetaChunk) <= kABytes || (MT == 2 && !SP),
                   "sparse A + metadata fit the A region");
     static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "swizzle atoms stay aligned");
@@ -155,7 +156,8 @@ struct Cfg {
     static_assert((2 * kStages + 2 * kAcc + 3) * 8 + 12 <= 256, "barriers and flags fit their 256-byte region");
     static_assert(MT == 1 || BNC == BN_MAX, "narrow rings are for 128-row tiles");
     static_assert(KC == 1 || (KC == 2 && MT == 1 && (BNC <= 128 || PAIR)), "two-chunk stages: 128-row tiles");
-    static_assert(!PAIR || (MT == 1 && !SP && BNC == BN_MAX && KC == 2), "CTA pairs: dense 256 x 256 tiles");
+    static_assert(!PAIR || (MT == 1 && KC == 2 && BNC == (SP ? SPARSE_BN_MAX_MT2 : BN_MAX)),
+                  "CTA pairs: dense 256 x 256 or 2:4 256 x 224 tiles");
     static_assert(kBChunk % 1024 == 0, "B chunks stay swizzle-atom aligned");
     static_assert(!MX || (MT == 1 && !SP && (BNC == 128 || (BNC == BN_MAX && (KC == 1 || PAIR)))),
                   "block-scaled launches: 128-row dense tiles, 128 or 256 wide, or CTA pairs");
@@ -659,7 +661,7 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
     if (warp == 2 && lane == 0 && tile0 < total_tiles && !prm.withhold_loads) {
         const int bn = P_first.bn;
         const int prow0 = PAIR ? tc_first.m_blk * 2 * BM + BM * static_cast<int>(rank) : tc_first.m_blk * BM * MT;
-        const int pcol0 = tc_first.n_blk * bn + (PAIR ? (BN_MAX / 2) * static_cast<int>(rank) : 0) +
+        const int pcol0 = tc_first.n_blk * bn + (PAIR ? (BNC / 2) * static_cast<int>(rank) : 0) +
                           (mc > 0 ? qrank * (bn / (mc > 0 ? mc : 1)) : 0);
         const int kb0 = tc_first.slice * P_first.kb_per_split;
         const int kb1 = min(min(P_first.k_blocks, kb0 + P_first.kb_per_split), kb0 + PREFETCH_STAGES * KC);
@@ -792,11 +794,12 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                     }
                     const uint32_t sa = smem_base + stage * C::kStageBytes;
                     if constexpr (PAIR) {
-                        // this CTA's 128 rows of A and 128 rows of B; both CTAs'
-                        // copies complete on the even CTA's barrier
+                        // this CTA's 128 rows of A and half of the tile's B rows
+                        // (2:4: kept codes and metadata of its 128 rows of A); both
+                        // CTAs' copies complete on the even CTA's barrier
                         const uint32_t fb = rank == 0 ? full_bar(stage) : cluster_map(full_bar(stage), 0u);
                         const int prow0 = tc.m_blk * 2 * BM + BM * static_cast<int>(rank);
-                        const int pcol0 = tc.n_blk * P.bn + (BN_MAX / 2) * static_cast<int>(rank);
+                        const int pcol0 = tc.n_blk * P.bn + (BNC / 2) * static_cast<int>(rank);
                         // block-scaled: by TMA, completing on the same barrier, each
                         // CTA's scale chunks of its 128 rows of A and of both 128-row
                         // halves of the tile's B (KC k-blocks each)
@@ -813,7 +816,12 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                                 tma_load_3d_pair(sf + (1 + h) * KC * C::kSfChunk, &prm.prob[tc.p].tmSFQ, fb, 0, 0,
                                                  (tc.n_blk * C::kSfQ + h) * P.sf_kb + kb);
                         }
-                        if (P.tma3d) {
+                        if constexpr (SP) {
+                            // kept codes of the KC k-blocks, then their metadata
+                            tma_load_3d_pair(sa, map_p, fb, 0, prow0, kb);
+                            tma_load_3d_pair(sa + KC * C::kSpChunk, map_e, fb, 0, prow0, kb);
+                            tma_load_3d_pair(sa + C::kABytes, map_q, fb, 0, pcol0, kb);
+                        } else if (P.tma3d) {
                             tma_load_3d_pair(sa, map_p, fb, 0, prow0, kb);
                             tma_load_3d_pair(sa + C::kABytes, map_q, fb, 0, pcol0, kb);
                         } else {
@@ -967,7 +975,20 @@ __global__ void __launch_bounds__(Cfg<MT, SP, BNC, KC, MX, PAIR>::kThreads, 1)
                             // each CTA's 128 rows of A and of B sit at these offsets
                             const uint64_t adesc = sdesc_kmajor_sw128(sa + c * C::kAChunk);
                             const uint64_t bdesc_c = sdesc_kmajor_sw128(sa + C::kABytes + c * b_chunk);
-                            if constexpr (MX) {
+                            if constexpr (SP) {
+                                // both CTAs' metadata of k-block c -> their own
+                                // tensor memory (each CTA's 128 rows), then the
+                                // M = 256 MMAs over logical K = 64 steps
+                                const uint32_t sm_meta = sa + KC * C::kSpChunk + c * C::kMetaChunk;
+                                const uint32_t mcol = static_cast<uint32_t>(C::kMetaCol0 + 4 * (stage * KC + c));
+                                tmem_cp_128x128b_pair(tmem_base + mcol, sdesc_rows16_noswizzle(sm_meta));
+                                const uint64_t sp_desc = sdesc_kmajor_sw64(sa + c * C::kSpChunk);
+#pragma unroll
+                                for (int k = 0; k < BK / 64; ++k)
+                                    mma_sp_f8f6f4_pair(d_tmem, sp_desc + 2u * k, bdesc_c + 4u * k,
+                                                       tmem_base + mcol + 2u * k, idesc,
+                                                       (first | c | k) != 0 ? 1u : 0u);
+                            } else if constexpr (MX) {
                                 // both CTAs' scale chunks of k-block c -> their own
                                 // tensor memory: A's 4 ring columns (the CTA's rows),
                                 // then B's 8 (all 256 rows of the tile)
@@ -1512,7 +1533,7 @@ int fill_problem(Problem& pr, const Job& j, int bn, int mt, int kc)
         // metadata in 16-byte chunks, B in 128-byte chunks
         if (!make_map3(&pr.tmP, j.P, j.rows_p, j.K / 2, j.K / 2, BK / 2, box_p, kc, CU_TENSOR_MAP_SWIZZLE_64B) ||
             !make_map3(&pr.tmE, j.E, j.rows_p, j.K / 8, j.K / 8, BK / 8, box_p, kc, CU_TENSOR_MAP_SWIZZLE_NONE) ||
-            !make_map3(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, bn, kc, CU_TENSOR_MAP_SWIZZLE_128B))
+            !make_map3(&pr.tmQ, j.Q, j.rows_q, j.K, j.ldq, BK, box_q, kc, CU_TENSOR_MAP_SWIZZLE_128B))
             return FP8_ERR_CUDA;
         pr.tma3d = 1;
     } else {
@@ -1795,6 +1816,23 @@ bool mixed_kinds(const Job* jobs, int n)
     return false;
 }
 
+// CTA pairs (mt 3) take launches allowed two CTAs or more whose problems are
+// all dense with 256-wide N tiles, or all 2:4-sparse with N tiles of at least
+// 224 (run 224 wide), and block-scaled launches of one problem.
+bool pairs_allowed(const Job* jobs, const int* bns, int n, int max_ctas, int bn_cap)
+{
+    if (n <= 0 || (jobs[0].sfp != nullptr && n != 1) || (max_ctas > 0 && max_ctas < 2))
+        return false;
+    bool dense = true, sparse = jobs[0].sfp == nullptr;
+    for (int i = 0; i < n; ++i) {
+        dense = dense && jobs[i].E == nullptr && bns[i] == BN_MAX;
+        sparse = sparse && jobs[i].E != nullptr && bns[i] >= SPARSE_BN_MAX_MT2;
+    }
+    if (dense)
+        return bn_cap == 0 || bn_cap >= BN_MAX;
+    return sparse && (bn_cap == 0 || bn_cap >= SPARSE_BN_MAX_MT2);
+}
+
 // Tile shape of a launch, in order of precedence: an explicit choice (the
 // autotuner's candidates), the process-wide override, the autotuner's cached
 // winner for this shape signature, the heuristic.  Heuristic: 256-row tiles
@@ -1809,10 +1847,7 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
     TileChoice c;
     if (expl && expl->mt) {
         c = *expl;
-        bool pair_ok = n > 0 && (jobs[0].sfp == nullptr || n == 1) && (c.bn_cap == 0 || c.bn_cap >= BN_MAX) &&
-                       (max_ctas <= 0 || max_ctas >= 2);
-        for (int i = 0; i < n; ++i)
-            pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
+        const bool pair_ok = pairs_allowed(jobs, bns, n, max_ctas, c.bn_cap);
         if (c.mt == 3 && !pair_ok)
             c.mt = 1;
     } else {
@@ -1828,12 +1863,7 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
                     c.group_m = it->second.group_m;
             }
         }
-        // CTA pairs (mt 3) take dense problems whose N tiles are 256 wide,
-        // in launches allowed two CTAs or more
-        bool pair_ok = n > 0 && (jobs[0].sfp == nullptr || n == 1) && (c.bn_cap == 0 || c.bn_cap >= BN_MAX) &&
-                       (max_ctas <= 0 || max_ctas >= 2);
-        for (int i = 0; i < n; ++i)
-            pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
+        const bool pair_ok = pairs_allowed(jobs, bns, n, max_ctas, c.bn_cap);
         if (c.mt == 3 && !pair_ok)
             c.mt = 0;
         if (c.mt == 0) {
@@ -1904,7 +1934,7 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
     const int kc = ((c.mt == 1 && max_bn <= 128 && (!any_sparse || all_sparse)) || c.mt == 3) ? 2 : 1;
     for (int i = 0; i < n; ++i) {
         int bn = bns[i];
-        if (c.mt == 2 && sparse)
+        if ((c.mt == 2 || c.mt == 3) && sparse)
             bn = std::min(bn, SPARSE_BN_MAX_MT2);
         int rc = fill_problem(prm.prob[i], jobs[i], bn, c.mt, kc);
         if (rc != FP8_OK)
@@ -1927,7 +1957,8 @@ int build_plan_tiles(Params<MAXP>& prm, const Job* jobs, const int* bns_in, int 
         return FP8_ERR_UNSUPPORTED;
     }
     if (c.mt == 3)
-        return plan<MAXP, 1, false, BN_MAX, 2, false, true>(prm, max_ctas, pl);
+        return sparse ? plan<MAXP, 1, true, SPARSE_BN_MAX_MT2, 2, false, true>(prm, max_ctas, pl)
+                      : plan<MAXP, 1, false, BN_MAX, 2, false, true>(prm, max_ctas, pl);
     if (c.mt == 1) {
         if (kc == 2 && all_sparse) {
             if (max_bn <= 16)
@@ -2394,6 +2425,23 @@ extern "C" int gemm_fp8_dense_plan(int64_t M, int64_t N, int64_t K, int out_dtyp
     return describe_plan(j, pick_bn(j.rows_p, j.rows_q, j.K, BN_MAX), true, M, N, info);
 }
 
+extern "C" int gemm_fp8_sparse24_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info* info)
+{
+    using namespace gb300;
+    const int rc = check_plan_args(M, N, K, out_dtype, info);
+    if (rc != FP8_OK)
+        return rc;
+    if (K % 128 != 0)
+        return FP8_ERR_SHAPE;
+    const uint8_t* fake = reinterpret_cast<const uint8_t*>(uintptr_t(1) << 20);
+    const float* one = device_one();
+    Job j = make_job(M, N, K, fake, K / 2, fake, fake, K, one, 0, one, 0, 1.0f, const_cast<uint8_t*>(fake), N,
+                     out_dtype, 0, FP8_E4M3, FP8_E4M3);
+    const int prc = describe_plan(j, pick_bn(j.rows_p, j.rows_q, j.K, SPARSE_BN_MAX), true, M, N, info);
+    info->swapped = 0;                                  // A is always the sparse P side
+    return prc;
+}
+
 extern "C" int gemm_fp8_mx_plan(int64_t M, int64_t N, int64_t K, int out_dtype, fp8_gemm_plan_info* info)
 {
     using namespace gb300;
@@ -2705,11 +2753,9 @@ extern "C" int gemm_fp8_grouped_autotune(const fp8_gemm_problem* problems, int n
     // two k-blocks per stage up to 128 wide); split counts stay fixed per
     // problem, so no candidate changes a result
     int max_bn = 0;
-    bool pair_ok = jobs[0].sfp == nullptr;
-    for (int i = 0; i < n; ++i) {
+    const bool pair_ok = jobs[0].sfp == nullptr && pairs_allowed(jobs, bns, n, max_ctas, 0);
+    for (int i = 0; i < n; ++i)
         max_bn = std::max(max_bn, bns[i]);
-        pair_ok = pair_ok && jobs[i].E == nullptr && bns[i] == BN_MAX;
-    }
     std::vector<TileChoice> cands;
     const int gms[5] = {2, 4, 8, 16, 32};
     for (int mt = 1; mt <= 3; ++mt) {

@@ -474,6 +474,28 @@ __device__ __forceinline__ void tmem_cp_32x128b_warpx4_pair(uint32_t taddr, uint
     asm volatile("tcgen05.cp.cta_group::2.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
 }
 
+// 2:4-sparse MMA of a CTA pair (M = 256 over the two CTAs, logical K = 64):
+// each CTA's shared memory holds the kept codes of its own 128 rows of A and
+// N / 2 rows of B, and its tensor memory the metadata of its own 128 rows at
+// meta_tmem (the layout of mma_sp_f8f6f4).
+__device__ __forceinline__ void mma_sp_f8f6f4_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                                   uint32_t meta_tmem, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "tcgen05.mma.sp.cta_group::2.kind::f8f6f4 [%0], %1, %2, [%3], %4, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(meta_tmem), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// As tmem_cp_128x128b for a CTA pair: each CTA's shared memory at the
+// descriptor's offset goes to its own tensor memory at taddr.
+__device__ __forceinline__ void tmem_cp_128x128b_pair(uint32_t taddr, uint64_t sdesc)
+{
+    asm volatile("tcgen05.cp.cta_group::2.128x128b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
 // Arrive once on the mbarrier at shared-memory offset `bar` of every CTA in
 // cta_mask (cluster ranks) when the pair's tcgen05 operations issued so far
 // by this thread have completed.
