@@ -395,8 +395,8 @@ int gemm_fp8_grouped_ex(const fp8_gemm_problem *problems, int num_problems, int 
  * with K >= 4096, occupy as many SMs as 128-row tiles would: 3 when pairs
  * apply as above, else 2; a launch mixing dense and sparse problems always
  * uses 1).
- * group_m: M-blocks per raster band (0 = 16, or 8 for CTA-pair launches
- * whose operands exceed the L2 cache).  Results do not depend on
+ * group_m: M-blocks per raster band (0 = 16, or 8 for dense CTA-pair
+ * launches whose operands exceed the L2 cache).  Results do not depend on
  * either.  Affects launches enqueued after the call, from any thread. */
 int fp8_gemm_set_tile_config(int mt, int group_m);
 

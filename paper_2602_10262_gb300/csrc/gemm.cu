@@ -46,7 +46,7 @@ constexpr int BK = 128;                   // codes per k-block (one 128-byte swi
 constexpr int BN_MAX = 256;
 constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M_DEFAULT = 16;       // raster: M-blocks per band
-constexpr int GROUP_M_PAIR_LARGE = 8;     // CTA-pair launches whose operands exceed L2
+constexpr int GROUP_M_PAIR_LARGE = 8;     // dense CTA-pair launches whose operands exceed L2
 constexpr int PREFETCH_STAGES = 2;        // first-tile stages prefetched into L2 at kernel entry
 // 2:4-sparse tiles: per stage the kept A codes (rows x 64 bytes, 64-byte
 // swizzle) and the metadata (rows x 16 bytes) fill the A region; the metadata
@@ -1901,11 +1901,15 @@ TileChoice choose(const Job* jobs, const int* bns, int n, int max_ctas, const Ti
         // root of the tiles per wave.  Pairs run half as many tiles at once
         // as one-CTA tiles: measured at 16384^3, 8-row bands read 4.09 GB
         // from HBM per launch against 4.95 GB for 16-row ones, in the same
-        // time (one-CTA 256-row tiles: 3.13 GB at 16, 3.25 at 8).
+        // time (one-CTA 256-row tiles: 3.13 GB at 16, 3.25 at 8).  2:4 pairs
+        // read 0.625 of the dense A bytes per row, which moves the best band
+        // up: 16-row bands ran 2.5 % faster than 8-row ones at 16384^3 and
+        // 16384 x 4096 x 14336, and level on smaller shapes.
         bool beyond_l2 = false;
         for (int i = 0; i < n; ++i)
             beyond_l2 = beyond_l2 || (jobs[i].rows_p + jobs[i].rows_q) * jobs[i].K > l2_bytes();
-        c.group_m = c.mt == 3 && beyond_l2 ? GROUP_M_PAIR_LARGE : GROUP_M_DEFAULT;
+        const bool sparse_list = n > 0 && jobs[0].E != nullptr;
+        c.group_m = c.mt == 3 && beyond_l2 && !sparse_list ? GROUP_M_PAIR_LARGE : GROUP_M_DEFAULT;
     }
     return c;
 }

@@ -169,3 +169,11 @@ def test_sparse_narrow_tiles_take_no_pairs(gb, pair):
     """Forced pairs fall back where they do not apply: N tiles under 224."""
     info = gb.gemm_fp8_sparse24_plan(2048, 200, 1024)
     assert info["mt"] != 3 and info["cluster"] == 0, info
+
+
+def test_sparse_pair_raster_band(gb):
+    """2:4 pair launches keep 16-row raster bands even beyond L2 (their A
+    rows are 0.625 of the dense bytes); dense pairs there take 8."""
+    assert gb.gemm_fp8_sparse24_plan(16384, 16384, 16384)["mt"] == 3
+    assert gb.gemm_fp8_sparse24_plan(16384, 16384, 16384)["group_m"] == 16
+    assert gb.gemm_fp8_dense_plan(16384, 16384, 16384)["group_m"] == 8
