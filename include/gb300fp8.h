@@ -343,6 +343,11 @@ int gemm_fp8_sparse24_fmt(int64_t M, int64_t N, int64_t K, const uint8_t *a_vals
  * checked as a whole and then run as consecutive launches of up to that
  * many problems each, in list order, on `stream` (the autotuner and the
  * CUDA-graph form take at most FP8_GROUPED_MAX_PROBLEMS: FP8_ERR_SHAPE).
+ * One launch runs one tile kind, so (unless fp8_gemm_set_tile_config forces
+ * a kind, or the autotuner has tuned this exact list) the problems that
+ * would run on CTA-pair tiles alone are launched apart from the rest, one
+ * launch for the dense ones and one for the 2:4 ones, after a launch of the
+ * rest; the CUDA-graph form keeps the whole list in one launch.
  * Results are bitwise identical to issuing each problem alone.
  * ------------------------------------------------------------------------- */
 #define FP8_GROUPED_MAX_PROBLEMS 32

@@ -2726,8 +2726,47 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
     if (rc != FP8_OK || n == 0)
         return rc;
     static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
-    memset(&prm, 0, sizeof(prm));
-    return run_jobs(prm, jobs, bns, n, max_ctas, st);
+    // A launch takes one tile kind, and one small or mixed-kind problem puts
+    // the whole list on 128-row tiles.  So problems that would run on CTA
+    // pairs alone (the large ones) are launched apart from the rest, one
+    // launch per kind (dense, 2:4), after the rest; a list whose tile kind
+    // is forced or tuned as a whole keeps its one launch.
+    int group[FP8_GROUPED_MAX_PROBLEMS];
+    int count[3] = {0, 0, 0};
+    bool whole = n == 1 || g_force_mt.load(std::memory_order_relaxed) != 0;
+    if (!whole) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        whole = g_tuned.count(signature(jobs, bns, n, max_ctas)) != 0;
+    }
+    for (int i = 0; i < n; ++i) {
+        group[i] = 0;
+        if (!whole && choose(&jobs[i], &bns[i], 1, max_ctas, nullptr).mt == 3)
+            group[i] = jobs[i].E ? 2 : 1;
+        ++count[group[i]];
+    }
+    if (count[0] == n || count[1] == n || count[2] == n) {
+        memset(&prm, 0, sizeof(prm));
+        return run_jobs(prm, jobs, bns, n, max_ctas, st);
+    }
+    for (int g = 0; g < 3; ++g) {
+        Job gj[FP8_GROUPED_MAX_PROBLEMS];
+        int gbn[FP8_GROUPED_MAX_PROBLEMS];
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            if (group[i] == g) {
+                gj[m] = jobs[i];
+                gbn[m] = bns[i];
+                ++m;
+            }
+        }
+        if (m == 0)
+            continue;
+        memset(&prm, 0, sizeof(prm));
+        rc = run_jobs(prm, gj, gbn, m, max_ctas, st);
+        if (rc != FP8_OK)
+            return rc;
+    }
+    return FP8_OK;
 }
 
 extern "C" int gemm_fp8_grouped_autotune(const fp8_gemm_problem* problems, int num_problems,

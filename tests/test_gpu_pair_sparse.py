@@ -177,3 +177,50 @@ def test_sparse_pair_raster_band(gb):
     assert gb.gemm_fp8_sparse24_plan(16384, 16384, 16384)["mt"] == 3
     assert gb.gemm_fp8_sparse24_plan(16384, 16384, 16384)["group_m"] == 16
     assert gb.gemm_fp8_dense_plan(16384, 16384, 16384)["group_m"] == 8
+
+
+def test_grouped_list_split_by_tile_kind_equals_singles(gb, orc):
+    """A list mixing large dense and 2:4 problems (CTA-pair tiles alone) with
+    small ones runs as separate launches per tile kind; every output equals
+    the problem issued alone, bit for bit, and forcing one kind for the
+    whole list changes nothing either."""
+    shapes = [(2048, 2560, 1024, False), (4096, 2048, 1024, True), (64, 512, 256, False),
+              (300, 200, 512, True), (1024, 4096, 2048, False)]
+    probs, outs, singles, keep = [], [], [], []
+    for i, (M, N, K, sparse) in enumerate(shapes):
+        A, dA = orc.quantize(workloads.randn_f32((M, K), seed=300 + i), 1)
+        B, dB = orc.quantize(workloads.randn_f32((N, K), seed=310 + i), 1)
+        tB, tdA, tdB = _cuda(B), _cuda(dA), _cuda(dB)
+        C = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+        if sparse:
+            vals, meta = orc.prune24(A)
+            tv, tm = _cuda(vals), _cuda(meta)
+            probs.append(gb.make_problem(tv, tB, tdA, 1, tdB, 1, C, 1.0, gb.OUT_BF16, A_meta=tm))
+            singles.append(gb.gemm_fp8_sparse24(tv, tm, tB, tdA, 1, tdB, 1, 1.0, gb.OUT_BF16))
+            keep += [tv, tm]
+        else:
+            tA = _cuda(A)
+            probs.append(gb.make_problem(tA, tB, tdA, 1, tdB, 1, C, 1.0, gb.OUT_BF16))
+            singles.append(gb.gemm_fp8_dense(tA, tB, tdA, 1, tdB, 1, 1.0, gb.OUT_BF16))
+            keep.append(tA)
+        keep += [tB, tdA, tdB]
+        outs.append(C)
+    assert gb.gemm_fp8_dense_plan(2048, 2560, 1024)["mt"] == 3
+    assert gb.gemm_fp8_sparse24_plan(4096, 2048, 1024)["mt"] == 3
+    assert gb.gemm_fp8_dense_plan(1024, 4096, 2048)["mt"] == 1
+    gb.gemm_fp8_grouped(probs)
+    torch.cuda.synchronize()
+    assert gb.fp8_last_device_error() == 0
+    for i, (C, Cs) in enumerate(zip(outs, singles)):
+        assert torch.equal(C, Cs), i
+    try:
+        gb.fp8_gemm_set_tile_config(1, 0)
+        for C in outs:
+            C.zero_()
+        gb.gemm_fp8_grouped_ex(probs, 136)
+        torch.cuda.synchronize()
+        assert gb.fp8_last_device_error() == 0
+    finally:
+        gb.fp8_gemm_set_tile_config(0, 0)
+    for i, (C, Cs) in enumerate(zip(outs, singles)):
+        assert torch.equal(C, Cs), i
