@@ -97,6 +97,11 @@ constexpr int SPARSE_BN_MAX_MT2 = 224;
 // k-blocks per stage, three 64 KB stages) and holding its 128 x 256 half of
 // the accumulator; the even CTA issues the MMAs.  Per SM that is MT = 2's
 // bytes per FLOP with half of MT = 2's tensor memory per accumulator.
+// 2:4 pairs (SP): 256 x 224 tiles, each CTA loading the kept codes and
+// metadata of its 128 rows of A and 112 rows of B per k-block (four 48 KB
+// stages of two k-blocks); two 224-column accumulators at columns 0 and 256
+// and the metadata ring between them (columns 224..255, each CTA holding its
+// own rows' metadata).
 constexpr int PAIR_TMEM_COLS = 512;       // columns per CTA: two accumulators (the epilogue of
                                           // one tile overlaps the MMAs of the next)
 
