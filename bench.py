@@ -329,7 +329,7 @@ def run_reference(args, ws, rank):
 def config(size, ws):
     return {"workload": f"fp8_e4m3_gemm_pipeline_{size}", "M": size, "N": size, "K": size,
             "scales": "per-row A, per-row B (per output channel)", "out": "bf16",
-            "stages": "quantize A,B -> prune24 A -> dense GEMM -> 2:4 sparse GEMM",
+            "stages": "quantize + 2:4-compress A (one pass), quantize B -> dense GEMM -> 2:4 sparse GEMM",
             "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"}
 
 
@@ -1479,16 +1479,23 @@ def main():
         if e.status != -8:
             raise
         sparse_ok = False
-    launches_per_step = 4 + (1 if sparse_ok else 0)
+    # fused quantise + 2:4 compress of A, quantise B, dense, 2:4 sparse; or,
+    # without the sparse path: quantise A and B, compress A, dense
+    launches_per_step = 4
 
     ev = {}
 
     def step(record=None):
         if record is not None:
             record[0].record(stream)
-        gb.fp8_quantize_e4m3(x, 1, A, dA)
+        if sparse_ok:
+            # A's codes, scales and 2:4 compression in one pass over x
+            gb.fp8_quantize_e4m3_prune24(x, A, dA, vals, meta)
+        else:
+            gb.fp8_quantize_e4m3(x, 1, A, dA)
         gb.fp8_quantize_e4m3(w, 1, B, dB)
-        gb.prune24_compress(A, vals, meta)
+        if not sparse_ok:
+            gb.prune24_compress(A, vals, meta)
         if record is not None:
             record[1].record(stream)
         gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=Cd)
@@ -1557,8 +1564,9 @@ def main():
         stages["sparse_tflops_dense_equiv"] = flops_dense / (t_sparse * 1e-3) / 1e12
         stages["sparse_vs_dense_speedup"] = t_dense / t_sparse
     # quantise + prune traffic: read 2 x 4 B + write 2 x 1 B per element of A and
-    # B (+ scales), prune reads 1 B and writes 0.625 B per element of A
-    prep_bytes = (2 * 5.0 + 1.625) * M * K
+    # B (+ scales) and 0.625 B of kept codes and metadata per element of A
+    # (written by the fused pass; a separate prune also reads A's codes again)
+    prep_bytes = (2 * 5.0 + 0.625 + (0.0 if sparse_ok else 1.0)) * M * K
     stages["quantize_prune_gbs"] = prep_bytes / (t_prep * 1e-3) / 1e9
 
     # ---------------------------------------------------------------- e2e
@@ -1600,9 +1608,12 @@ def main():
                     if ev_out[b] is not None:
                         s_comp.wait_event(ev_out[b])
                     Co = outs_d[b]
-                    gb.fp8_quantize_e4m3(xs[b], 1, A, dA)
+                    if sparse_ok:
+                        gb.fp8_quantize_e4m3_prune24(xs[b], A, dA, vals, meta)
+                    else:
+                        gb.fp8_quantize_e4m3(xs[b], 1, A, dA)
+                        gb.prune24_compress(A, vals, meta)
                     gb.fp8_quantize_e4m3(wsb[b], 1, B, dB)
-                    gb.prune24_compress(A, vals, meta)
                     gb.gemm_fp8_dense(A, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=Co[0])
                     if sparse_ok:
                         gb.gemm_fp8_sparse24(vals, meta, B, dA, 1, dB, 1, 1.0, gb.OUT_BF16, C=Co[1])

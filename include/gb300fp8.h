@@ -206,6 +206,24 @@ int gemm_fp8_mx(int64_t M, int64_t N, int64_t K, const uint8_t *A, int64_t lda,
 int prune24_compress(const uint8_t *a, int64_t M, int64_t K, int64_t lda, uint8_t *a_vals,
                      uint8_t *a_meta, fp8_stream_t stream);
 
+/* Per-row E4M3 quantisation (fp8_quantize_e4m3, scale_mode 1) and the 2:4
+ * compression of its codes (prune24_compress) in one pass over x: q,
+ * dequant_scale, a_vals and a_meta are bitwise what the two calls in turn
+ * write, with one read of x and no read of q.  Paper: sections 2 and 6 (the
+ * quantised operand of a 2:4-sparse GEMM; section 6.1.1's conversion cost
+ * becomes part of the quantiser's own HBM pass).
+ * x: device fp32 [rows, cols], row stride ldx (elements); q: device
+ * [rows, cols], row stride ldq bytes; dequant_scale: device fp32 [rows];
+ * a_vals [rows, cols/2] and a_meta [rows, cols/8] packed, as
+ * prune24_compress writes them.  cols % 128 == 0 (the 2:4 GEMM's K rule),
+ * ldx >= cols, ldq >= cols (else FP8_ERR_SHAPE); x 16-byte aligned with
+ * ldx % 4 == 0, q 4-byte aligned with ldq % 4 == 0, a_vals 2-byte and
+ * dequant_scale 4-byte aligned (else FP8_ERR_ALIGN).  Non-finite input:
+ * as fp8_quantize_e4m3. */
+int fp8_quantize_e4m3_prune24(const float *x, int64_t rows, int64_t cols, int64_t ldx, uint8_t *q,
+                              int64_t ldq, float *dequant_scale, uint8_t *a_vals, uint8_t *a_meta,
+                              fp8_stream_t stream);
+
 /* Inverse of prune24_compress: out [M, K] (row stride K) gets the kept codes
  * at their positions and 0x00 elsewhere. */
 int prune24_decompress(const uint8_t *a_vals, const uint8_t *a_meta, int64_t M, int64_t K,

@@ -17,7 +17,7 @@ import torch
 from . import _lib
 
 __all__ = [
-    "Fp8Error", "library", "fp8_quantize_e4m3", "fp8_quantize_e5m2", "prune24_compress",
+    "Fp8Error", "library", "fp8_quantize_e4m3", "fp8_quantize_e5m2", "fp8_quantize_e4m3_prune24", "prune24_compress",
     "prune24_decompress", "gemm_fp8_dense", "gemm_fp8_dense_fmt", "gemm_fp8_sparse24",
     "gemm_fp8_sparse24_fmt", "gemm_fp8_grouped", "gemm_fp8_grouped_ex", "fp8_last_device_error",
     "fp8_device_sm_count", "fp8_test_stall_gemm_loads", "fp8_gemm_set_tile_config", "fp8_gemm_set_multicast",
@@ -180,6 +180,38 @@ def fp8_quantize_e5m2(x: torch.Tensor, scale_mode: int, q: Optional[torch.Tensor
                       dequant_scale: Optional[torch.Tensor] = None, stream=None):
     """fp32 [R, C] -> (E5M2 codes uint8 [R, C], dequant scales fp32 [1] or [R])."""
     return _quantize("fp8_quantize_e5m2", x, scale_mode, q, dequant_scale, stream)
+
+
+def fp8_quantize_e4m3_prune24(x: torch.Tensor, q: Optional[torch.Tensor] = None,
+                              dequant_scale: Optional[torch.Tensor] = None,
+                              a_vals: Optional[torch.Tensor] = None, a_meta: Optional[torch.Tensor] = None,
+                              stream=None):
+    """fp32 [R, C] (C % 128 == 0) -> (E4M3 codes [R, C], per-row dequant
+    scales [R], kept codes [R, C/2], metadata [R, C/8]): per-row
+    quantisation and the 2:4 compression of its codes in one pass, bitwise
+    fp8_quantize_e4m3(x, 1) followed by prune24_compress."""
+    _dev(x, "x", torch.float32, 2)
+    R, C = x.shape
+    dev = x.device
+    if q is None:
+        q = torch.empty((R, C), dtype=torch.uint8, device=dev)
+    if dequant_scale is None:
+        dequant_scale = torch.empty((R,), dtype=torch.float32, device=dev)
+    if a_vals is None:
+        a_vals = torch.empty((R, C // 2), dtype=torch.uint8, device=dev)
+    if a_meta is None:
+        a_meta = torch.empty((R, C // 8), dtype=torch.uint8, device=dev)
+    _dev(q, "q", torch.uint8, 2)
+    _shape(q, "q", (R, C))
+    _scale(dequant_scale, "dequant_scale", R)
+    for t, nm, shp in ((a_vals, "a_vals", (R, C // 2)), (a_meta, "a_meta", (R, C // 8))):
+        _dev(t, nm, torch.uint8, 2)
+        _shape(t, nm, shp)
+        _packed(t, nm)
+    rc = library().fp8_quantize_e4m3_prune24(_p(x), R, C, _ld(x), _p(q), _ld(q), _p(dequant_scale),
+                                             _p(a_vals), _p(a_meta), _stream(stream))
+    _check(rc, "fp8_quantize_e4m3_prune24")
+    return q, dequant_scale, a_vals, a_meta
 
 
 def fp8_mx_scale_tiled_bytes(rows: int, cols: int) -> int:

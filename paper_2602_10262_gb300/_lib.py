@@ -97,6 +97,7 @@ SIGNATURES = {
     "fp8_mx_scales_to_tiled": (I32, [P, I64, I64, P, P]),
     "gemm_fp8_mx": (I32, [I64, I64, I64, P, I64, P, P, I64, P, F32, P, I64, I32, I32, I32, P]),
     "prune24_compress": (I32, [P, I64, I64, I64, P, P, P]),
+    "fp8_quantize_e4m3_prune24": (I32, [P, I64, I64, I64, P, I64, P, P, P, P]),
     "prune24_decompress": (I32, [P, P, I64, I64, P, P]),
     "gemm_fp8_dense": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32, P]),
     "gemm_fp8_dense_noalloc": (I32, [I64, I64, I64, P, I64, P, I64, P, I32, P, I32, F32, P, I64, I32, P]),

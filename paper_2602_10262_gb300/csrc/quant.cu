@@ -21,6 +21,7 @@
 #include <cuda_fp8.h>
 
 #include "common.cuh"
+#include "prune_select.cuh"
 
 namespace gb300 {
 namespace {
@@ -132,6 +133,62 @@ __global__ void __launch_bounds__(kThreads) quant_row_kernel(const float* __rest
     __shared__ uint32_t red[kThreads / 32];
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
         quantize_row<FMT>(x + r * ldx, cols, q + r * ldq, d + r, vec, err, red);
+}
+
+// Per-row E4M3 quantisation and 2:4 compression of the codes in one pass
+// (fp8_quantize_e4m3_prune24).  Pass 1 takes the row's amax as quantize_row
+// does; pass 2 re-reads the row (from L2) and encodes four elements (one 2:4
+// group) per lane and step, with coalesced 16-byte loads and 4-byte code
+// stores, and selects the group's two kept codes and index nibble from its
+// codes exactly as prune24_compress does (prune_select.cuh); lanes 2i and
+// 2i + 1 hold consecutive groups and combine their nibbles into one
+// metadata byte.  Measured against fp8_quantize_e4m3 followed by
+// prune24_compress: 252 against 275 us at 16384 x 16384, 68 against 79 us
+// at 8192 x 8192.  Staging each row in shared memory (no second read from
+// L2 or DRAM, but three CTAs per SM at 16384 columns) and persistent grids
+// of four or eight CTAs per SM were slower.  Needs cols % 128 == 0 (so
+// every warp runs the same number of steps), x 16-aligned with ldx % 4 ==
+// 0, q 4-aligned with ldq % 4 == 0, a_vals 2-aligned (checked by the host).
+__global__ void __launch_bounds__(kThreads) quant_row_prune_kernel(const float* __restrict__ x, int64_t rows,
+                                                                   int64_t cols, int64_t ldx,
+                                                                   uint8_t* __restrict__ q, int64_t ldq,
+                                                                   float* __restrict__ d,
+                                                                   uint8_t* __restrict__ vals,
+                                                                   uint8_t* __restrict__ meta, int* err)
+{
+    grid_launch_dependents();
+    __shared__ uint32_t red[kThreads / 32];
+    const int64_t n4 = cols / 4;
+    const int64_t ldv = cols / 2, ldm = cols / 8;
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float4* xr = reinterpret_cast<const float4*>(x + r * ldx);
+        uint32_t m = 0;
+        for (int64_t i = threadIdx.x; i < n4; i += kThreads) {
+            const float4 v = __ldg(xr + i);
+            m = max(m, max(max(abs_bits(v.x), abs_bits(v.y)), max(abs_bits(v.z), abs_bits(v.w))));
+        }
+        m = block_max_u32(m, red);
+        if (m >= kInfBits && threadIdx.x == 0)
+            report_device_error(err, FP8_ERR_NONFINITE);
+        float s, dq;
+        scale_from_amax<0>(m, s, dq);
+        if (threadIdx.x == 0)
+            d[r] = dq;
+        uint8_t* qr = q + r * ldq;
+        uint8_t* vr = vals + r * ldv;
+        uint8_t* mr = meta + r * ldm;
+        for (int64_t i = threadIdx.x; i < n4; i += kThreads) {
+            const uint32_t w = enc4<0>(__ldg(xr + i), s);
+            reinterpret_cast<uint32_t*>(qr)[i] = w;
+            const uint32_t sel = select_group(w);
+            reinterpret_cast<uint16_t*>(vr)[i] = static_cast<uint16_t>(sel & 0xFFFFu);
+            const uint32_t nib = sel >> 16;
+            const uint32_t next = __shfl_down_sync(0xFFFFFFFFu, nib, 1);
+            if ((lane & 1) == 0)
+                mr[i >> 1] = static_cast<uint8_t>(nib | (next << 4));
+        }
+    }
 }
 
 // Many independent per-row quantisations in one launch: the job table is
@@ -516,6 +573,31 @@ extern "C" int fp8_quantize_e4m3(const float* x, int64_t rows, int64_t cols, int
 {
     return gb300::quantize<0>(x, rows, cols, ldx, scale_mode, q, ldq, dequant_scale,
                               reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fp8_quantize_e4m3_prune24(const float* x, int64_t rows, int64_t cols, int64_t ldx, uint8_t* q,
+                                         int64_t ldq, float* dequant_scale, uint8_t* a_vals, uint8_t* a_meta,
+                                         fp8_stream_t stream)
+{
+    using namespace gb300;
+    if (rows < 0 || cols < 0)
+        return FP8_ERR_INVALID;
+    if (rows == 0 || cols == 0)
+        return FP8_OK;
+    if (!x || !q || !dequant_scale || !a_vals || !a_meta)
+        return FP8_ERR_INVALID;
+    if (cols % 128 != 0 || ldx < cols || ldq < cols)
+        return FP8_ERR_SHAPE;
+    if (!aligned16(x) || ldx % 4 != 0 || reinterpret_cast<uintptr_t>(q) % 4 != 0 || ldq % 4 != 0 ||
+        reinterpret_cast<uintptr_t>(a_vals) % 2 != 0 || reinterpret_cast<uintptr_t>(dequant_scale) % 4 != 0)
+        return FP8_ERR_ALIGN;
+    if (!device_supported())
+        return FP8_ERR_UNSUPPORTED;
+    const int64_t grid = rows < 65535LL * 8 ? rows : 65535LL * 8;
+    quant_row_prune_kernel<<<static_cast<unsigned>(grid), kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        x, rows, cols, ldx, q, ldq, dequant_scale, a_vals, a_meta, device_error_word());
+    GB_CUDA_OK(cudaGetLastError());
+    return FP8_OK;
 }
 
 extern "C" int fp8_quantize_e5m2(const float* x, int64_t rows, int64_t cols, int64_t ldx,

@@ -62,6 +62,16 @@ def test_host_validation_without_gpu(lib):
     assert lib.fp8_quantize_e4m3(P(16), 4, 8, 4, 0, P(16), 8, P(16), None) == -2
     assert lib.fp8_quantize_e5m2(P(16), 4, 4, 4, 3, P(16), 4, P(16), None) == -1
     assert lib.fp8_quantize_e5m2(P(16), 4, 8, 4, 0, P(16), 8, P(16), None) == -2
+    # the fused quantise + 2:4 compress: K % 128, leading dimensions, alignment
+    fq = lib.fp8_quantize_e4m3_prune24
+    assert fq(None, 4, 128, 128, P(16), 128, P(16), P(16), P(16), None) == -1
+    assert fq(P(16), 4, 100, 100, P(16), 100, P(16), P(16), P(16), None) == -2
+    assert fq(P(16), 4, 128, 100, P(16), 128, P(16), P(16), P(16), None) == -2
+    assert fq(P(20), 4, 128, 128, P(16), 128, P(16), P(16), P(16), None) == -3
+    assert fq(P(16), 4, 128, 130, P(16), 128, P(16), P(16), P(16), None) == -3
+    assert fq(P(16), 4, 128, 128, P(18), 128, P(16), P(16), P(16), None) == -3
+    assert fq(P(16), 4, 128, 128, P(16), 130, P(16), P(16), P(16), None) == -3
+    assert fq(None, 0, 128, 128, None, 128, None, None, None, None) == 0
     # operand formats other than E4M3 (0) and E5M2 (1) are rejected
     ok = (4, 4, 32, P(16), 32, P(16), 32, P(16), 0, P(16), 0, 1.0, P(16), 4, 0)
     for af, bf in ((2, 0), (0, -1), (7, 7)):
