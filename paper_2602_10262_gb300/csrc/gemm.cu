@@ -2731,6 +2731,18 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
     if (rc != FP8_OK || n == 0)
         return rc;
     static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
+    static thread_local Params<1> prm1;
+    // a one-problem launch takes the one-problem kernel variant: the same
+    // tiles and arithmetic, with a 32nd of the kernel parameters to upload
+    // (measured: 6.05 against 6.78 us for a 1024^3 launch)
+    auto run = [&](const Job* js, const int* bs, int m) -> int {
+        if (m == 1) {
+            memset(&prm1, 0, sizeof(prm1));
+            return run_jobs(prm1, js, bs, 1, max_ctas, st);
+        }
+        memset(&prm, 0, sizeof(prm));
+        return run_jobs(prm, js, bs, m, max_ctas, st);
+    };
     // A launch takes one tile kind, and one small or mixed-kind problem puts
     // the whole list on 128-row tiles.  So problems that would run on CTA
     // pairs alone (the large ones) are launched apart from the rest, one
@@ -2749,10 +2761,8 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
             group[i] = jobs[i].E ? 2 : 1;
         ++count[group[i]];
     }
-    if (count[0] == n || count[1] == n || count[2] == n) {
-        memset(&prm, 0, sizeof(prm));
-        return run_jobs(prm, jobs, bns, n, max_ctas, st);
-    }
+    if (count[0] == n || count[1] == n || count[2] == n)
+        return run(jobs, bns, n);
     for (int g = 0; g < 3; ++g) {
         Job gj[FP8_GROUPED_MAX_PROBLEMS];
         int gbn[FP8_GROUPED_MAX_PROBLEMS];
@@ -2766,8 +2776,7 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
         }
         if (m == 0)
             continue;
-        memset(&prm, 0, sizeof(prm));
-        rc = run_jobs(prm, gj, gbn, m, max_ctas, st);
+        rc = run(gj, gbn, m);
         if (rc != FP8_OK)
             return rc;
     }
