@@ -2732,13 +2732,15 @@ extern "C" int gemm_fp8_grouped_ex(const fp8_gemm_problem* problems, int num_pro
         return rc;
     static thread_local Params<FP8_GROUPED_MAX_PROBLEMS> prm;
     static thread_local Params<1> prm1;
-    // a one-problem launch takes the one-problem kernel variant: the same
-    // tiles and arithmetic, with a 32nd of the kernel parameters to upload
-    // (measured: 6.05 against 6.78 us for a 1024^3 launch)
+    // a one-problem launch runs as a single call does: the one-problem
+    // kernel variant (the same tiles and arithmetic, a 32nd of the kernel
+    // parameters to upload: 6.05 against 6.78 us for a 1024^3 launch) and,
+    // uncapped, split-K slices added within clusters (64 x 8192 x 8192:
+    // 19.7 against 21.6 us through the workspace; bitwise the same sums)
     auto run = [&](const Job* js, const int* bs, int m) -> int {
         if (m == 1) {
             memset(&prm1, 0, sizeof(prm1));
-            return run_jobs(prm1, js, bs, 1, max_ctas, st);
+            return run_jobs(prm1, js, bs, 1, max_ctas, st, nullptr, true);
         }
         memset(&prm, 0, sizeof(prm));
         return run_jobs(prm, js, bs, m, max_ctas, st);
