@@ -365,7 +365,9 @@ int gemm_fp8_sparse24_fmt(int64_t M, int64_t N, int64_t K, const uint8_t *a_vals
  * a kind, or the autotuner has tuned this exact list) the problems that
  * would run on CTA-pair tiles alone are launched apart from the rest, one
  * launch for the dense ones and one for the 2:4 ones, after a launch of the
- * rest; the CUDA-graph form keeps the whole list in one launch.
+ * rest; the CUDA-graph form keeps the whole list in one launch.  A list
+ * of one problem runs as the single call would (the same kernel variant
+ * and, without a CTA cap, split-K slices added within clusters).
  * Results are bitwise identical to issuing each problem alone.
  * ------------------------------------------------------------------------- */
 #define FP8_GROUPED_MAX_PROBLEMS 32
