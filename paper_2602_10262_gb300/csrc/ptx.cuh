@@ -1,5 +1,5 @@
 // Inline-PTX building blocks for sm_103a: mbarrier, TMA (cp.async.bulk.tensor),
-// tcgen05 (TMEM alloc / MMA / commit / ld / st / cp) and fences.
+// tcgen05 (TMEM alloc / MMA / commit / ld / cp) and fences.
 //
 // Every wait here is bounded: it polls the barrier and gives up after a
 // limit (kWaitLimitNs unless the launch sets another) of %globaltimer, so a
@@ -380,11 +380,6 @@ __device__ __forceinline__ void tmem_ld_wait()
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_st_wait()
-{
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
 // 32 lanes x 32 bits, 16 consecutive columns: thread t of the warp receives
 // columns [col, col + 16) of lane (lane_base + t).
 __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)[16])
@@ -397,19 +392,6 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
-}
-
-// 32 lanes x 32 bits, one column: thread t writes v to lane (lane_base + t).
-__device__ __forceinline__ void tmem_st_32x32b_x1(uint32_t taddr, uint32_t v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void tmem_st_32x32b_x2(uint32_t taddr, uint32_t v0, uint32_t v1)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(v0),
-                 "r"(v1)
-                 : "memory");
 }
 
 // ---------------------------------------------------------------- CTA pairs (cta_group::2)
