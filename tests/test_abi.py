@@ -99,6 +99,21 @@ def test_stall_switch_validates_and_resets(lib):
     assert lib.fp8_test_stall_gemm_loads(0, 0.0) == 0
 
 
+def test_plan_queries_reject_bad_arguments(lib):
+    """The plan queries (dense, 2:4, block-scaled) refuse a missing info
+    struct, empty or negative sizes and bad output types before any CUDA
+    call, and sizes past int32 / 2 as shapes."""
+    from paper_2602_10262_gb300 import _lib
+    info = _lib.FP8PlanInfo()
+    ref = ctypes.byref(info)
+    for fn in (lib.gemm_fp8_dense_plan, lib.gemm_fp8_sparse24_plan, lib.gemm_fp8_mx_plan):
+        assert fn(256, 256, 256, 0, None) == -1
+        assert fn(0, 256, 256, 0, ref) == -1
+        assert fn(256, -1, 256, 0, ref) == -1
+        assert fn(256, 256, 256, 2, ref) == -1
+        assert fn(1 << 31, 256, 256, 0, ref) == -2
+
+
 def test_tile_and_multicast_switches_validate(lib):
     # launch-shape switches (no CUDA call): out-of-range values are refused,
     # the defaults are restored
